@@ -1,0 +1,316 @@
+#!/usr/bin/env python3
+"""Benchmark: parallel tempering + isoenergetic cluster moves on GB300.
+
+Workload (default): 3D Edwards-Anderson spin glass, L = 8 periodic cubic
+lattice (512 spins), Gaussian couplings N(0,1) in fp32, 1000 disorder
+instances in one launch, 24 temperatures geometric in [0.2, 2.0], 2 replicas
+per temperature, ICM at T <= 1.0, one PT pass and one measurement per sweep.
+A step = `--sweeps-per-step` full simulation steps (Metropolis sweep, step
+2a/2b at the 17 ICM temperatures, PT pass, observables) of all instances.
+
+Prints one JSON line.  `value` is spin updates per ns over the K timed steps
+(device time from CUDA events on the launching stream, state resident in HBM,
+L2 flushed between steps); `e2e` is the same metric through the C ABI with
+host buffers (H2D of couplings and spins, run, D2H of the observables).
+`--impl reference` times the CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1501_05630_gb300 import inputs as I  # noqa: E402
+
+WORKLOADS = {
+    "3d_gauss_L8": dict(lattice=I.CUBIC3D, L=8, disorder=I.GAUSS, n_inst=1000, T=(0.2, 2.0, 24), T_icm=1.0,
+                        seed=0x1501056300000002,
+                        desc="3D EA L=8 periodic (512 spins), Gaussian N(0,1) fp32, 1000 instances, "
+                             "24 T geometric [0.2,2.0], 2 replicas/T, ICM T<=1.0"),
+    "chimera_pmj_C8": dict(lattice=I.CHIMERA, L=8, disorder=I.PM_J, n_inst=10000, T=(0.2, 3.0, 30), T_icm=1.5,
+                           seed=0x1501056300000003,
+                           desc="chimera C_8 (512 spins), +-J, 10^4 instances multispin-coded, "
+                                "30 T geometric [0.2,3.0], ICM T<=1.5"),
+    "2d_pmj_L8": dict(lattice=I.SQUARE2D, L=8, disorder=I.PM_J, n_inst=1, T=(0.2, 1.5, 16), T_icm=1.0,
+                      seed=0x1501056300000001,
+                      desc="2D EA L=8 periodic (64 spins), +-J, 1 instance, 16 T geometric [0.2,1.5], ICM T<=1.0"),
+}
+
+# Algorithmic thread-operations per spin update of the fused kernel's sweep
+# (Philox4x32-10 share: 10 rounds x (2 wide multiplies + 2 three-input XORs)
+# / 4 draws = 10; local field: z sign injections + z adds; acceptance:
+# uniform, scale, exp2, compare, flip = 5; energy accumulation 1).
+ALG_OPS = {I.GAUSS: lambda z: 10 + 2 * z + 5 + 1,
+           # +-J bit-sliced: field ~1 per bit; extract 3, index 1, load 1, compare 1, flip 1, energy 1
+           I.PM_J: lambda z: 10 + 1 + 8}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_throughput(wl, sweeps: int, n_inst: int, threads: int):
+    """The CPU oracle, as it stands, on n_inst instances x `sweeps` sweeps,
+    instances spread over `threads` host threads (ctypes drops the GIL)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from oracle import oracle as O
+    g = O.Geometry(wl["lattice"], wl["L"])
+    T = I.ladder(*wl["T"])
+    J = I.couplings(g.Nb, wl["disorder"], wl["seed"], range(n_inst))
+    s0 = I.initial_spins(g.N, 2 * len(T), wl["seed"], range(n_inst))
+    insts = [O.Instance(g, J[a].astype(np.float64), T, s0[a], pm=(wl["disorder"] == I.PM_J),
+                        T_icm=wl["T_icm"], seed=wl["seed"], inst=a) for a in range(n_inst)]
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(threads) as ex:
+        list(ex.map(lambda x: x.run(sweeps), insts))
+    dt = time.perf_counter() - t0
+    updates = n_inst * sweeps * g.N * 2 * len(T)
+    return updates / dt / 1e9, dt, updates
+
+
+def run_reference(args, wl, rank):
+    cores = os.cpu_count() or 1
+    if rank != 0:
+        return
+    sweeps = args.ref_sweeps
+    vals = []
+    for _ in range(args.warmup):
+        oracle_throughput(wl, sweeps, cores, cores)
+    for _ in range(args.steps):
+        v, dt, _ = oracle_throughput(wl, sweeps, cores, cores)
+        vals.append(v)
+    value = float(np.mean(vals))
+    n_icm = int(np.sum(I.ladder(*wl["T"]) <= wl["T_icm"]))
+    sample = f"{cores} instances x {sweeps} sweeps per step (of {wl['n_inst']} instances), {cores} threads"
+    print(json.dumps({
+        "impl": "reference", "metric": "spin_updates_per_ns", "value": value, "unit": "updates/ns",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if wl["disorder"] == I.GAUSS else "int64",
+        "data": "synthetic", "config": {"workload": args.workload, "desc": wl["desc"], "n_icm": n_icm},
+        "cpu_baseline": {"value": value, "unit": "updates/ns", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "updates/ns", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS))
+    ap.add_argument("--sweeps-per-step", type=int, default=256)
+    ap.add_argument("--ref-sweeps", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, wl, rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1501_05630_gb300 import build, icmpt
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build.build()
+    stream = torch.cuda.current_stream()
+    ctx = icmpt.Context(local, stream.cuda_stream)
+
+    n = wl["n_inst"]
+    T = I.ladder(*wl["T"])
+    N, Nb = icmpt.lattice_size(wl["lattice"], wl["L"])
+    R = 2 * len(T)
+    ids = np.arange(rank * n, (rank + 1) * n, dtype=np.uint32)   # weak scaling: disjoint instances per rank
+    J = I.couplings(Nb, wl["disorder"], wl["seed"], ids)
+    s0 = I.initial_spins(N, R, wl["seed"], ids)
+    J_pin = torch.from_numpy(J).pin_memory()
+    s_pin = torch.from_numpy(s0).pin_memory()
+    J_dev, s_dev = J_pin.cuda(), s_pin.cuda()
+    b = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], J_dev, T, wl["T_icm"], wl["seed"],
+                    spins=s_dev, instance_ids=ids)
+    info = b.info()
+    S = args.sweeps_per_step
+    n_icm = int(np.sum(T <= wl["T_icm"]))
+    updates_per_step = n * R * N * S
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        b.run(S)
+    barrier()
+    launches0 = b.info()["launches"]
+    times = []
+    with ClockSampler(local) as clk:
+        barrier()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(S)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        barrier()
+        t_wall = time.perf_counter() - t_wall
+    launches = b.info()["launches"] - launches0
+    ms = float(np.sum(times))
+    if world > 1:
+        tt = torch.tensor([ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = updates_per_step * args.steps * world / (ms * 1e6)
+    icm_moves_per_s = n * n_icm * S * args.steps * world / (ms * 1e-3)
+
+    # end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        hb = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], J_pin.numpy(), T, wl["T_icm"], wl["seed"],
+                         spins=s_pin.numpy(), instance_ids=ids)
+        for _ in range(2):
+            hb.load(J_pin.numpy(), s_pin.numpy())
+            hb.run(S)
+            hb.read_observables(hist=False)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hb.load(J_pin.numpy(), s_pin.numpy())          # H2D: couplings + spins
+            hb.run(S)
+            o = hb.read_observables(hist=False)            # D2H: accumulators (waits)
+        barrier()
+        dt = time.perf_counter() - t0
+        if world > 1:
+            tt = torch.tensor([dt], device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            dt = float(tt.item())
+        h2d = J.nbytes + s0.nbytes
+        d2h = o.accE.nbytes + 4 * o.acc_n.nbytes + o.n_meas.nbytes
+        e2e = {"value": updates_per_step * args.steps * world / (dt * 1e9), "unit": "updates/ns",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+        hb.close()
+
+    peaks, peak_src = _peaks()
+    z = 6 if wl["lattice"] != I.SQUARE2D else 4
+    ops_per_update = ALG_OPS[wl["disorder"]](z)
+    per_launch_ms = ms / max(args.steps, 1) / (world if False else 1)
+    achieved = updates_per_step * ops_per_update / (per_launch_ms * 1e-3) / 1e12     # Tops/s
+    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12                   # issue limit
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "fused_kernel",
+                "ops_per_update": ops_per_update,
+                "peak_note": f"152 SMs x 128 thread-instr/clk x sm_max_mhz ({peak_src})"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        ref_sweeps = args.ref_sweeps
+        v, dt, _ = oracle_throughput(wl, ref_sweeps, cores, cores)
+        cpu = {"value": v, "unit": "updates/ns", "cores": cores, "kind": "oracle",
+               "sample": f"{cores} instances x {ref_sweeps} sweeps of the same workload, {dt:.1f} s"}
+
+    if rank == 0:
+        out = {
+            "metric": "spin_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if wl["disorder"] == I.GAUSS else "u32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "instances_per_gpu": n,
+                       "sweeps_per_step": S, "n_icm": n_icm, "l2": "flushed between steps (256 MB write)",
+                       "threads": info["threads"], "ctas_per_sm": info["ctas_per_sm"], "grid": info["grid"],
+                       "smem_bytes": info["smem_bytes"]},
+            "icm_moves_per_s": icm_moves_per_s,
+            "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
+            "clocks": clk.summary(), "wall_s": t_wall,
+        }
+        print(json.dumps(out))
+    b.close()
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

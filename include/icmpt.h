@@ -1,0 +1,202 @@
+/*
+ * icmpt.h -- C ABI of the GB300 library for parallel tempering (PT) with
+ * isoenergetic cluster moves (ICM) on Ising spin glasses (Zhu, Ochoa,
+ * Katzgraber, "Efficient Cluster Algorithm for Spin Glasses in Any Space
+ * Dimension").
+ *
+ * One simulation step of every instance is, in this order (the paper's
+ * "Isoenergetic cluster algorithm", steps 1, 2a, 2b, 3):
+ *   1  one Metropolis sweep of each of the 2 N_T replicas (checkerboard:
+ *      all sites of colour 0, then all of colour 1);
+ *   2a at each ICM temperature, if more than N/2 sites have q_i = -1, the
+ *      spins of copy 1 are all reversed;
+ *   2b at each ICM temperature (T_k <= T_icm), one Houdayer cluster move:
+ *      a uniformly chosen site with q_i = s_i^a s_i^b = -1 seeds the
+ *      connected component of {i : q_i = -1}, which is flipped in both copies;
+ *   3  one PT pass per copy over the neighbouring temperature pairs;
+ *   then the observables of "Benchmark model and observables" (energy, site
+ *   overlap, link overlap q_l, P(q)) are accumulated when t >= t_meas.
+ *
+ * H = -sum_<ij> J_ij s_i s_j, each bond once.
+ *
+ * Conventions for every entry point:
+ *  - Return value: ICM_OK (0) or a negative icm_status.  No C++ exception
+ *    crosses the ABI.  After an error, icm_last_error(ctx) describes it.
+ *  - Handles are opaque and owned by the library; free them with *_destroy.
+ *  - Input arrays are read during the call (host arrays are copied into
+ *    device memory before the call returns); the caller keeps ownership.
+ *  - Output buffers belong to the caller.  Pointers are host pointers unless
+ *    ICM_DEVICE_PTR is set in `flags`, in which case they are device
+ *    pointers on the context's device (e.g. the data of a CUDA torch tensor).
+ *  - Device work is enqueued on the context's stream and is asynchronous;
+ *    the read functions and icm_sync wait for it.
+ *  - A context is used by one host thread at a time.
+ *
+ * Random numbers: Philox4x32-10 (Salmon et al., SC'11), key = the 64-bit
+ * seed, counters keyed by logical coordinates only (never by batch slot or
+ * thread), so that every instance's trajectory is a function of
+ * (seed, instance id, inputs) alone:
+ *   Metropolis update of replica position r = 2k+c at site i, sweep t:
+ *       word r&3 of ctr {i, t, r>>2, inst}
+ *   ICM seed at temperature k, sweep t:     word 0 of ctr {k, t, 0, 1<<24 | inst}
+ *   PT decision, copy c, pair (k,k+1):      word 0 of ctr {k, t, c, 2<<24 | inst}
+ */
+#ifndef ICMPT_H
+#define ICMPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t icm_status;
+#define ICM_OK 0
+#define ICM_ERR_ARG (-1)      /* invalid argument */
+#define ICM_ERR_OOM (-2)      /* device or host allocation failed */
+#define ICM_ERR_BUDGET (-3)   /* request does not fit the memory budget */
+#define ICM_ERR_CUDA (-4)     /* a CUDA runtime call failed */
+#define ICM_ERR_TIMEOUT (-5)  /* a bounded device wait expired */
+#define ICM_ERR_STATE (-6)    /* call not valid in the current state */
+#define ICM_ERR_UNSUPPORTED (-7) /* size or feature beyond this build's limits */
+
+/* Lattice kinds ("Results in two and three space dimensions, as well as on
+ * the nonplanar chimera topology").
+ *   ICM_SQUARE2D : L x L periodic square lattice, site i = x + L y,
+ *                  bond b = 2i + d to the +x (d=0) / +y (d=1) neighbour.
+ *   ICM_CUBIC3D  : L^3 periodic cubic lattice, site i = x + L(y + L z),
+ *                  bond b = 3i + d to the +x / +y / +z neighbour.
+ *   ICM_CHIMERA  : C_M, M x M unit cells of K_{4,4}, open boundary,
+ *                  site i = 8(rM + c) + 4h + k (shore h, index k).  Bonds:
+ *                  in-cell b = 16 cell + 4 k0 + k1 joins (h=0,k0)-(h=1,k1);
+ *                  then (r,c,0,k)-(r+1,c,0,k) at b = 16M^2 + 4(rM+c) + k;
+ *                  then (r,c,1,k)-(r,c+1,1,k) at
+ *                  b = 16M^2 + 4M(M-1) + 4(r(M-1)+c) + k.
+ * Lattices need an even L >= 2 (the two-colouring); L = 2 keeps the doubled
+ * bonds of the torus as separate bonds.                                     */
+typedef enum { ICM_SQUARE2D = 0, ICM_CUBIC3D = 1, ICM_CHIMERA = 2 } icm_lattice;
+
+/* Disorder ("the interactions J_ij are selected from a Gaussian distribution
+ * with mean zero and variance J^2 = 1"; bimodal disorder in the discussion of
+ * degenerate ground states).
+ *   ICM_PM_J  : J = +-1, int8 per bond; integer arithmetic, results are
+ *               bit-exact functions of the inputs.
+ *   ICM_GAUSS : J real, float32 per bond; fp32 arithmetic.               */
+typedef enum { ICM_PM_J = 0, ICM_GAUSS = 1 } icm_disorder;
+
+#define ICM_DEVICE_PTR 1u     /* flags: the buffer is a device pointer */
+
+typedef struct icm_ctx icm_ctx;
+typedef struct icm_batch icm_batch;
+
+/* Which steps run at sweep t (each applies when t % every == 0; 0 = never). */
+typedef struct {
+    int32_t icm_every;        /* steps 2a/2b; default 1 */
+    int32_t swap_every;       /* step 3; default 1 */
+    int32_t enable_2a;        /* step 2a on/off; default 1 */
+    int32_t enable_metropolis;/* step 1 on/off (off only for tests); default 1 */
+    int64_t t_meas;           /* accumulate observables when t >= t_meas; default 0 */
+    int32_t trace;            /* record the last sweep's ICM/PT decisions; default 0 */
+    int32_t reserved;
+} icm_schedule;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * (NULL = the legacy default stream) on which all work is enqueued.       */
+icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream);
+icm_status icm_ctx_destroy(icm_ctx *ctx);
+/* Description of the last error on this context; owned by the context and
+ * valid until the next call on it.  Never NULL.                            */
+const char *icm_last_error(const icm_ctx *ctx);
+/* Wait for all work enqueued on the context's stream. */
+icm_status icm_sync(icm_ctx *ctx);
+
+/* Number of sites N and bonds N_b of a lattice (host only, no device work). */
+icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_t *n_bonds);
+
+/* ---------------------------------------------------------------- batches */
+
+/* Create a batch of n_inst disorder instances of one lattice and disorder
+ * kind that share one temperature ladder.
+ *   couplings : [n_inst][N_b] in bond order; int8 (+-1) for ICM_PM_J,
+ *               float32 for ICM_GAUSS.  Required.
+ *   spins     : [n_inst][2 n_T][N] int8 (+1/-1), replica r = 2k + c is copy
+ *               c at temperature position k.  NULL = all spins +1.
+ *   instance_ids : [n_inst] uint32 < 2^24, the instance's RNG key.
+ *               NULL = 0 .. n_inst-1.
+ *   T         : [n_T] temperatures, strictly ascending, > 0 (position k = 0
+ *               is the lowest temperature); 2 <= n_T <= 32.
+ *   T_icm     : steps 2a/2b run at every k with T_k <= T_icm.
+ *   seed      : 64-bit Philox key.
+ * The schedule starts at its defaults; the sweep counter of every instance
+ * starts at 0.  Errors: ICM_ERR_ARG (bad sizes or values),
+ * ICM_ERR_UNSUPPORTED (instance too large for one CTA's shared memory),
+ * ICM_ERR_OOM, ICM_ERR_CUDA.                                                */
+icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder,
+                            int32_t n_inst, const void *couplings, const int8_t *spins,
+                            const uint32_t *instance_ids, const double *T, int32_t n_T,
+                            double T_icm, uint64_t seed, uint32_t flags, icm_batch **out);
+icm_status icm_batch_destroy(icm_batch *b);
+
+/* Replace the couplings and/or spins of every instance (either may be NULL
+ * to keep it), reset sweep counters to `t0` and clear the observables.
+ * Layouts as in icm_batch_create.                                          */
+icm_status icm_batch_load(icm_batch *b, const void *couplings, const int8_t *spins,
+                          uint32_t t0, uint32_t flags);
+
+icm_status icm_set_schedule(icm_batch *b, const icm_schedule *s);
+icm_status icm_get_schedule(const icm_batch *b, icm_schedule *s);
+
+/* Enqueue n_sweeps simulation steps of every instance (one kernel launch).
+ * Asynchronous. */
+icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps);
+
+/* ---------------------------------------------------------------- reads
+ * Every read waits for the batch's outstanding work.                      */
+
+/* Spins [n_inst][2 n_T][N] int8 +-1, site order, replica r = 2k + c. */
+icm_status icm_read_spins(icm_batch *b, int8_t *out, uint32_t flags);
+/* Energies [n_inst][2 n_T] (double; exact integers for ICM_PM_J). */
+icm_status icm_read_energies(icm_batch *b, double *out, uint32_t flags);
+/* Sweep counters [n_inst]. */
+icm_status icm_read_sweeps(icm_batch *b, uint32_t *out, uint32_t flags);
+
+/* Accumulated observables since the last clear; per temperature k, over the
+ * measured sweeps (n_meas[inst] of them):
+ *   accE   [n_inst][n_T] double : sum of E_{2k} + E_{2k+1}
+ *   acc_n  [n_inst][n_T] int64  : sum of n = #{i : q_i = -1}
+ *   acc_q2 [n_inst][n_T] int64  : sum of (N - 2n)^2       (N^2 q^2)
+ *   acc_pmin [n_inst][n_T] int64: sum of min(n, N - n)     (N p, Fig. 1)
+ *   acc_d  [n_inst][n_T] int64  : sum of #{bonds with q_i q_j = -1}
+ *                                 (q_l = 1 - 2 d / N_b)
+ *   hist   [n_inst][n_T][N+1] int64 : histogram of n       (P(q))
+ *   n_meas [n_inst] int64
+ * Any output pointer may be NULL to skip it.                               */
+icm_status icm_read_observables(icm_batch *b, double *accE, int64_t *acc_n, int64_t *acc_q2,
+                                int64_t *acc_pmin, int64_t *acc_d, int64_t *hist,
+                                int64_t *n_meas, uint32_t flags);
+icm_status icm_clear_observables(icm_batch *b);
+
+/* Decisions of the last sweep of the last icm_run_sweeps (schedule.trace = 1):
+ *   n_pre [n_inst][n_T] int32 : n before step 2a (-1: no ICM at k)
+ *   flip2a [n_inst][n_T] int32: step 2a reversed copy 1
+ *   seed_site [n_inst][n_T] int32 : seed site (-1: none)
+ *   csize [n_inst][n_T] int32 : cluster size
+ *   esum_before / esum_after [n_inst][n_T] double : E_a + E_b around 2a/2b
+ *   swap_acc [n_inst][2][n_T - 1] uint8 : PT decisions per copy
+ * Any output pointer may be NULL.                                          */
+icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t *seed_site,
+                          int32_t *csize, double *esum_before, double *esum_after,
+                          uint8_t *swap_acc, uint32_t flags);
+
+/* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
+ * dynamic shared memory bytes per CTA and kernel launches issued so far. */
+icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,
+                          int32_t *grid, int32_t *smem_bytes, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ICMPT_H */

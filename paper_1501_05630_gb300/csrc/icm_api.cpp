@@ -1,0 +1,651 @@
+// icm_api.cpp -- host half of the C ABI declared in include/icmpt.h.
+//
+// Builds the lattice (bond order as documented in the header), the
+// colour-major site positions and neighbour tables, the integer acceptance
+// tables of the +-J path, allocates the batch's device state and launches
+// the kernels of pt_icm.cu on the context's stream.
+#include "icmpt.h"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "icm_internal.h"
+
+struct icm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int num_sms = 0;
+    int max_smem_optin = 0;
+    std::string err = "no error";
+};
+
+namespace {
+
+struct Geometry {
+    int N = 0, Nb = 0, Z = 0;
+    std::vector<int> bi, bj;        // bond endpoints, bond order
+    std::vector<uint8_t> color;     // [N]
+};
+
+int lattice_size(int lattice, int L, int *N, int *Nb)
+{
+    if (L < 1) return -1;
+    switch (lattice) {
+    case ICM_SQUARE2D: *N = L * L; *Nb = 2 * L * L; return 0;
+    case ICM_CUBIC3D: *N = L * L * L; *Nb = 3 * L * L * L; return 0;
+    case ICM_CHIMERA: *N = 8 * L * L; *Nb = 16 * L * L + 8 * L * (L - 1); return 0;
+    default: return -1;
+    }
+}
+
+// Bond list in the order documented for each lattice kind in icmpt.h.
+bool build_geometry(int lattice, int L, Geometry &g)
+{
+    if (lattice_size(lattice, L, &g.N, &g.Nb)) return false;
+    g.bi.resize(g.Nb);
+    g.bj.resize(g.Nb);
+    g.color.resize(g.N);
+    if (lattice == ICM_SQUARE2D) {
+        g.Z = 4;
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                const int i = x + L * y;
+                g.color[i] = (uint8_t)((x + y) & 1);
+                g.bi[2 * i] = i;
+                g.bj[2 * i] = ((x + 1) % L) + L * y;
+                g.bi[2 * i + 1] = i;
+                g.bj[2 * i + 1] = x + L * ((y + 1) % L);
+            }
+    } else if (lattice == ICM_CUBIC3D) {
+        g.Z = 6;
+        for (int z = 0; z < L; ++z)
+            for (int y = 0; y < L; ++y)
+                for (int x = 0; x < L; ++x) {
+                    const int i = x + L * (y + L * z);
+                    g.color[i] = (uint8_t)((x + y + z) & 1);
+                    const int nx = ((x + 1) % L) + L * (y + L * z);
+                    const int ny = x + L * (((y + 1) % L) + L * z);
+                    const int nz = x + L * (y + L * ((z + 1) % L));
+                    g.bi[3 * i] = i; g.bj[3 * i] = nx;
+                    g.bi[3 * i + 1] = i; g.bj[3 * i + 1] = ny;
+                    g.bi[3 * i + 2] = i; g.bj[3 * i + 2] = nz;
+                }
+    } else {
+        g.Z = 6;
+        const int M = L;
+        auto site = [M](int r, int c, int h, int k) { return 8 * (r * M + c) + 4 * h + k; };
+        for (int r = 0; r < M; ++r)
+            for (int c = 0; c < M; ++c)
+                for (int h = 0; h < 2; ++h)
+                    for (int k = 0; k < 4; ++k) g.color[site(r, c, h, k)] = (uint8_t)((r + c + h) & 1);
+        int b = 0;
+        for (int cell = 0; cell < M * M; ++cell)
+            for (int k0 = 0; k0 < 4; ++k0)
+                for (int k1 = 0; k1 < 4; ++k1, ++b) {
+                    g.bi[b] = 8 * cell + k0;
+                    g.bj[b] = 8 * cell + 4 + k1;
+                }
+        for (int r = 0; r + 1 < M; ++r)
+            for (int c = 0; c < M; ++c)
+                for (int k = 0; k < 4; ++k, ++b) {
+                    g.bi[b] = site(r, c, 0, k);
+                    g.bj[b] = site(r + 1, c, 0, k);
+                }
+        for (int r = 0; r < M; ++r)
+            for (int c = 0; c + 1 < M; ++c)
+                for (int k = 0; k < 4; ++k, ++b) {
+                    g.bi[b] = site(r, c, 1, k);
+                    g.bj[b] = site(r, c + 1, 1, k);
+                }
+        if (b != g.Nb) return false;
+    }
+    return true;
+}
+
+// floor(exp(a) * 2^32), saturated at 2^32 - 1 (a <= 0).
+uint32_t acceptance_threshold(double a)
+{
+    const double v = std::floor(std::exp(a) * 4294967296.0);
+    if (v >= 4294967295.0) return 4294967295u;
+    if (v <= 0.0) return 0u;
+    return (uint32_t)v;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+};
+
+}  // namespace
+
+struct icm_batch {
+    icm_ctx *ctx = nullptr;
+    int lattice = 0, L = 0, disorder = 0, n_inst = 0, nT = 0;
+    bool gauss = false;
+    double T_icm = 0.0;
+    uint64_t seed = 0;
+    Geometry geo;
+    std::vector<double> T;
+    icm_schedule sched{};
+    icm::KParams kp{};
+    int threads = 0, grid = 0, ctas_per_sm = 0;
+    int64_t launches = 0;
+    std::vector<void *> allocs;
+    // staging buffers for loads and reads
+    void *raw_coup = nullptr;     // [n_inst][Nb] int8 or float
+    int8_t *raw_spins = nullptr;  // [n_inst][R][N]
+    double *raw_E = nullptr;      // [n_inst][R]
+    int32_t *edge_bond = nullptr; // [N][Z]
+};
+
+namespace {
+
+icm_status fail(icm_ctx *ctx, icm_status code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+    return code;
+}
+
+icm_status cuda_fail(icm_ctx *ctx, cudaError_t e, const char *what)
+{
+    return fail(ctx, ICM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ICM_CUDA(ctx, call)                                   \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+    } while (0)
+
+template <typename T>
+icm_status dalloc(icm_batch *b, T **p, size_t count)
+{
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(b->ctx, ICM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->allocs.push_back(q);
+    *p = (T *)q;
+    return ICM_OK;
+}
+
+icm_status copy_in(icm_ctx *ctx, void *dst, const void *src, size_t bytes, uint32_t flags)
+{
+    const cudaMemcpyKind kind = (flags & ICM_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ICM_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream));
+    return ICM_OK;
+}
+
+icm_status copy_out(icm_ctx *ctx, void *dst, const void *src, size_t bytes, uint32_t flags)
+{
+    const cudaMemcpyKind kind = (flags & ICM_DEVICE_PTR) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    ICM_CUDA(ctx, cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream));
+    return ICM_OK;
+}
+
+icm_status upload_state(icm_batch *b, const void *couplings, const int8_t *spins, uint32_t flags)
+{
+    icm_ctx *ctx = b->ctx;
+    icm::KParams &P = b->kp;
+    if (couplings) {
+        const size_t bytes = (size_t)b->n_inst * P.Nb * (b->gauss ? 4 : 1);
+        icm_status st = copy_in(ctx, b->raw_coup, couplings, bytes, flags);
+        if (st) return st;
+        ICM_CUDA(ctx, icm::launch_expand_couplings(b->raw_coup, b->gauss, b->edge_bond, b->n_inst, P.N, P.Z, P.Nb,
+                                                   const_cast<float *>(P.Jd), const_cast<uint8_t *>(P.Jb),
+                                                   ctx->stream));
+    }
+    if (spins) {
+        const size_t bytes = (size_t)b->n_inst * P.R * P.N;
+        icm_status st = copy_in(ctx, b->raw_spins, spins, bytes, flags);
+        if (st) return st;
+        ICM_CUDA(ctx, icm::launch_pack_spins(b->raw_spins, P.spins, P.pos2site, b->n_inst, P.R, P.G, P.N,
+                                             ctx->stream));
+    }
+    ICM_CUDA(ctx, icm::launch_init_energies(P, b->gauss, ctx->stream));
+    return ICM_OK;
+}
+
+icm_status clear_observables(icm_batch *b)
+{
+    icm_ctx *ctx = b->ctx;
+    icm::KParams &P = b->kp;
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    ICM_CUDA(ctx, cudaMemsetAsync(P.accE, 0, nk * sizeof(double), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.acc64, 0, 4 * nk * sizeof(long long), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.hist, 0, nk * (P.N + 1) * sizeof(unsigned long long), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.n_meas, 0, (size_t)b->n_inst * sizeof(long long), ctx->stream));
+    return ICM_OK;
+}
+
+void destroy_batch(icm_batch *b)
+{
+    if (!b) return;
+    if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
+    for (void *p : b->allocs) cudaFree(p);
+    delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream)
+{
+    if (!out) return ICM_ERR_ARG;
+    *out = nullptr;
+    icm_ctx *ctx = new (std::nothrow) icm_ctx();
+    if (!ctx) return ICM_ERR_OOM;
+    ctx->device = device;
+    ctx->stream = (cudaStream_t)cuda_stream;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return ICM_ERR_CUDA;
+    }
+    *out = ctx;
+    return ICM_OK;
+}
+
+icm_status icm_ctx_destroy(icm_ctx *ctx)
+{
+    if (!ctx) return ICM_ERR_ARG;
+    delete ctx;
+    return ICM_OK;
+}
+
+const char *icm_last_error(const icm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+icm_status icm_sync(icm_ctx *ctx)
+{
+    if (!ctx) return ICM_ERR_ARG;
+    ICM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_t *n_bonds)
+{
+    int N, Nb;
+    if (!n_sites || !n_bonds || lattice_size(lattice, L, &N, &Nb)) return ICM_ERR_ARG;
+    *n_sites = N;
+    *n_bonds = Nb;
+    return ICM_OK;
+}
+
+icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
+                            const void *couplings, const int8_t *spins, const uint32_t *instance_ids,
+                            const double *T, int32_t n_T, double T_icm, uint64_t seed, uint32_t flags,
+                            icm_batch **out)
+{
+    if (!ctx) return ICM_ERR_ARG;
+    if (!out) return fail(ctx, ICM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (lattice < 0 || lattice > 2) return fail(ctx, ICM_ERR_ARG, "unknown lattice kind");
+    if (disorder != ICM_PM_J && disorder != ICM_GAUSS) return fail(ctx, ICM_ERR_ARG, "unknown disorder kind");
+    if (lattice != ICM_CHIMERA && (L < 2 || (L & 1))) return fail(ctx, ICM_ERR_ARG, "lattices need an even L >= 2");
+    if (lattice == ICM_CHIMERA && L < 1) return fail(ctx, ICM_ERR_ARG, "chimera needs M >= 1");
+    if (n_inst < 1) return fail(ctx, ICM_ERR_ARG, "n_inst must be >= 1");
+    if (!couplings) return fail(ctx, ICM_ERR_ARG, "couplings are required");
+    if (!T || n_T < 2 || n_T > 32) return fail(ctx, ICM_ERR_ARG, "need 2 <= n_T <= 32 temperatures");
+    for (int k = 0; k < n_T; ++k) {
+        if (!(T[k] > 0.0) || !std::isfinite(T[k])) return fail(ctx, ICM_ERR_ARG, "temperatures must be finite and > 0");
+        if (k && !(T[k] > T[k - 1])) return fail(ctx, ICM_ERR_ARG, "temperatures must be strictly ascending");
+    }
+    icm_batch *b = new (std::nothrow) icm_batch();
+    if (!b) return fail(ctx, ICM_ERR_OOM, "host allocation failed");
+    b->ctx = ctx;
+    b->lattice = lattice;
+    b->L = L;
+    b->disorder = disorder;
+    b->gauss = (disorder == ICM_GAUSS);
+    b->n_inst = n_inst;
+    b->nT = n_T;
+    b->T_icm = T_icm;
+    b->seed = seed;
+    b->T.assign(T, T + n_T);
+    b->sched = icm_schedule{1, 1, 1, 1, 0, 0, 0};
+    if (!build_geometry(lattice, L, b->geo)) {
+        destroy_batch(b);
+        return fail(ctx, ICM_ERR_ARG, "geometry construction failed");
+    }
+    Geometry &g = b->geo;
+    const int N = g.N, Z = g.Z, R = 2 * n_T, G = (R + 31) / 32;
+    if (N > 65535) {
+        destroy_batch(b);
+        return fail(ctx, ICM_ERR_UNSUPPORTED, "more than 65535 sites");
+    }
+    // colour-major positions, ascending site index inside a colour
+    std::vector<int> pos(N);
+    std::vector<uint16_t> pos2site(N);
+    int cnt[2] = {0, 0};
+    for (int i = 0; i < N; ++i) cnt[g.color[i]]++;
+    if (cnt[0] != N / 2 || cnt[1] != N / 2) {
+        destroy_batch(b);
+        return fail(ctx, ICM_ERR_ARG, "colour classes are not balanced");
+    }
+    int next[2] = {0, N / 2};
+    for (int i = 0; i < N; ++i) {
+        pos[i] = next[g.color[i]]++;
+        pos2site[pos[i]] = (uint16_t)i;
+    }
+    // incident bonds of every site in bond order, padded to Z with (self, -1)
+    std::vector<std::vector<std::pair<int, int>>> inc(N);
+    for (int e = 0; e < g.Nb; ++e) {
+        if (g.color[g.bi[e]] == g.color[g.bj[e]]) {
+            destroy_batch(b);
+            return fail(ctx, ICM_ERR_ARG, "bond inside a colour class");
+        }
+        inc[g.bi[e]].push_back({g.bj[e], e});
+        inc[g.bj[e]].push_back({g.bi[e], e});
+    }
+    std::vector<uint16_t> nbr((size_t)N * Z);
+    std::vector<int32_t> edge_bond((size_t)N * Z);
+    std::vector<uint8_t> zdeg(N);
+    bool uniform = true;
+    for (int i = 0; i < N; ++i) {
+        const int deg = (int)inc[i].size();
+        if (deg < 4 || deg > Z) {
+            destroy_batch(b);
+            return fail(ctx, ICM_ERR_UNSUPPORTED, "site degree outside 4..6");
+        }
+        if (deg != Z) uniform = false;
+        const int p = pos[i];
+        zdeg[p] = (uint8_t)deg;
+        for (int d = 0; d < Z; ++d) {
+            if (d < deg) {
+                nbr[(size_t)p * Z + d] = (uint16_t)pos[inc[i][d].first];
+                edge_bond[(size_t)p * Z + d] = inc[i][d].second;
+            } else {
+                nbr[(size_t)p * Z + d] = (uint16_t)p;
+                edge_bond[(size_t)p * Z + d] = -1;
+            }
+        }
+    }
+    // launch shape and shared memory
+    const int threads = icm::fused_threads(N);
+    const int nwarps = threads / 32;
+    const icm::SmemLayout sm = icm::smem_layout(N, Z, R, G, n_T, nwarps, b->gauss);
+    if (sm.total > ctx->max_smem_optin) {
+        destroy_batch(b);
+        return fail(ctx, ICM_ERR_UNSUPPORTED, "instance needs " + std::to_string(sm.total) +
+                                                  " bytes of shared memory, more than one CTA can hold");
+    }
+    const int half = N / 2;
+    if (((half + threads - 1) / threads) * Z >= 256 || (N + threads - 1) / threads >= 256) {
+        destroy_batch(b);
+        return fail(ctx, ICM_ERR_UNSUPPORTED, "too many sites per thread for the observable counters");
+    }
+    int ctas = 0;
+    cudaError_t ce = icm::fused_occupancy(b->gauss, Z, threads, sm.total, &ctas);
+    if (ce != cudaSuccess || ctas < 1) {
+        destroy_batch(b);
+        return ce != cudaSuccess ? cuda_fail(ctx, ce, "occupancy") : fail(ctx, ICM_ERR_UNSUPPORTED, "kernel does not fit");
+    }
+    b->threads = threads;
+    b->ctas_per_sm = ctas;
+    const int slots = ctx->num_sms * ctas;
+    b->grid = n_inst < slots ? n_inst : slots;
+
+    // temperature tables
+    std::vector<double> beta(n_T);
+    for (int k = 0; k < n_T; ++k) beta[k] = 1.0 / T[k];
+    std::vector<uint32_t> thr_metro((size_t)R * 8, 0u);
+    std::vector<float> b2l(R);
+    for (int r = 0; r < R; ++r) {
+        const double bk = beta[r / 2];
+        for (int m = 1; m <= 6; ++m) thr_metro[(size_t)r * 8 + m] = acceptance_threshold((double)(-2 * m) * bk);
+        b2l[r] = (float)(-2.0 * bk * 1.4426950408889634);
+    }
+    std::vector<uint32_t> thr_swap;
+    std::vector<int32_t> swap_off(n_T - 1), swap_len(n_T - 1);
+    for (int k = 0; k + 1 < n_T; ++k) {
+        const double db = beta[k] - beta[k + 1];
+        swap_off[k] = (int32_t)thr_swap.size();
+        int len = 0;
+        for (int d = 1; d <= g.Nb; ++d) {
+            const uint32_t v = acceptance_threshold((double)(-2 * d) * db);
+            if (v == 0u) break;
+            thr_swap.push_back(v);
+            ++len;
+        }
+        swap_len[k] = len;
+    }
+    if (thr_swap.empty()) thr_swap.push_back(0u);
+    int n_icm = 0;
+    while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
+
+    icm::KParams &P = b->kp;
+    P.N = N; P.Nb = g.Nb; P.nT = n_T; P.R = R; P.G = G; P.Z = Z; P.n_inst = n_inst; P.n_icm = n_icm;
+    P.half = half; P.NW = (N + 31) / 32; P.const_z = uniform ? Z : 0;
+    P.seed_lo = (uint32_t)(seed & 0xffffffffu);
+    P.seed_hi = (uint32_t)(seed >> 32);
+    P.sm = sm;
+
+    icm_status st = ICM_OK;
+    uint16_t *d_nbr, *d_pos2site;
+    uint8_t *d_zdeg, *d_Jb;
+    float *d_Jd, *d_Ef, *d_b2l, *d_treb, *d_trea;
+    int32_t *d_Ei, *d_off, *d_len, *d_trn, *d_trf, *d_trs, *d_trc;
+    uint32_t *d_spins, *d_t, *d_id, *d_thr, *d_thrs;
+    double *d_beta, *d_accE;
+    long long *d_acc64, *d_nmeas;
+    unsigned long long *d_hist;
+    uint8_t *d_trsw;
+    const size_t nk = (size_t)n_inst * n_T;
+    if ((st = dalloc(b, &d_nbr, (size_t)N * Z)) || (st = dalloc(b, &d_pos2site, N)) || (st = dalloc(b, &d_zdeg, N)) ||
+        (st = dalloc(b, &b->edge_bond, (size_t)N * Z)) ||
+        (st = dalloc(b, &d_Jb, b->gauss ? 1 : (size_t)n_inst * N)) ||
+        (st = dalloc(b, &d_Jd, b->gauss ? (size_t)n_inst * N * Z : 1)) ||
+        (st = dalloc(b, &d_spins, (size_t)n_inst * G * N)) || (st = dalloc(b, &d_Ef, (size_t)n_inst * R)) ||
+        (st = dalloc(b, &d_Ei, (size_t)n_inst * R)) || (st = dalloc(b, &d_t, n_inst)) ||
+        (st = dalloc(b, &d_id, n_inst)) || (st = dalloc(b, &d_thr, (size_t)R * 8)) || (st = dalloc(b, &d_b2l, R)) ||
+        (st = dalloc(b, &d_beta, n_T)) || (st = dalloc(b, &d_thrs, thr_swap.size())) ||
+        (st = dalloc(b, &d_off, n_T - 1)) || (st = dalloc(b, &d_len, n_T - 1)) || (st = dalloc(b, &d_accE, nk)) ||
+        (st = dalloc(b, &d_acc64, 4 * nk)) || (st = dalloc(b, &d_hist, nk * (N + 1))) ||
+        (st = dalloc(b, &d_nmeas, n_inst)) || (st = dalloc(b, &d_trn, nk)) || (st = dalloc(b, &d_trf, nk)) ||
+        (st = dalloc(b, &d_trs, nk)) || (st = dalloc(b, &d_trc, nk)) || (st = dalloc(b, &d_treb, nk)) ||
+        (st = dalloc(b, &d_trea, nk)) || (st = dalloc(b, &d_trsw, (size_t)n_inst * 2 * (n_T - 1))) ||
+        (st = dalloc(b, (uint8_t **)&b->raw_coup, (size_t)n_inst * g.Nb * (b->gauss ? 4 : 1))) ||
+        (st = dalloc(b, &b->raw_spins, (size_t)n_inst * R * N)) || (st = dalloc(b, &b->raw_E, (size_t)n_inst * R))) {
+        destroy_batch(b);
+        return st;
+    }
+    P.nbr = d_nbr; P.pos2site = d_pos2site; P.zdeg = d_zdeg; P.Jb = d_Jb; P.Jd = d_Jd; P.spins = d_spins;
+    P.Ef = d_Ef; P.Ei = d_Ei; P.tsweep = d_t; P.inst_id = d_id; P.thr_metro = d_thr; P.b2l = d_b2l;
+    P.beta = d_beta; P.thr_swap = d_thrs; P.swap_off = d_off; P.swap_len = d_len; P.accE = d_accE;
+    P.acc64 = d_acc64; P.hist = d_hist; P.n_meas = d_nmeas; P.tr_n_pre = d_trn; P.tr_flip2a = d_trf;
+    P.tr_seed = d_trs; P.tr_csize = d_trc; P.tr_eb = d_treb; P.tr_ea = d_trea; P.tr_swap = d_trsw;
+
+    std::vector<uint32_t> ids(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        ids[i] = instance_ids ? instance_ids[i] : (uint32_t)i;
+        if (ids[i] >= (1u << 24)) {
+            destroy_batch(b);
+            return fail(ctx, ICM_ERR_ARG, "instance ids must be < 2^24");
+        }
+    }
+    cudaStream_t s = ctx->stream;
+#define UP(dst, vec) cudaMemcpyAsync(dst, (vec).data(), (vec).size() * sizeof((vec)[0]), cudaMemcpyHostToDevice, s)
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = UP(d_nbr, nbr);
+    if (e == cudaSuccess) e = UP(d_pos2site, pos2site);
+    if (e == cudaSuccess) e = UP(d_zdeg, zdeg);
+    if (e == cudaSuccess) e = UP(b->edge_bond, edge_bond);
+    if (e == cudaSuccess) e = UP(d_id, ids);
+    if (e == cudaSuccess) e = UP(d_thr, thr_metro);
+    if (e == cudaSuccess) e = UP(d_b2l, b2l);
+    if (e == cudaSuccess) e = UP(d_beta, beta);
+    if (e == cudaSuccess) e = UP(d_thrs, thr_swap);
+    if (e == cudaSuccess) e = UP(d_off, swap_off);
+    if (e == cudaSuccess) e = UP(d_len, swap_len);
+#undef UP
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_spins, 0, (size_t)n_inst * G * N * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_t, 0, (size_t)n_inst * 4, s);
+    if (e != cudaSuccess) {
+        destroy_batch(b);
+        return cuda_fail(ctx, e, "batch upload");
+    }
+    if ((st = clear_observables(b)) || (st = upload_state(b, couplings, spins, flags))) {
+        destroy_batch(b);
+        return st;
+    }
+    e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        destroy_batch(b);
+        return cuda_fail(ctx, e, "batch creation");
+    }
+    *out = b;
+    return ICM_OK;
+}
+
+icm_status icm_batch_destroy(icm_batch *b)
+{
+    if (!b) return ICM_ERR_ARG;
+    destroy_batch(b);
+    return ICM_OK;
+}
+
+icm_status icm_batch_load(icm_batch *b, const void *couplings, const int8_t *spins, uint32_t t0, uint32_t flags)
+{
+    if (!b) return ICM_ERR_ARG;
+    icm_status st;
+    if ((st = upload_state(b, couplings, spins, flags))) return st;
+    std::vector<uint32_t> t(b->n_inst, t0);
+    ICM_CUDA(b->ctx, cudaMemcpyAsync(b->kp.tsweep, t.data(), t.size() * 4, cudaMemcpyHostToDevice, b->ctx->stream));
+    if ((st = clear_observables(b))) return st;
+    // the host vector above must outlive the copy
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_set_schedule(icm_batch *b, const icm_schedule *s)
+{
+    if (!b || !s) return ICM_ERR_ARG;
+    if (s->icm_every < 0 || s->swap_every < 0) return fail(b->ctx, ICM_ERR_ARG, "negative schedule period");
+    b->sched = *s;
+    return ICM_OK;
+}
+
+icm_status icm_get_schedule(const icm_batch *b, icm_schedule *s)
+{
+    if (!b || !s) return ICM_ERR_ARG;
+    *s = b->sched;
+    return ICM_OK;
+}
+
+icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (n_sweeps == 0) return ICM_OK;
+    icm::KParams &P = b->kp;
+    P.icm_every = b->sched.icm_every;
+    P.swap_every = b->sched.swap_every;
+    P.enable_2a = b->sched.enable_2a;
+    P.enable_metropolis = b->sched.enable_metropolis;
+    P.trace = b->sched.trace;
+    P.t_meas = b->sched.t_meas;
+    ICM_CUDA(b->ctx, icm::launch_fused(P, b->gauss, b->threads, b->grid, n_sweeps, b->ctx->stream));
+    b->launches += 1;
+    return ICM_OK;
+}
+
+icm_status icm_read_spins(icm_batch *b, int8_t *out, uint32_t flags)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    ICM_CUDA(b->ctx, icm::launch_unpack_spins(P.spins, b->raw_spins, P.pos2site, b->n_inst, P.R, P.G, P.N,
+                                              b->ctx->stream));
+    icm_status st = copy_out(b->ctx, out, b->raw_spins, (size_t)b->n_inst * P.R * P.N, flags);
+    if (st) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_read_energies(icm_batch *b, double *out, uint32_t flags)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    ICM_CUDA(b->ctx, icm::launch_energies_to_double(P, b->gauss, b->raw_E, b->ctx->stream));
+    icm_status st = copy_out(b->ctx, out, b->raw_E, (size_t)b->n_inst * P.R * sizeof(double), flags);
+    if (st) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_read_sweeps(icm_batch *b, uint32_t *out, uint32_t flags)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    icm_status st = copy_out(b->ctx, out, b->kp.tsweep, (size_t)b->n_inst * 4, flags);
+    if (st) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_read_observables(icm_batch *b, double *accE, int64_t *acc_n, int64_t *acc_q2, int64_t *acc_pmin,
+                                int64_t *acc_d, int64_t *hist, int64_t *n_meas, uint32_t flags)
+{
+    if (!b) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    icm_status st = ICM_OK;
+    int64_t *outs[4] = {acc_n, acc_q2, acc_pmin, acc_d};
+    if (accE && (st = copy_out(b->ctx, accE, P.accE, nk * 8, flags))) return st;
+    for (int a = 0; a < 4; ++a)
+        if (outs[a] && (st = copy_out(b->ctx, outs[a], P.acc64 + a * nk, nk * 8, flags))) return st;
+    if (hist && (st = copy_out(b->ctx, hist, P.hist, nk * (P.N + 1) * 8, flags))) return st;
+    if (n_meas && (st = copy_out(b->ctx, n_meas, P.n_meas, (size_t)b->n_inst * 8, flags))) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_clear_observables(icm_batch *b)
+{
+    if (!b) return ICM_ERR_ARG;
+    return clear_observables(b);
+}
+
+icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t *seed_site, int32_t *csize,
+                          double *esum_before, double *esum_after, uint8_t *swap_acc, uint32_t flags)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (flags & ICM_DEVICE_PTR) return fail(b->ctx, ICM_ERR_ARG, "icm_read_trace takes host buffers");
+    icm::KParams &P = b->kp;
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    std::vector<float> eb(nk), ea(nk);
+    icm_status st = ICM_OK;
+    if (n_pre && (st = copy_out(b->ctx, n_pre, P.tr_n_pre, nk * 4, 0))) return st;
+    if (flip2a && (st = copy_out(b->ctx, flip2a, P.tr_flip2a, nk * 4, 0))) return st;
+    if (seed_site && (st = copy_out(b->ctx, seed_site, P.tr_seed, nk * 4, 0))) return st;
+    if (csize && (st = copy_out(b->ctx, csize, P.tr_csize, nk * 4, 0))) return st;
+    if ((st = copy_out(b->ctx, eb.data(), P.tr_eb, nk * 4, 0))) return st;
+    if ((st = copy_out(b->ctx, ea.data(), P.tr_ea, nk * 4, 0))) return st;
+    if (swap_acc && (st = copy_out(b->ctx, swap_acc, P.tr_swap, (size_t)b->n_inst * 2 * (P.nT - 1), 0))) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    for (size_t i = 0; i < nk; ++i) {
+        if (esum_before) esum_before[i] = eb[i];
+        if (esum_after) esum_after[i] = ea[i];
+    }
+    return ICM_OK;
+}
+
+icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *grid,
+                          int32_t *smem_bytes, int64_t *launches)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (threads) *threads = b->threads;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    if (grid) *grid = b->grid;
+    if (smem_bytes) *smem_bytes = b->kp.sm.total;
+    if (launches) *launches = b->launches;
+    return ICM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,94 @@
+// Internal declarations shared by the host half (icm_api.cpp) and the device
+// half (pt_icm.cu) of the library.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace icm {
+
+constexpr int kMaxZ = 6;          // largest degree of the supported graphs
+constexpr int kMaxR = 64;         // replicas per instance (2 N_T, N_T <= 32)
+constexpr int kMaxThreads = 128;  // threads per CTA of the fused kernel
+constexpr int kPlanes = 8;        // bit-planes of the vertical counters (counts < 256 per thread)
+
+// Byte offsets into the fused kernel's dynamic shared memory.
+struct SmemLayout {
+    int spins;      // uint32 [G][N]
+    int nbr;        // uint16 [N][Z]   neighbour positions, padding = self
+    int zdeg;       // uint8  [N]      degree (+-J only)
+    int pos2site;   // uint16 [N]
+    int coup;       // float [N][Z] (Gaussian) or uint8 [N] bit d = (J < 0) (+-J)
+    int E;          // float or int32 [R]
+    int Epart;      // float or int32 [nwarps][R]
+    int rtab;       // uint32 [R][8] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
+    int icm_mask;   // uint32 [nwarps][NW]
+    int icm_C;      // uint32 [nwarps][NW]
+    int icm_queue;  // uint16 [nwarps][N]
+    int icm_tail;   // int32 [nwarps]
+    int swap_x;     // uint32 [2][32]
+    int swap_list;  // int32 [2][32]
+    int swap_n;     // int32 [2]
+    int cnt_n;      // int32 [32]
+    int cnt_d;      // int32 [32]
+    int accE;       // double [nT]
+    int acc64;      // int64 [4][nT]  n, q2, pmin, d
+    int nmeas;      // int64 [1]
+    int total;
+};
+
+// Everything the fused kernel reads or writes.  Device pointers.
+struct KParams {
+    int N, Nb, nT, R, G, Z, n_inst, n_icm, half, NW;
+    int const_z;                  // degree when uniform (lattices), 0 = per-site table
+    // geometry, shared by all instances of the batch
+    const uint16_t *nbr;          // [N][Z]
+    const uint8_t *zdeg;          // [N]
+    const uint16_t *pos2site;     // [N]
+    // per instance
+    const float *Jd;              // [n_inst][N][Z]  (Gaussian)
+    const uint8_t *Jb;            // [n_inst][N]     (+-J)
+    uint32_t *spins;              // [n_inst][G][N]
+    float *Ef;                    // [n_inst][R]     (Gaussian)
+    int32_t *Ei;                  // [n_inst][R]     (+-J)
+    uint32_t *tsweep;             // [n_inst]
+    const uint32_t *inst_id;      // [n_inst]
+    // temperature tables
+    const uint32_t *thr_metro;    // [R][8]
+    const float *b2l;             // [R]
+    const double *beta;           // [nT]
+    const uint32_t *thr_swap;     // concatenated per pair k
+    const int32_t *swap_off;      // [nT-1]
+    const int32_t *swap_len;      // [nT-1]
+    // schedule
+    int icm_every, swap_every, enable_2a, enable_metropolis, trace;
+    long long t_meas;
+    uint32_t seed_lo, seed_hi;
+    // observables
+    double *accE;                 // [n_inst][nT]
+    long long *acc64;             // [4][n_inst][nT]: n, (N-2n)^2, min(n,N-n), d
+    unsigned long long *hist;     // [n_inst][nT][N+1]
+    long long *n_meas;            // [n_inst]
+    // trace of the last sweep
+    int32_t *tr_n_pre, *tr_flip2a, *tr_seed, *tr_csize;  // [n_inst][nT]
+    float *tr_eb, *tr_ea;                                // [n_inst][nT]
+    uint8_t *tr_swap;                                    // [n_inst][2][nT-1]
+    SmemLayout sm;
+};
+
+SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int nwarps, bool gauss);
+int fused_threads(int N);
+
+// Host-callable launchers (pt_icm.cu).  Return a cudaError_t.
+cudaError_t fused_occupancy(bool gauss, int Z, int threads, int smem, int *ctas_per_sm);
+cudaError_t launch_fused(const KParams &P, bool gauss, int threads, int grid, uint32_t n_sweeps,
+                         cudaStream_t st);
+cudaError_t launch_pack_spins(const int8_t *src, uint32_t *dst, const uint16_t *pos2site, int n_inst,
+                              int R, int G, int N, cudaStream_t st);
+cudaError_t launch_unpack_spins(const uint32_t *src, int8_t *dst, const uint16_t *pos2site, int n_inst,
+                                int R, int G, int N, cudaStream_t st);
+cudaError_t launch_expand_couplings(const void *bond_J, bool gauss, const int32_t *edge_bond, int n_inst,
+                                    int N, int Z, int Nb, float *Jd, uint8_t *Jb, cudaStream_t st);
+cudaError_t launch_init_energies(const KParams &P, bool gauss, cudaStream_t st);
+cudaError_t launch_energies_to_double(const KParams &P, bool gauss, double *out, cudaStream_t st);
+
+}  // namespace icm

@@ -1,0 +1,258 @@
+"""Thin Python binding of libicmpt.so (argument marshalling only).
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+only converts numpy arrays / CUDA torch tensors into pointers and sizes.  If
+the library has not been built, importing works but creating a Context raises
+``RuntimeError``: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+from .inputs import CHIMERA, CUBIC3D, GAUSS, PM_J, SQUARE2D  # noqa: F401  (re-exported constants)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libicmpt.so")
+DEVICE_PTR = 1
+
+_lock = threading.Lock()
+_lib = None
+
+_ERRORS = {-1: "ICM_ERR_ARG", -2: "ICM_ERR_OOM", -3: "ICM_ERR_BUDGET", -4: "ICM_ERR_CUDA",
+           -5: "ICM_ERR_TIMEOUT", -6: "ICM_ERR_STATE", -7: "ICM_ERR_UNSUPPORTED"}
+
+
+class IcmError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Schedule(ctypes.Structure):
+    _fields_ = [("icm_every", ctypes.c_int32), ("swap_every", ctypes.c_int32), ("enable_2a", ctypes.c_int32),
+                ("enable_metropolis", ctypes.c_int32), ("t_meas", ctypes.c_int64), ("trace", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+EXPORTS = [
+    "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_lattice_size", "icm_batch_create",
+    "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
+    "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
+    "icm_read_trace", "icm_batch_info",
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libicmpt.so; raises RuntimeError when it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libicmpt.so not built ({path}); run paper_1501_05630_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, u32, u64, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
+        L.icm_ctx_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+        L.icm_ctx_destroy.argtypes = [vp]
+        L.icm_last_error.argtypes = [vp]
+        L.icm_last_error.restype = ctypes.c_char_p
+        L.icm_sync.argtypes = [vp]
+        L.icm_lattice_size.argtypes = [i32, i32, vp, vp]
+        L.icm_batch_create.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, vp, i32, ctypes.c_double, u64, u32,
+                                       ctypes.POINTER(vp)]
+        L.icm_batch_destroy.argtypes = [vp]
+        L.icm_batch_load.argtypes = [vp, vp, vp, u32, u32]
+        L.icm_set_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+        L.icm_get_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
+        L.icm_run_sweeps.argtypes = [vp, u32]
+        L.icm_read_spins.argtypes = [vp, vp, u32]
+        L.icm_read_energies.argtypes = [vp, vp, u32]
+        L.icm_read_sweeps.argtypes = [vp, vp, u32]
+        L.icm_read_observables.argtypes = [vp] + [vp] * 7 + [u32]
+        L.icm_clear_observables.argtypes = [vp]
+        L.icm_read_trace.argtypes = [vp] + [vp] * 7 + [u32]
+        L.icm_batch_info.argtypes = [vp] + [vp] * 5
+        for name in EXPORTS:
+            if name != "icm_last_error":
+                getattr(L, name).restype = i32
+        _ = i64
+        _lib = L
+        return L
+
+
+def lattice_size(lattice: int, L: int):
+    lib = load_library()
+    n, nb = ctypes.c_int32(), ctypes.c_int32()
+    rc = lib.icm_lattice_size(lattice, L, ctypes.byref(n), ctypes.byref(nb))
+    if rc:
+        raise IcmError(rc, "bad lattice")
+    return n.value, nb.value
+
+
+def _ptr(a):
+    """(pointer, flags) of a numpy array or a CUDA torch tensor."""
+    if a is None:
+        return None, 0
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr(), (DEVICE_PTR if a.is_cuda else 0)
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+class Context:
+    """A device and a stream (a cudaStream_t handle as int, or None)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load_library()
+        h = ctypes.c_void_p()
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        rc = self._lib.icm_ctx_create(ctypes.byref(h), int(device), st)
+        if rc:
+            raise IcmError(rc, "icm_ctx_create failed (no CUDA device?)")
+        self._h = h
+
+    def check(self, rc: int):
+        if rc:
+            raise IcmError(rc, self._lib.icm_last_error(self._h).decode())
+
+    def sync(self):
+        self.check(self._lib.icm_sync(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.icm_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class Observables:
+    accE: np.ndarray
+    acc_n: np.ndarray
+    acc_q2: np.ndarray
+    acc_pmin: np.ndarray
+    acc_d: np.ndarray
+    hist: np.ndarray
+    n_meas: np.ndarray
+
+
+class Batch:
+    """n_inst disorder instances sharing one lattice, disorder kind and ladder."""
+
+    def __init__(self, ctx: Context, lattice: int, L: int, disorder: int, couplings, T, T_icm: float,
+                 seed: int, spins=None, instance_ids=None):
+        self.ctx = ctx
+        self._lib = ctx._lib
+        self.lattice, self.L, self.disorder = int(lattice), int(L), int(disorder)
+        self.N, self.Nb = lattice_size(lattice, L)
+        self.T = np.ascontiguousarray(T, dtype=np.float64)
+        self.nT = len(self.T)
+        self.R = 2 * self.nT
+        n_inst = couplings.shape[0]
+        self.n_inst = int(n_inst)
+        cp, cflags = _ptr(couplings)
+        sp, sflags = _ptr(spins)
+        if spins is not None and cflags != sflags:
+            raise ValueError("couplings and spins must both be host or both be device buffers")
+        ids = None if instance_ids is None else np.ascontiguousarray(instance_ids, dtype=np.uint32)
+        h = ctypes.c_void_p()
+        ctx.check(self._lib.icm_batch_create(
+            ctx._h, self.lattice, self.L, self.disorder, self.n_inst, cp, sp,
+            None if ids is None else ids.ctypes.data, self.T.ctypes.data, self.nT, float(T_icm),
+            int(seed) & 0xFFFFFFFFFFFFFFFF, cflags, ctypes.byref(h)))
+        self._h = h
+
+    # -- control
+    def schedule(self) -> Schedule:
+        s = Schedule()
+        self.ctx.check(self._lib.icm_get_schedule(self._h, ctypes.byref(s)))
+        return s
+
+    def set_schedule(self, **kw):
+        s = self.schedule()
+        for k, v in kw.items():
+            setattr(s, k, int(v))
+        self.ctx.check(self._lib.icm_set_schedule(self._h, ctypes.byref(s)))
+
+    def run(self, n_sweeps: int):
+        self.ctx.check(self._lib.icm_run_sweeps(self._h, int(n_sweeps)))
+
+    def load(self, couplings=None, spins=None, t0: int = 0):
+        cp, cf = _ptr(couplings)
+        sp, sf = _ptr(spins)
+        self.ctx.check(self._lib.icm_batch_load(self._h, cp, sp, int(t0), cf | sf))
+
+    def clear_observables(self):
+        self.ctx.check(self._lib.icm_clear_observables(self._h))
+
+    # -- reads
+    def read_spins(self, out=None):
+        if out is None:
+            out = np.empty((self.n_inst, self.R, self.N), dtype=np.int8)
+        p, f = _ptr(out)
+        self.ctx.check(self._lib.icm_read_spins(self._h, p, f))
+        return out
+
+    def read_energies(self, out=None):
+        if out is None:
+            out = np.empty((self.n_inst, self.R), dtype=np.float64)
+        p, f = _ptr(out)
+        self.ctx.check(self._lib.icm_read_energies(self._h, p, f))
+        return out
+
+    def read_sweeps(self):
+        out = np.empty(self.n_inst, dtype=np.uint32)
+        self.ctx.check(self._lib.icm_read_sweeps(self._h, out.ctypes.data, 0))
+        return out
+
+    def read_observables(self, hist: bool = True) -> Observables:
+        n, nT = self.n_inst, self.nT
+        o = Observables(np.empty((n, nT)), *[np.empty((n, nT), np.int64) for _ in range(4)],
+                        np.empty((n, nT, self.N + 1), np.int64) if hist else None, np.empty(n, np.int64))
+        self.ctx.check(self._lib.icm_read_observables(
+            self._h, o.accE.ctypes.data, o.acc_n.ctypes.data, o.acc_q2.ctypes.data, o.acc_pmin.ctypes.data,
+            o.acc_d.ctypes.data, o.hist.ctypes.data if hist else None, o.n_meas.ctypes.data, 0))
+        return o
+
+    def read_trace(self) -> dict:
+        n, nT = self.n_inst, self.nT
+        tr = dict(n_pre=np.empty((n, nT), np.int32), flip2a=np.empty((n, nT), np.int32),
+                  seed_site=np.empty((n, nT), np.int32), csize=np.empty((n, nT), np.int32),
+                  esum_before=np.empty((n, nT)), esum_after=np.empty((n, nT)),
+                  swap_acc=np.empty((n, 2, nT - 1), np.uint8))
+        self.ctx.check(self._lib.icm_read_trace(self._h, *[tr[k].ctypes.data for k in (
+            "n_pre", "flip2a", "seed_site", "csize", "esum_before", "esum_after", "swap_acc")], 0))
+        return tr
+
+    def info(self) -> dict:
+        t, c, g, s = (ctypes.c_int32() for _ in range(4))
+        la = ctypes.c_int64()
+        self.ctx.check(self._lib.icm_batch_info(self._h, ctypes.byref(t), ctypes.byref(c), ctypes.byref(g),
+                                                ctypes.byref(s), ctypes.byref(la)))
+        return dict(threads=t.value, ctas_per_sm=c.value, grid=g.value, smem_bytes=s.value, launches=la.value)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.icm_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,304 @@
+"""Parity of the CUDA library (through its C ABI) with the CPU oracle.
+
++-J couplings: bit-exact, sweep by sweep (spins, integer energies, n before
+step 2a, step-2a decisions, seed sites, cluster sizes, PT decisions) and for
+the accumulated observables.  Gaussian couplings: statistical agreement
+(energy per spin, link overlap, overlap distribution within 3.5 standard
+errors over instances), energy conservation of every cluster move to 1e-5
+of sum |J| in fp32, and the Eq. 1 identity.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import exact
+from oracle import oracle as O
+from paper_1501_05630_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def icm():
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = icmpt.Context(0)
+    yield icmpt, ctx
+    ctx.close()
+
+
+def _setup(kind, L, dis, n_inst, T, seed, ids=None):
+    g = O.Geometry(kind, L)
+    ids = list(range(n_inst)) if ids is None else list(ids)
+    J = I.couplings(g.Nb, dis, seed, ids)
+    s0 = I.initial_spins(g.N, 2 * len(T), seed, ids)
+    return g, J, s0, ids
+
+
+def _oracle(g, J, s0, T, T_icm, seed, inst, dis, **kw):
+    return O.Instance(g, J.astype(np.float64), T, s0, pm=(dis == I.PM_J), T_icm=T_icm, seed=seed,
+                      inst=inst, **kw)
+
+
+TRACE_KEYS = ("n_pre", "flip2a", "seed_site", "csize", "esum_before", "esum_after")
+
+
+def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, check_every=1, **sched):
+    icmpt, ctx = icm
+    T = I.ladder(T_lo, T_hi, nT)
+    g, J, s0, ids = _setup(kind, L, I.PM_J, n_inst, T, seed)
+    b = icmpt.Batch(ctx, kind, L, I.PM_J, J, T, T_icm, seed, spins=s0)
+    b.set_schedule(trace=1, **sched)
+    refs = [_oracle(g, J[a], s0[a], T, T_icm, seed, ids[a], I.PM_J, **sched) for a in range(n_inst)]
+    done = 0
+    while done < sweeps:
+        step = min(check_every, sweeps - done)
+        b.run(step)
+        trs = [r.run(step, trace=True) for r in refs]
+        done += step
+        spins, E, tr = b.read_spins(), b.read_energies(), b.read_trace()
+        for a, r in enumerate(refs):
+            assert np.array_equal(spins[a], r.s), (a, done, "spins")
+            assert np.array_equal(E[a], r.E), (a, done, E[a], r.E)
+            for key in TRACE_KEYS:
+                assert np.array_equal(tr[key][a], trs[a][key]), (a, done, key, tr[key][a], trs[a][key])
+            if nT > 1:
+                assert np.array_equal(tr["swap_acc"][a], trs[a]["swap_acc"]), (a, done, "swap")
+    o = b.read_observables()
+    for a, r in enumerate(refs):
+        assert np.array_equal(o.accE[a], r.accE)
+        assert np.array_equal(o.acc_n[a], r.acc_n)
+        assert np.array_equal(o.acc_q2[a], r.acc_q2)
+        assert np.array_equal(o.acc_pmin[a], r.acc_pmin)
+        assert np.array_equal(o.acc_d[a], r.acc_d)
+        assert np.array_equal(o.hist[a], r.hist)
+        assert o.n_meas[a] == r.n_meas[0]
+    assert np.all(b.read_sweeps() == sweeps)
+    b.close()
+
+
+# ----------------------------------------------------------------------------- +-J, bit-exact
+def test_pmj_2d_L8_sweep_by_sweep(icm):
+    """2D L=8 +-J, 16 temperatures in [0.2, 1.5], ICM for T <= 1: every sweep."""
+    _compare_sweeps(icm, O.SQUARE2D, 8, 16, 0.2, 1.5, 1.0, 1, 200, 0x1501056300000001)
+
+
+def test_pmj_2d_L8_full_run_4096_sweeps(icm):
+    """The full 2D L=8 workload: 4096 sweeps, measured from sweep 2048."""
+    icmpt, ctx = icm
+    seed = 0x1501056300000001
+    T = I.ladder(0.2, 1.5, 16)
+    g, J, s0, ids = _setup(O.SQUARE2D, 8, I.PM_J, 1, T, seed)
+    b = icmpt.Batch(ctx, O.SQUARE2D, 8, I.PM_J, J, T, 1.0, seed, spins=s0)
+    b.set_schedule(t_meas=2048)
+    b.run(4096)
+    r = _oracle(g, J[0], s0[0], T, 1.0, seed, 0, I.PM_J, t_meas=2048)
+    r.run(4096)
+    assert np.array_equal(b.read_spins()[0], r.s)
+    assert np.array_equal(b.read_energies()[0], r.E)
+    o = b.read_observables()
+    assert np.array_equal(o.hist[0], r.hist) and np.array_equal(o.acc_d[0], r.acc_d)
+    assert np.array_equal(o.accE[0], r.accE) and o.n_meas[0] == 2048
+
+
+@pytest.mark.parametrize("kind,L,nT,T_hi,T_icm,n_inst", [
+    (O.CUBIC3D, 4, 24, 2.0, 1.0, 3),     # two spin words per site (48 replicas)
+    (O.CUBIC3D, 6, 10, 2.0, 1.0, 2),     # 108 sites per colour: ragged against 128 threads
+    (O.CHIMERA, 3, 30, 3.0, 1.5, 2),     # per-site degree 5/6, padded neighbour lists
+    (O.SQUARE2D, 2, 4, 1.5, 1.0, 2),     # doubled bonds of the smallest torus
+    (O.CUBIC3D, 2, 3, 2.0, 1.0, 2),
+    (O.SQUARE2D, 6, 2, 1.5, 1.0, 1),     # fewest temperatures
+    (O.CHIMERA, 1, 32, 3.0, 1.5, 1),     # most temperatures: 64 replicas, two full words
+])
+def test_pmj_sweep_by_sweep_shapes(icm, kind, L, nT, T_hi, T_icm, n_inst):
+    _compare_sweeps(icm, kind, L, nT, 0.2, T_hi, T_icm, n_inst, 40, 0xC0FFEE + L)
+
+
+@pytest.mark.parametrize("sched", [
+    dict(enable_2a=0), dict(icm_every=0), dict(swap_every=0), dict(icm_every=3, swap_every=2),
+    dict(enable_metropolis=0), dict(t_meas=10**9),
+])
+def test_pmj_schedule_variants(icm, sched):
+    _compare_sweeps(icm, O.CUBIC3D, 4, 8, 0.3, 2.0, 1.2, 2, 25, 77, **sched)
+
+
+def test_pmj_multi_sweep_launches(icm):
+    """Several sweeps per launch give the same state as one sweep per launch."""
+    _compare_sweeps(icm, O.CHIMERA, 4, 12, 0.2, 3.0, 1.5, 3, 90, 5, check_every=30)
+
+
+def test_pmj_chimera_C8_full_batch_sampled(icm):
+    """The chimera C_8 workload's shape: 10^4 instances, 30 temperatures, in one
+    launch; sampled instances re-run alone by the oracle must match bit for bit."""
+    icmpt, ctx = icm
+    seed = 0x1501056300000003
+    T = I.ladder(0.2, 3.0, 30)
+    n = 10000
+    g = O.Geometry(O.CHIMERA, 8)
+    J = I.couplings(g.Nb, I.PM_J, seed, range(n))
+    s0 = I.initial_spins(g.N, 60, seed, range(n))
+    b = icmpt.Batch(ctx, O.CHIMERA, 8, I.PM_J, J, T, 1.5, seed, spins=s0)
+    b.run(24)
+    spins, E = b.read_spins(), b.read_energies()
+    for a in (0, 1, 4999, 9998, 9999):
+        r = _oracle(g, J[a], s0[a], T, 1.5, seed, a, I.PM_J)
+        r.run(24)
+        assert np.array_equal(spins[a], r.s), a
+        assert np.array_equal(E[a], r.E), a
+    # every instance: integer energies consistent with its spins
+    for a in range(0, n, 997):
+        e = -(J[a][None, :].astype(np.int64) * spins[a][:, g.bi] * spins[a][:, g.bj]).sum(1)
+        assert np.array_equal(e, E[a].astype(np.int64))
+
+
+def test_mix_invariance(icm):
+    """An instance gives the same result alone and inside a larger batch."""
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 12)
+    seed = 99
+    g = O.Geometry(O.CUBIC3D, 4)
+    for dis in (I.PM_J, I.GAUSS):
+        J = I.couplings(g.Nb, dis, seed, range(40))
+        s0 = I.initial_spins(g.N, 24, seed, range(40))
+        big = icmpt.Batch(ctx, O.CUBIC3D, 4, dis, J, T, 1.0, seed, spins=s0)
+        big.run(50)
+        alone = icmpt.Batch(ctx, O.CUBIC3D, 4, dis, J[17:18].copy(), T, 1.0, seed, spins=s0[17:18].copy(),
+                            instance_ids=[17])
+        alone.run(50)
+        assert np.array_equal(big.read_spins()[17], alone.read_spins()[0])
+        assert np.array_equal(big.read_energies()[17], alone.read_energies()[0])
+
+
+# ----------------------------------------------------------------------------- Gaussian, statistical
+def test_gauss_energy_conservation_and_consistency(icm):
+    """Every cluster move keeps E_a + E_b to 1e-5 sum|J| (fp32); device energies
+    agree with energies recomputed from the spins."""
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 24)
+    seed = 0x1501056300000002
+    g, J, s0, ids = _setup(O.CUBIC3D, 8, I.GAUSS, 64, T, seed)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_schedule(trace=1)
+    scale = np.abs(J).astype(np.float64).sum(1)
+    moves = 0
+    for rep in range(6):
+        b.run(7)
+        tr = b.read_trace()
+        icm_k = tr["n_pre"] >= 0
+        moves += int((tr["csize"] > 0).sum())
+        err = np.abs(tr["esum_after"] - tr["esum_before"])[icm_k]
+        assert np.all(err <= 1e-5 * np.repeat(scale[:, None], 24, 1)[icm_k])
+        spins, E = b.read_spins(), b.read_energies()
+        Jd = J.astype(np.float64)
+        e_ref = -np.einsum("b,rb->r", Jd[0], spins[0][:, g.bi] * spins[0][:, g.bj])
+        for a in range(0, 64, 9):
+            e_ref = -np.einsum("b,rb->r", Jd[a], (spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64))
+            assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a])
+    assert moves > 100
+
+
+def _stats(samples):
+    s = np.asarray(samples, dtype=np.float64)
+    return s.mean(0), s.std(0, ddof=1) / math.sqrt(len(s))
+
+
+def test_gauss_statistical_agreement_with_oracle(icm):
+    """3D L=4 Gaussian, 96 instances: per-temperature energy, link overlap and
+    <q^2> from the GPU agree with the oracle's on the same instances."""
+    icmpt, ctx = icm
+    T = I.ladder(0.3, 2.0, 8)
+    seed = 4242
+    n = 96
+    g, J, s0, ids = _setup(O.CUBIC3D, 4, I.GAUSS, n, T, seed)
+    sweeps, t_meas = 4000, 1000
+    b = icmpt.Batch(ctx, O.CUBIC3D, 4, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_schedule(t_meas=t_meas)
+    b.run(sweeps)
+    o = b.read_observables()
+    m = o.n_meas[:, None].astype(np.float64)
+    gpu = dict(e=o.accE / (2 * g.N * m), q_l=1 - 2 * o.acc_d / (g.Nb * m), q2=o.acc_q2 / (g.N ** 2 * m))
+    cpu = {k: [] for k in gpu}
+    for a in range(n):
+        r = _oracle(g, J[a], s0[a], T, 1.0, seed, a, I.GAUSS, t_meas=t_meas)
+        r.run(sweeps)
+        ob = r.observables()
+        for k in cpu:
+            cpu[k].append(ob[k])
+    for k in gpu:
+        d = gpu[k] - np.asarray(cpu[k])          # paired by instance: disorder cancels
+        mu, se = _stats(d)
+        assert np.all(np.abs(mu) <= 3.5 * se + 1e-9), (k, mu, se)
+
+
+def test_gauss_matches_exact_enumeration(icm):
+    """2D L=4 Gaussian (N = 16): 64 independent chains of one instance agree
+    with exact enumeration (energy, link overlap, symmetrised P(q))."""
+    icmpt, ctx = icm
+    T = I.ladder(0.4, 2.0, 6)
+    seed = 5
+    g = O.Geometry(O.SQUARE2D, 4)
+    J1 = I.couplings(g.Nb, I.GAUSS, seed, [0])[0]
+    n = 64
+    J = np.repeat(J1[None], n, 0)
+    s0 = I.initial_spins(g.N, 12, seed, range(1000, 1000 + n))
+    b = icmpt.Batch(ctx, O.SQUARE2D, 4, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_schedule(t_meas=1000)
+    b.run(5000)
+    o = b.read_observables()
+    m = o.n_meas[:, None].astype(np.float64)
+    st = exact.all_states(g.N)
+    E = exact.energies(g.bi, g.bj, J1.astype(np.float64), st)
+    ex = [exact.thermal(g.bi, g.bj, J1.astype(np.float64), g.N, t, st, E) for t in T]
+    for name, vals in (("e", o.accE / (2 * g.N * m)), ("q_l", 1 - 2 * o.acc_d / (g.Nb * m))):
+        mu, se = _stats(vals)
+        want = np.array([x[name] for x in ex])
+        assert np.all(np.abs(mu - want) <= 3.5 * se + 1e-4), (name, mu, se, want)
+    P = o.hist / m[:, :, None] if o.hist.ndim == 3 else None
+    for k in (0, len(T) - 1):
+        sym = (P[:, k] + P[:, k, ::-1]) / 2
+        mu, se = _stats(sym)
+        assert np.all(np.abs(mu - ex[k]["P_n"]) <= 3.5 * se + 2e-3)
+
+
+def test_gauss_eq1_identity(icm):
+    """Eq. 1: disorder-averaged e = -(N_b/N)(1 - [q_l])/T at equilibrium
+    (3D L=4, 200 instances, well-thermalised moderate temperatures)."""
+    icmpt, ctx = icm
+    T = I.ladder(0.6, 2.0, 8)
+    seed = 31
+    n = 200
+    g, J, s0, ids = _setup(O.CUBIC3D, 4, I.GAUSS, n, T, seed)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 4, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_schedule(t_meas=2000)
+    b.run(10000)
+    o = b.read_observables()
+    m = o.n_meas[:, None].astype(np.float64)
+    e = o.accE / (2 * g.N * m)
+    ql = 1 - 2 * o.acc_d / (g.Nb * m)
+    d = e + (g.Nb / g.N) * (1 - ql) / T[None, :]
+    mu, se = _stats(d)
+    assert np.all(np.abs(mu) <= 3.5 * se + 2e-3), (mu, se)
+
+
+# ----------------------------------------------------------------------------- limits and errors
+def test_largest_supported_instance(icm):
+    """3D L=12 (1728 sites), 48 replicas: one CTA holds the whole instance."""
+    _compare_sweeps(icm, O.CUBIC3D, 12, 24, 0.2, 2.0, 1.0, 2, 6, 12, check_every=3)
+
+
+def test_invalid_arguments(icm):
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 4)
+    J = I.couplings(48, I.PM_J, 0, [0])
+    with pytest.raises(icmpt.IcmError):
+        icmpt.Batch(ctx, O.SQUARE2D, 5, I.PM_J, I.couplings(50, I.PM_J, 0, [0]), T, 1.0, 0)   # odd L
+    with pytest.raises(icmpt.IcmError):
+        icmpt.Batch(ctx, O.CUBIC3D, 4, I.PM_J, I.couplings(192, I.PM_J, 0, [0]), T[::-1].copy(), 1.0, 0)
+    with pytest.raises(icmpt.IcmError):
+        icmpt.Batch(ctx, O.CUBIC3D, 4, I.PM_J, I.couplings(192, I.PM_J, 0, [0]), I.ladder(0.2, 2, 33), 1.0, 0)
+    with pytest.raises(icmpt.IcmError):
+        icmpt.Batch(ctx, O.SQUARE2D, 256, I.PM_J, I.couplings(2 * 256 * 256, I.PM_J, 0, [0]), T, 1.0, 0)
+    del J
