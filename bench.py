@@ -137,6 +137,16 @@ def oracle_throughput(wl, sweeps: int, n_inst: int, threads: int):
     return updates / dt / 1e9, dt, updates
 
 
+def calibrate_sweeps(wl, cores, seconds):
+    """Sweeps per instance so that 2*cores instances take about `seconds`."""
+    rate, dt, _ = oracle_throughput(wl, 4, 1, 1)            # updates/ns of one core
+    from oracle import oracle as O
+    g = O.Geometry(wl["lattice"], wl["L"])
+    per_sweep = g.N * 2 * len(I.ladder(*wl["T"]))
+    sweeps = int(seconds * rate * 1e9 * cores / (2 * cores * per_sweep))
+    return max(4, sweeps)
+
+
 def run_reference(args, wl, rank):
     cores = os.cpu_count() or 1
     if rank != 0:
@@ -170,6 +180,7 @@ def main():
     ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS))
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--ref-sweeps", type=int, default=32)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -285,10 +296,11 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
-        ref_sweeps = args.ref_sweeps
-        v, dt, _ = oracle_throughput(wl, ref_sweeps, cores, cores)
+        ref_sweeps = calibrate_sweeps(wl, cores, args.cpu_seconds)
+        v, dt, _ = oracle_throughput(wl, ref_sweeps, 2 * cores, cores)
         cpu = {"value": v, "unit": "updates/ns", "cores": cores, "kind": "oracle",
-               "sample": f"{cores} instances x {ref_sweeps} sweeps of the same workload, {dt:.1f} s"}
+               "sample": f"{2 * cores} of the {wl['n_inst']} instances x {ref_sweeps} sweeps "
+                         f"({dt:.1f} s on {cores} threads)"}
 
     if rank == 0:
         out = {

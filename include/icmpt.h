@@ -106,6 +106,8 @@ typedef struct {
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * (NULL = the legacy default stream) on which all work is enqueued.       */
 icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream);
+/* Destroys the context and every batch still alive on it (their handles
+ * become invalid). */
 icm_status icm_ctx_destroy(icm_ctx *ctx);
 /* Description of the last error on this context; owned by the context and
  * valid until the next call on it.  Never NULL.                            */

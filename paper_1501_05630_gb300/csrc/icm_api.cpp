@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <set>
 #include <string>
 #include <vector>
 
@@ -21,6 +22,7 @@ struct icm_ctx {
     int num_sms = 0;
     int max_smem_optin = 0;
     std::string err = "no error";
+    std::set<icm_batch *> batches;   // live batches, freed with the context
 };
 
 namespace {
@@ -226,7 +228,10 @@ icm_status clear_observables(icm_batch *b)
 void destroy_batch(icm_batch *b)
 {
     if (!b) return;
-    if (b->ctx) cudaStreamSynchronize(b->ctx->stream);
+    if (b->ctx) {
+        cudaStreamSynchronize(b->ctx->stream);
+        b->ctx->batches.erase(b);
+    }
     for (void *p : b->allocs) cudaFree(p);
     delete b;
 }
@@ -258,6 +263,7 @@ icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream)
 icm_status icm_ctx_destroy(icm_ctx *ctx)
 {
     if (!ctx) return ICM_ERR_ARG;
+    while (!ctx->batches.empty()) destroy_batch(*ctx->batches.begin());
     delete ctx;
     return ICM_OK;
 }
@@ -404,6 +410,8 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         for (int m = 1; m <= 6; ++m) thr_metro[(size_t)r * 8 + m] = acceptance_threshold((double)(-2 * m) * bk);
         b2l[r] = (float)(-2.0 * bk * 1.4426950408889634);
     }
+    std::vector<float> dbeta_l2e(n_T - 1);
+    for (int k = 0; k + 1 < n_T; ++k) dbeta_l2e[k] = (float)((beta[k] - beta[k + 1]) * 1.4426950408889634);
     std::vector<uint32_t> thr_swap;
     std::vector<int32_t> swap_off(n_T - 1), swap_len(n_T - 1);
     for (int k = 0; k + 1 < n_T; ++k) {
@@ -436,6 +444,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     int32_t *d_Ei, *d_off, *d_len, *d_trn, *d_trf, *d_trs, *d_trc;
     uint32_t *d_spins, *d_t, *d_id, *d_thr, *d_thrs;
     double *d_beta, *d_accE;
+    float *d_dbl;
     long long *d_acc64, *d_nmeas;
     unsigned long long *d_hist;
     uint8_t *d_trsw;
@@ -447,7 +456,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         (st = dalloc(b, &d_spins, (size_t)n_inst * G * N)) || (st = dalloc(b, &d_Ef, (size_t)n_inst * R)) ||
         (st = dalloc(b, &d_Ei, (size_t)n_inst * R)) || (st = dalloc(b, &d_t, n_inst)) ||
         (st = dalloc(b, &d_id, n_inst)) || (st = dalloc(b, &d_thr, (size_t)R * 8)) || (st = dalloc(b, &d_b2l, R)) ||
-        (st = dalloc(b, &d_beta, n_T)) || (st = dalloc(b, &d_thrs, thr_swap.size())) ||
+        (st = dalloc(b, &d_beta, n_T)) || (st = dalloc(b, &d_dbl, n_T - 1)) || (st = dalloc(b, &d_thrs, thr_swap.size())) ||
         (st = dalloc(b, &d_off, n_T - 1)) || (st = dalloc(b, &d_len, n_T - 1)) || (st = dalloc(b, &d_accE, nk)) ||
         (st = dalloc(b, &d_acc64, 4 * nk)) || (st = dalloc(b, &d_hist, nk * (N + 1))) ||
         (st = dalloc(b, &d_nmeas, n_inst)) || (st = dalloc(b, &d_trn, nk)) || (st = dalloc(b, &d_trf, nk)) ||
@@ -460,7 +469,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     }
     P.nbr = d_nbr; P.pos2site = d_pos2site; P.zdeg = d_zdeg; P.Jb = d_Jb; P.Jd = d_Jd; P.spins = d_spins;
     P.Ef = d_Ef; P.Ei = d_Ei; P.tsweep = d_t; P.inst_id = d_id; P.thr_metro = d_thr; P.b2l = d_b2l;
-    P.beta = d_beta; P.thr_swap = d_thrs; P.swap_off = d_off; P.swap_len = d_len; P.accE = d_accE;
+    P.beta = d_beta; P.dbeta_l2e = d_dbl; P.thr_swap = d_thrs; P.swap_off = d_off; P.swap_len = d_len; P.accE = d_accE;
     P.acc64 = d_acc64; P.hist = d_hist; P.n_meas = d_nmeas; P.tr_n_pre = d_trn; P.tr_flip2a = d_trf;
     P.tr_seed = d_trs; P.tr_csize = d_trc; P.tr_eb = d_treb; P.tr_ea = d_trea; P.tr_swap = d_trsw;
 
@@ -483,6 +492,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     if (e == cudaSuccess) e = UP(d_thr, thr_metro);
     if (e == cudaSuccess) e = UP(d_b2l, b2l);
     if (e == cudaSuccess) e = UP(d_beta, beta);
+    if (e == cudaSuccess) e = UP(d_dbl, dbeta_l2e);
     if (e == cudaSuccess) e = UP(d_thrs, thr_swap);
     if (e == cudaSuccess) e = UP(d_off, swap_off);
     if (e == cudaSuccess) e = UP(d_len, swap_len);
@@ -502,6 +512,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         destroy_batch(b);
         return cuda_fail(ctx, e, "batch creation");
     }
+    ctx->batches.insert(b);
     *out = b;
     return ICM_OK;
 }

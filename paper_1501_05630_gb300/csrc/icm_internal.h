@@ -56,6 +56,7 @@ struct KParams {
     const uint32_t *thr_metro;    // [R][8]
     const float *b2l;             // [R]
     const double *beta;           // [nT]
+    const float *dbeta_l2e;       // [nT-1] (beta_k - beta_{k+1}) log2(e)
     const uint32_t *thr_swap;     // concatenated per pair k
     const int32_t *swap_off;      // [nT-1]
     const int32_t *swap_len;      // [nT-1]

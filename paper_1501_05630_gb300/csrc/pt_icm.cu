@@ -394,9 +394,11 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
         S.swap_x[c * 32 + k] = x[0];
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    const int second = blockDim.x > 32 ? 32 : 1;   // copy 1 runs on another warp when there is one
+    if (threadIdx.x == 0 || threadIdx.x == second) {
         ET *E = (ET *)S.E;
-        for (int c = 0; c < 2; ++c) {
+        const int c = threadIdx.x == 0 ? 0 : 1;
+        {
             int ns = 0;
             for (int k = 0; k < np; ++k) {
                 const int ra = 2 * k + c, rb = ra + 2;
@@ -404,8 +406,9 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
                 const uint32_t x = S.swap_x[c * 32 + k];
                 bool acc;
                 if constexpr (GAUSS) {
-                    const double delta = (P.beta[k] - P.beta[k + 1]) * ((double)ek - (double)ek1);
-                    acc = (delta >= 0.0) || ((double)(x >> 8) * (1.0 / 16777216.0) < exp(delta));
+                    // log2(e) (beta_k - beta_{k+1}) (E_k - E_{k+1}); accept iff >= 0 or u < 2^delta
+                    const float delta = P.dbeta_l2e[k] * (ek - ek1);
+                    acc = (delta >= 0.f) || ((float)(x >> 8) * (1.0f / 16777216.0f) < ex2_approx(delta));
                 } else {
                     const int dE = ek - ek1;
                     if (dE >= 0) {
@@ -488,8 +491,7 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
         }
     }
     __syncthreads();
-    if (threadIdx.x < nT) {
-        const int k = threadIdx.x;
+    for (int k = threadIdx.x; k < nT; k += blockDim.x) {
         const long long n = S.cnt_n[k], d = S.cnt_d[k];
         S.cnt_n[k] = 0;
         S.cnt_d[k] = 0;
@@ -571,10 +573,10 @@ __global__ void __launch_bounds__(kMaxThreads, 4) fused_kernel(const KParams P, 
                 __syncthreads();
                 half_sweep<GAUSS, Z, 1>(P, S, t, inst);
                 __syncthreads();
-                if (tid < R) {
+                for (int r = tid; r < R; r += nth) {
                     ET e = ET(0);
-                    for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + tid];
-                    ((ET *)S.E)[tid] = e;
+                    for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + r];
+                    ((ET *)S.E)[r] = e;
                 }
                 __syncthreads();
             }

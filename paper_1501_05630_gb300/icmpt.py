@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 from dataclasses import dataclass
 
 import numpy as np
@@ -120,6 +121,7 @@ class Context:
         if rc:
             raise IcmError(rc, "icm_ctx_create failed (no CUDA device?)")
         self._h = h
+        self._batches = weakref.WeakSet()
 
     def check(self, rc: int):
         if rc:
@@ -130,6 +132,8 @@ class Context:
 
     def close(self):
         if getattr(self, "_h", None):
+            for b in list(self._batches):      # the library frees them with the context
+                b._h = None
             self._lib.icm_ctx_destroy(self._h)
             self._h = None
 
@@ -176,6 +180,7 @@ class Batch:
             None if ids is None else ids.ctypes.data, self.T.ctypes.data, self.nT, float(T_icm),
             int(seed) & 0xFFFFFFFFFFFFFFFF, cflags, ctypes.byref(h)))
         self._h = h
+        ctx._batches.add(self)
 
     # -- control
     def schedule(self) -> Schedule:
@@ -247,9 +252,9 @@ class Batch:
         return dict(threads=t.value, ctas_per_sm=c.value, grid=g.value, smem_bytes=s.value, launches=la.value)
 
     def close(self):
-        if getattr(self, "_h", None):
+        if getattr(self, "_h", None) and getattr(self.ctx, "_h", None):
             self._lib.icm_batch_destroy(self._h)
-            self._h = None
+        self._h = None
 
     def __del__(self):
         try:
