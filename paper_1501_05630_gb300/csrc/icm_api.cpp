@@ -376,9 +376,11 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         }
     }
     // launch shape and shared memory
+    int n_icm = 0;
+    while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
     const int threads = icm::fused_threads(N);
     const int nwarps = threads / 32;
-    const icm::SmemLayout sm = icm::smem_layout(N, Z, R, G, n_T, nwarps, b->gauss);
+    const icm::SmemLayout sm = icm::smem_layout(N, Z, R, G, n_T, n_icm, nwarps, b->gauss);
     if (sm.total > ctx->max_smem_optin) {
         destroy_batch(b);
         return fail(ctx, ICM_ERR_UNSUPPORTED, "instance needs " + std::to_string(sm.total) +
@@ -427,8 +429,6 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         swap_len[k] = len;
     }
     if (thr_swap.empty()) thr_swap.push_back(0u);
-    int n_icm = 0;
-    while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
 
     icm::KParams &P = b->kp;
     P.N = N; P.Nb = g.Nb; P.nT = n_T; P.R = R; P.G = G; P.Z = Z; P.n_inst = n_inst; P.n_icm = n_icm;

@@ -16,18 +16,18 @@ struct SmemLayout {
     int spins;      // uint32 [G][N]
     int nbr;        // uint16 [N][Z]   neighbour positions, padding = self
     int zdeg;       // uint8  [N]      degree (+-J only)
-    int pos2site;   // uint16 [N]
     int coup;       // float [N][Z] (Gaussian) or uint8 [N] bit d = (J < 0) (+-J)
     int E;          // float or int32 [R]
     int Epart;      // float or int32 [nwarps][R]
     int rtab;       // uint32 [R][8] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
-    int icm_mask;   // uint32 [nwarps][NW]
-    int icm_C;      // uint32 [nwarps][NW]
-    int icm_queue;  // uint16 [nwarps][N]
-    int icm_tail;   // int32 [nwarps]
+    int icm_mask;   // uint32 [n_icm][NW] overlap masks per ICM pair
+    int icm_C;      // uint32 [G][N]     cluster bits (bit 2k: site in pair k's cluster)
     int swap_x;     // uint32 [2][32]
     int swap_list;  // int32 [2][32]
     int swap_n;     // int32 [2]
+    int flipw;      // uint32 [2]      step-2a reversal masks of the two words
+    int icm_seed;   // int32 [32]      seed position per ICM pair (-1: none)
+    int next_pair;  // int32 [1]       dynamic pair counter
     int cnt_n;      // int32 [32]
     int cnt_d;      // int32 [32]
     int accE;       // double [nT]
@@ -76,7 +76,7 @@ struct KParams {
     SmemLayout sm;
 };
 
-SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int nwarps, bool gauss);
+SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss);
 int fused_threads(int N);
 
 // Host-callable launchers (pt_icm.cu).  Return a cudaError_t.

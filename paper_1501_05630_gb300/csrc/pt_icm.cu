@@ -30,6 +30,25 @@
 #include <cstdio>
 #include <type_traits>
 
+// Optional per-phase cycle counters (compile with -DICM_PHASE_TIMERS): thread 0
+// of every CTA adds the clock64() cycles between phase marks to a global
+// table, read back by icm_debug_phase_cycles().  Off by default; no work is
+// skipped either way.
+#ifdef ICM_PHASE_TIMERS
+__device__ unsigned long long g_icm_phase_cycles[16];
+#define PHASE_INIT() long long ph_last_ = clock64(); long long ph_acc_[8] = {0, 0, 0, 0, 0, 0, 0, 0}
+#define PHASE_MARK(i) do { if (threadIdx.x == 0) { const long long n_ = clock64(); ph_acc_[i] += n_ - ph_last_; ph_last_ = n_; } } while (0)
+#define PHASE_FLUSH() do { if (threadIdx.x == 0) for (int i_ = 0; i_ < 7; ++i_) atomicAdd(&g_icm_phase_cycles[i_], (unsigned long long)ph_acc_[i_]); } while (0)
+#define ICM_SUB_INIT() long long icm_t0_ = clock64()
+#define ICM_SUB(i) do { if (threadIdx.x == 0) { const long long n_ = clock64(); atomicAdd(&g_icm_phase_cycles[i], (unsigned long long)(n_ - icm_t0_)); icm_t0_ = n_; } } while (0)
+#else
+#define ICM_SUB_INIT() do { } while (0)
+#define ICM_SUB(i) do { } while (0)
+#define PHASE_INIT() do { } while (0)
+#define PHASE_MARK(i) do { } while (0)
+#define PHASE_FLUSH() do { } while (0)
+#endif
+
 namespace icm {
 
 namespace {
@@ -57,6 +76,28 @@ __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, 
     o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
 }
 
+// Two Philox4x32-10 blocks with counters {c0, c1, c2, c3} and {c0, c1, c2+1, c3},
+// written as two independent chains so that the scheduler can interleave them.
+__device__ __forceinline__ void philox10x2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
+                                           uint32_t k1, uint32_t (&o)[4], uint32_t (&p)[4])
+{
+    uint32_t a0 = c0, a1 = c1, a2 = c2, a3 = c3;
+    uint32_t b0 = c0, b1 = c1, b2 = c2 + 1u, b3 = c3;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t ma0 = (uint64_t)a0 * 0xD2511F53ull, ma1 = (uint64_t)a2 * 0xCD9E8D57ull;
+        const uint64_t mb0 = (uint64_t)b0 * 0xD2511F53ull, mb1 = (uint64_t)b2 * 0xCD9E8D57ull;
+        const uint32_t na0 = (uint32_t)(ma1 >> 32) ^ a1 ^ k0, na2 = (uint32_t)(ma0 >> 32) ^ a3 ^ k1;
+        const uint32_t nb0 = (uint32_t)(mb1 >> 32) ^ b1 ^ k0, nb2 = (uint32_t)(mb0 >> 32) ^ b3 ^ k1;
+        a1 = (uint32_t)ma1; a3 = (uint32_t)ma0; a0 = na0; a2 = na2;
+        b1 = (uint32_t)mb1; b3 = (uint32_t)mb0; b0 = nb0; b2 = nb2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3;
+    p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3;
+}
+
 __device__ __forceinline__ float ex2_approx(float x)
 {
     float y;
@@ -79,6 +120,23 @@ __device__ __forceinline__ T transpose_reduce(T (&a)[32], int lane)
         }
     }
     return a[0];
+}
+
+// Sum of a[j] over the 32 lanes, delivered to lanes 2j and 2j+1 (16 shuffles).
+template <typename T>
+__device__ __forceinline__ T transpose_reduce16(T (&a)[16], int lane)
+{
+#pragma unroll
+    for (int s = 8; s >= 1; s >>= 1) {
+        const bool upper = (lane & (2 * s)) != 0;
+#pragma unroll
+        for (int j = 0; j < s; ++j) {
+            const T send = upper ? a[j] : a[j + s];
+            const T keep = upper ? a[j + s] : a[j];
+            a[j] = keep + __shfl_xor_sync(kFull, send, 2 * s);
+        }
+    }
+    return a[0] + __shfl_xor_sync(kFull, a[0], 1);
 }
 
 template <typename T>
@@ -112,7 +170,6 @@ struct Sm {
     uint32_t *s;
     uint16_t *nbr;
     uint8_t *zdeg;
-    uint16_t *pos2site;
     float *Jd;
     uint8_t *Jb;
     void *E;
@@ -121,11 +178,12 @@ struct Sm {
     float *b2l;
     uint32_t *mask;
     uint32_t *C;
-    uint16_t *queue;
-    int *tail;
     uint32_t *swap_x;
     int *swap_list;
     int *swap_n;
+    uint32_t *flipw;
+    int *icm_seed;
+    int *next_pair;
     int *cnt_n;
     int *cnt_d;
     double *accE;
@@ -139,7 +197,6 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.s = (uint32_t *)(base + L.spins);
     S.nbr = (uint16_t *)(base + L.nbr);
     S.zdeg = (uint8_t *)(base + L.zdeg);
-    S.pos2site = (uint16_t *)(base + L.pos2site);
     S.Jd = (float *)(base + L.coup);
     S.Jb = (uint8_t *)(base + L.coup);
     S.E = base + L.E;
@@ -148,11 +205,12 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.b2l = (float *)(base + L.rtab);
     S.mask = (uint32_t *)(base + L.icm_mask);
     S.C = (uint32_t *)(base + L.icm_C);
-    S.queue = (uint16_t *)(base + L.icm_queue);
-    S.tail = (int *)(base + L.icm_tail);
     S.swap_x = (uint32_t *)(base + L.swap_x);
     S.swap_list = (int *)(base + L.swap_list);
     S.swap_n = (int *)(base + L.swap_n);
+    S.flipw = (uint32_t *)(base + L.flipw);
+    S.icm_seed = (int *)(base + L.icm_seed);
+    S.next_pair = (int *)(base + L.next_pair);
     S.cnt_n = (int *)(base + L.cnt_n);
     S.cnt_d = (int *)(base + L.cnt_d);
     S.accE = (double *)(base + L.accE);
@@ -161,143 +219,193 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     return S;
 }
 
+// Neighbour positions of position p (padding entries repeat p), read as
+// 32-bit pairs from the [N][Z] uint16 table (Z even, so rows are 4-byte aligned).
+template <int Z>
+__device__ __forceinline__ void load_nbrs(const uint16_t *nbr, int p, int (&q)[Z])
+{
+    const uint32_t *w = (const uint32_t *)(nbr + p * Z);
+#pragma unroll
+    for (int i = 0; i < Z / 2; ++i) {
+        const uint32_t v = w[i];
+        q[2 * i] = (int)(v & 0xffffu);
+        q[2 * i + 1] = (int)(v >> 16);
+    }
+}
+
 // ---------------------------------------------------------------------------
-// Step 1: one checkerboard half-sweep (colour COLOR) of every replica.
-template <bool GAUSS, int Z, int COLOR>
-__device__ __forceinline__ void half_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
+// Step 1: one pass of a checkerboard half-sweep (colour COLOR) over the 16
+// replica bits [32 g + 16 H, 32 g + 16 H + 16) of every site word of that
+// colour.  Bits at or above R ("ghost" replicas of a partly used last word)
+// are updated at beta = 0 and never read, so the inner loop has no guards.
+// Two Philox4x32-10 blocks are generated together (8 draws) so that their
+// dependency chains interleave.
+template <bool GAUSS, int Z, int COLOR, int H>
+__device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int N = P.N, half = P.half, nth = blockDim.x;
-    const int iters = (half + nth - 1) / nth;
-    for (int g = 0; g < P.G; ++g) {
-        const int nbits = min(32, P.R - 32 * g);
-        uint32_t *sg = S.s + g * N;
-        ET acc[32];
+    const int rbase = 32 * g + 16 * H;
+    const int npairs8 = (P.R - rbase + 7) >> 3;   // 8-bit groups holding at least one live replica (1 or 2)
+    uint32_t *sg = S.s + g * N;
+    ET acc[16];
 #pragma unroll
-        for (int b = 0; b < 32; ++b) acc[b] = ET(0);
-        for (int it = 0; it < iters; ++it) {
-            const int j = threadIdx.x + it * nth;
-            if (j >= half) continue;
-            const int p = COLOR * half + j;
-            const uint32_t sw = sg[p];
-            const uint32_t site = S.pos2site[p];
-            uint32_t flip = 0;
-            uint32_t x[4] = {0u, 0u, 0u, 0u};
-            if constexpr (GAUSS) {
-                float Jv[Z];
-                uint32_t nw[Z];
+    for (int b = 0; b < 16; ++b) acc[b] = ET(0);
+    for (int j = threadIdx.x; j < half; j += nth) {
+        const int p = COLOR * half + j;
+        const uint32_t sw = sg[p];
+        const uint32_t site = __ldg(P.pos2site + p);
+        uint32_t flip = 0;
+        if constexpr (GAUSS) {
+            float Jv[Z];
+            uint32_t nw[Z];
+            int q[Z];
+            load_nbrs<Z>(S.nbr, p, q);
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    nw[d] = sg[S.nbr[p * Z + d]];
-                    Jv[d] = S.Jd[p * Z + d];
-                }
-                const float *b2l = S.b2l + 32 * g;
+            for (int d = 0; d < Z; ++d) {
+                nw[d] = sg[q[d]];
+                Jv[d] = S.Jd[p * Z + d];
+            }
+            const float *b2l = S.b2l + 32 * g;
 #pragma unroll
-                for (int b = 0; b < 32; ++b) {
-                    if (b < nbits) {
-                        if ((b & 3) == 0) philox10(site, t, (uint32_t)(32 * g + b) >> 2, inst, P.seed_lo, P.seed_hi, x);
+            for (int q = 0; q < 2; ++q) {
+                if (q < npairs8) {
+                    uint32_t x[4], y[4];
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * q, inst, P.seed_lo, P.seed_hi, x, y);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int b = 16 * H + 8 * q + i;   // bit inside the word (compile-time)
                         float h = 0.f;
 #pragma unroll
                         for (int d = 0; d < Z; ++d)
                             h += __uint_as_float(__float_as_uint(Jv[d]) ^ ((nw[d] << (31 - b)) & 0x80000000u));
                         const float sh = __uint_as_float(__float_as_uint(h) ^ ((sw << (31 - b)) & 0x80000000u));
-                        const float u = __uint_as_float(0x3f800000u | (x[b & 3] >> 9)) - 1.0f;
+                        const uint32_t xr = i < 4 ? x[i] : y[i - 4];
+                        const float u = __uint_as_float(0x3f800000u | (xr >> 9)) - 1.0f;
                         const bool a = (sh <= 0.f) || (u < ex2_approx(b2l[b] * sh));
                         flip |= (uint32_t)a << b;
-                        if (COLOR == 1) acc[b] += a ? sh : -sh;
-                    }
-                }
-            } else {
-                uint32_t c0 = 0, c1 = 0, c2 = 0;
-                const uint32_t jb = S.Jb[p];
-#pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const uint32_t u = sw ^ sg[S.nbr[p * Z + d]] ^ (0u - ((jb >> d) & 1u));
-                    const uint32_t t0 = c0 & u;
-                    c0 ^= u;
-                    const uint32_t t1 = c1 & t0;
-                    c1 ^= t0;
-                    c2 |= t1;
-                }
-                const int z = P.const_z ? P.const_z : (int)S.zdeg[p];
-                // m = z - 2u <= 0  <=>  u >= ceil(z/2): always accepted
-                flip = (z <= 4) ? (c2 | c1) : (c2 | (c1 & c0));
-                const uint32_t *thr = S.thr + 32 * g * 8;
-#pragma unroll
-                for (int b = 0; b < 32; ++b) {
-                    if (b < nbits) {
-                        if ((b & 3) == 0) philox10(site, t, (uint32_t)(32 * g + b) >> 2, inst, P.seed_lo, P.seed_hi, x);
-                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
-                        const int m = z - 2 * u;
-                        const uint32_t th = thr[b * 8 + (m > 0 ? m : 0)];
-                        flip |= (uint32_t)(x[b & 3] < th) << b;
-                        if (COLOR == 1) acc[b] += ((flip >> b) & 1u) ? m : -m;
+                        if (COLOR == 1) acc[8 * q + i] += a ? sh : -sh;
                     }
                 }
             }
-            sg[p] = sw ^ flip;
+        } else {
+            uint32_t c0 = 0, c1 = 0, c2 = 0;
+            const uint32_t jb = S.Jb[p];
+            int q[Z];
+            load_nbrs<Z>(S.nbr, p, q);
+#pragma unroll
+            for (int d = 0; d < Z; ++d) {
+                const uint32_t u = sw ^ sg[q[d]] ^ (0u - ((jb >> d) & 1u));
+                const uint32_t t0 = c0 & u;
+                c0 ^= u;
+                const uint32_t t1 = c1 & t0;
+                c1 ^= t0;
+                c2 |= t1;
+            }
+            const int z = P.const_z ? P.const_z : (int)S.zdeg[p];
+            // m = z - 2u <= 0  <=>  u >= ceil(z/2): always accepted
+            const uint32_t always = (z <= 4) ? (c2 | c1) : (c2 | (c1 & c0));
+            flip = always & (0xFFFFu << (16 * H));
+            const uint32_t *thr = S.thr + 32 * g * 8;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (q < npairs8) {
+                    uint32_t x[4], y[4];
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * q, inst, P.seed_lo, P.seed_hi, x, y);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int b = 16 * H + 8 * q + i;
+                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                        const int m = z - 2 * u;
+                        const uint32_t xr = i < 4 ? x[i] : y[i - 4];
+                        const uint32_t th = thr[b * 8 + (m > 0 ? m : 0)];
+                        flip |= (uint32_t)(xr < th) << b;
+                        if (COLOR == 1) acc[8 * q + i] += ((flip >> b) & 1u) ? m : -m;
+                    }
+                }
+            }
         }
-        if (COLOR == 1) {
-            const ET v = transpose_reduce(acc, lane);
-            if (lane < nbits) ((ET *)S.Epart)[warp * P.R + 32 * g + lane] = v;
-        }
+        sg[p] = sw ^ flip;
+    }
+    if (COLOR == 1) {
+        const ET v = transpose_reduce16(acc, lane);
+        const int r = rbase + (lane >> 1);
+        if (!(lane & 1) && r < P.R) ((ET *)S.Epart)[warp * P.R + r] = v;
+    }
+}
+
+template <bool GAUSS, int Z, int COLOR>
+__device__ __forceinline__ void half_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
+{
+    for (int g = 0; g < P.G; ++g) {
+        sweep_pass<GAUSS, Z, COLOR, 0>(P, S, t, inst, g);
+        if (32 * g + 16 < P.R) sweep_pass<GAUSS, Z, COLOR, 1>(P, S, t, inst, g);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Steps 2a and 2b for temperature position k, executed by one warp.
+// Steps 2a and 2b at every ICM temperature k < n_icm.
+//  (a) overlap masks of all pairs by warp ballots (bit 2k of s ^ (s >> 1)),
+//  (b) one thread per pair: n, the step-2a decision, the seed by rank,
+//  (c) every site word: reversal of copy 1 for the pairs that need it,
+//  (d) one warp per pair (taken dynamically): breadth-first growth of the
+//      seed's component of {q = -1}, flip in both copies by atomic XOR, and
+//      E_a's change from the cluster's boundary bonds (E_b changes by minus it).
 template <bool GAUSS, int Z>
-__device__ void cluster_move(const KParams &P, const Sm &S, int k, uint32_t t, uint32_t inst, int slot,
-                             bool trace)
+__device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int N = P.N, NW = P.NW;
-    const int ra = 2 * k, g = ra >> 5, ba = ra & 31;
-    uint32_t *sg = S.s + g * N;
-    uint32_t *mask = S.mask + warp * NW;
-    uint32_t *C = S.C + warp * NW;
-    uint16_t *queue = S.queue + warp * N;
-    int *tailp = S.tail + warp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int N = P.N, NW = P.NW, nicm = P.n_icm, G = P.G;
     ET *E = (ET *)S.E;
+    ICM_SUB_INIT();
 
-    // site overlap q_i = s_i^a s_i^b; bit set where q_i = -1
-    int n = 0;
-    for (int m = 0; m < NW; ++m) {
+    // (a) masks
+    for (int m = warp; m < NW; m += nwarps) {
         const int p = 32 * m + lane;
-        uint32_t bit = 0;
+        uint32_t q0 = 0, q1 = 0;
         if (p < N) {
-            const uint32_t w = sg[p];
-            bit = ((w >> ba) ^ (w >> (ba + 1))) & 1u;
+            const uint32_t w0 = S.s[p];
+            q0 = w0 ^ (w0 >> 1);
+            if (G > 1) {
+                const uint32_t w1 = S.s[N + p];
+                q1 = w1 ^ (w1 >> 1);
+            }
         }
-        const uint32_t word = __ballot_sync(kFull, bit);
-        if (lane == 0) mask[m] = word;
-        n += __popc(word);
-    }
-    const int n_pre = n;
-    const float esum_before = (float)(E[ra] + E[ra + 1]);
-    int flipped = 0;
-    __syncwarp();
-    if (P.enable_2a && 2 * n > N) {  // step 2a: reverse every spin of copy 1
-        for (int p = lane; p < N; p += 32) atomicXor(&sg[p], 1u << (ba + 1));
-        for (int m = lane; m < NW; m += 32) {
-            const int rem = N - 32 * m;
-            const uint32_t valid = rem >= 32 ? kFull : ((1u << rem) - 1u);
-            mask[m] = ~mask[m] & valid;
+        for (int k = 0; k < nicm; ++k) {
+            const uint32_t word = __ballot_sync(kFull, ((k < 16 ? q0 : q1) >> (2 * (k & 15))) & 1u);
+            if (lane == (k & 31)) S.mask[k * NW + m] = word;
         }
-        n = N - n;
-        flipped = 1;
     }
-    __syncwarp();
-    int seed = -1, csize = 0;
-    if (n > 0) {  // step 2b: one Houdayer move
-        if (lane == 0) {
+    if (tid < 2) S.flipw[tid] = 0u;
+    if (tid == 0) S.next_pair[0] = 0;
+    __syncthreads();
+
+    // (b) per pair: n, step 2a, seed
+    for (int k = tid; k < nicm; k += nth) {
+        uint32_t *Mk = S.mask + k * NW;
+        int n = 0;
+        for (int m = 0; m < NW; ++m) n += __popc(Mk[m]);
+        const int n_pre = n;
+        int flipped = 0;
+        if (P.enable_2a && 2 * n > N) {
+            for (int m = 0; m < NW; ++m) {
+                const int rem = N - 32 * m;
+                Mk[m] = ~Mk[m] & (rem >= 32 ? kFull : ((1u << rem) - 1u));
+            }
+            n = N - n;
+            flipped = 1;
+            atomicOr(&S.flipw[(2 * k + 1) >> 5], 1u << ((2 * k + 1) & 31));
+        }
+        int seed = -1;
+        if (n > 0) {
             uint32_t x[4];
             philox10((uint32_t)k, t, 0u, (1u << 24) | inst, P.seed_lo, P.seed_hi, x);
             uint32_t rank = (uint32_t)(((uint64_t)x[0] * (uint32_t)n) >> 32);
             for (int m = 0; m < NW; ++m) {
-                uint32_t w = mask[m];
+                uint32_t w = Mk[m];
                 const uint32_t c = (uint32_t)__popc(w);
                 if (rank < c) {
                     for (uint32_t r = 0; r < rank; ++r) w &= w - 1u;
@@ -307,77 +415,180 @@ __device__ void cluster_move(const KParams &P, const Sm &S, int k, uint32_t t, u
                 rank -= c;
             }
         }
-        seed = __shfl_sync(kFull, seed, 0);
-        if (seed < 0) n = 0;   // unreachable when the mask holds n set bits
-    }
-    if (n > 0) {
-        for (int m = lane; m < NW; m += 32) C[m] = 0u;
-        __syncwarp();
-        if (lane == 0) {
-            C[seed >> 5] = 1u << (seed & 31);
-            queue[0] = (uint16_t)seed;
-            *tailp = 1;
+        S.icm_seed[k] = seed;
+        if (trace) {
+            const size_t o = (size_t)slot * P.nT + k;
+            P.tr_n_pre[o] = n_pre;
+            P.tr_flip2a[o] = flipped;
+            P.tr_seed[o] = seed >= 0 ? (int)__ldg(P.pos2site + seed) : -1;
+            P.tr_csize[o] = 0;
+            P.tr_eb[o] = (float)(E[2 * k] + E[2 * k + 1]);
+            P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
         }
-        __syncwarp();
-        // breadth-first growth of the seed's component of {q = -1}
-        int head = 0, tail = 1;
-        while (head < tail) {
-            for (int idx = head + lane; idx < tail; idx += 32) {
-                const int p = queue[idx];
+    }
+    __syncthreads();
+
+    // (c) step 2a: reverse copy 1 of the flagged pairs in every site word
+    const uint32_t f0 = S.flipw[0], f1 = S.flipw[1];
+    if (f0 | f1) {
+        for (int p = tid; p < N; p += nth) {
+            S.s[p] ^= f0;
+            if (G > 1) S.s[N + p] ^= f1;
+        }
+        __syncthreads();
+    }
+
+    // (d) clusters of all pairs at once.  C[g][p] holds bit 2k when site p
+    // belongs to pair k's cluster; the domain of pair k is bit 2k of
+    // s ^ (s >> 1).  Each iteration sets C_p |= domain_p & OR(C of the
+    // neighbours) over every site (in place: bits are only ever set), until an
+    // iteration changes nothing.  The fixed point is the component of each seed.
+    uint32_t act0 = 0u, act1 = 0u;
+    for (int k = 0; k < nicm; ++k)
+        if (S.icm_seed[k] >= 0) {
+            if (k < 16) act0 |= 1u << (2 * k);
+            else act1 |= 1u << (2 * (k - 16));
+        }
+    if ((act0 | act1) == 0u) {
+        __syncthreads();
+        return;
+    }
+    for (int i = tid; i < G * N; i += nth) S.C[i] = 0u;
+    __syncthreads();
+    for (int k = tid; k < nicm; k += nth) {
+        const int seed = S.icm_seed[k];
+        if (seed >= 0) atomicOr(&S.C[(k >> 4) * N + seed], 1u << (2 * (k & 15)));
+    }
+    __syncthreads();
+    ICM_SUB(8);
+    // Rounds over every site not yet absorbed (C != domain): C_p |= dom_p &
+    // OR(C of the neighbours), in place (bits are only ever set), until a
+    // round changes nothing.
+    int rounds = 0;
+    if (N <= 4 * nth) {
+        // each thread keeps its (at most 4) sites' neighbours, domains and
+        // cluster words in registers across rounds
+        int qn[4][Z];
+        uint32_t dom[4][2], cl[4][2];
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const int q = S.nbr[p * Z + d];
-                    const uint32_t bq = 1u << (q & 31);
-                    if (mask[q >> 5] & bq) {
-                        const uint32_t old = atomicOr(&C[q >> 5], bq);
-                        if (!(old & bq)) queue[atomicAdd(tailp, 1)] = (uint16_t)q;
+        for (int j = 0; j < 4; ++j) {
+            const int p = tid + j * nth;
+            const bool ok = p < N;
+            load_nbrs<Z>(S.nbr, ok ? p : 0, qn[j]);
+#pragma unroll
+            for (int g = 0; g < 2; ++g) {
+                uint32_t dm = 0u, c = 0u;
+                if (ok && g < G) {
+                    const uint32_t w = S.s[g * N + p];
+                    dm = (w ^ (w >> 1)) & (g ? act1 : act0);
+                    c = S.C[g * N + p];
+                }
+                dom[j][g] = dm;
+                cl[j][g] = c;
+            }
+        }
+        int grew;
+        do {
+            grew = 0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    if (dom[j][g] == cl[j][g]) continue;
+                    const uint32_t *Cg = S.C + g * N;
+                    uint32_t nb = 0u;
+#pragma unroll
+                    for (int d = 0; d < Z; ++d) nb |= Cg[qn[j][d]];
+                    const uint32_t nc = cl[j][g] | (dom[j][g] & nb);
+                    if (nc != cl[j][g]) {
+                        cl[j][g] = nc;
+                        S.C[g * N + tid + j * nth] = nc;
+                        grew = 1;
                     }
                 }
             }
-            __syncwarp();
-            head = tail;
-            tail = *(volatile int *)tailp;
-            __syncwarp();
-        }
-        csize = tail;
-        // flip the cluster in both copies; boundary bonds give E_a's change
-        ET delta = ET(0);
+            ++rounds;
+        } while (__syncthreads_or(grew));
+    } else {
+        int grew;
+        do {
+            grew = 0;
+            for (int g = 0; g < G; ++g) {
+                const uint32_t ag = g ? act1 : act0;
+                uint32_t *Cg = S.C + g * N;
+                for (int p = tid; p < N; p += nth) {
+                    const uint32_t w = S.s[g * N + p];
+                    const uint32_t dm = (w ^ (w >> 1)) & ag;
+                    const uint32_t c = Cg[p];
+                    if (dm == c) continue;
+                    int q[Z];
+                    load_nbrs<Z>(S.nbr, p, q);
+                    uint32_t nb = 0u;
+#pragma unroll
+                    for (int d = 0; d < Z; ++d) nb |= Cg[q[d]];
+                    const uint32_t nc = c | (dm & nb);
+                    if (nc != c) {
+                        Cg[p] = nc;
+                        grew = 1;
+                    }
+                }
+            }
+            ++rounds;
+        } while (__syncthreads_or(grew));
+    }
+#ifdef ICM_PHASE_TIMERS
+    if (tid == 0) atomicAdd(&g_icm_phase_cycles[11], (unsigned long long)rounds);
+#endif
+    ICM_SUB(9);
+
+    // (e) flip every cluster in both copies (bits 2k and 2k+1)
+    for (int i = tid; i < G * N; i += nth) {
+        const uint32_t c = S.C[i];
+        if (c) S.s[i] ^= c | (c << 1);
+    }
+    __syncthreads();
+    // one warp per pair: E_a changes by 2 J s_p s_q (pre-flip) over the
+    // cluster's boundary bonds (p inside, q outside the domain); E_b by minus it
+    for (int k = warp; k < nicm; k += nwarps) {
+        if (S.icm_seed[k] < 0) continue;
+        const int g = k >> 4, bit = 2 * (k & 15);
+        const uint32_t *sg = S.s + g * N, *Cg = S.C + g * N;
+        ET acc = ET(0);
+        int size = 0;
         for (int m = 0; m < NW; ++m) {
             const int p = 32 * m + lane;
-            if (p < N && ((C[m] >> lane) & 1u)) {
-                const uint32_t old = atomicXor(&sg[p], 3u << ba);
-                const uint32_t ap = (old >> ba) & 1u;
+            const bool in = p < N && ((Cg[p] >> bit) & 1u);
+            size += __popc(__ballot_sync(kFull, in));
+            if (!in) continue;
+            const uint32_t ap = ((sg[p] >> bit) & 1u) ^ 1u;   // copy-a spin of p before the flip
+            int q[Z];
+            load_nbrs<Z>(S.nbr, p, q);
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const int q = S.nbr[p * Z + d];
-                    if ((mask[q >> 5] >> (q & 31)) & 1u) continue;  // inside the domain (or padding)
-                    const uint32_t aq = (sg[q] >> ba) & 1u;
-                    if constexpr (GAUSS) {
-                        const float J = S.Jd[p * Z + d];
-                        delta += (ap ^ aq) ? -2.f * J : 2.f * J;
-                    } else {
-                        const uint32_t jneg = (S.Jb[p] >> d) & 1u;
-                        delta += (jneg ^ ap ^ aq) ? -2 : 2;
-                    }
+            for (int d = 0; d < Z; ++d) {
+                const uint32_t wq = sg[q[d]];
+                if (((wq ^ (wq >> 1)) >> bit) & 1u) continue;   // q in the domain (padding: q = p)
+                const uint32_t aq = (wq >> bit) & 1u;
+                if constexpr (GAUSS) {
+                    const float J = S.Jd[p * Z + d];
+                    acc += (ap ^ aq) ? -2.f * J : 2.f * J;
+                } else {
+                    acc += (((S.Jb[p] >> d) & 1u) ^ ap ^ aq) ? -2 : 2;
                 }
             }
         }
-        delta = warp_sum_lane0(delta);
+        acc = warp_sum_lane0(acc);
         if (lane == 0) {
-            E[ra] += delta;
-            E[ra + 1] -= delta;
+            E[2 * k] += acc;
+            E[2 * k + 1] -= acc;
+            if (trace) {
+                const size_t o = (size_t)slot * P.nT + k;
+                P.tr_csize[o] = size;
+                P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
+            }
         }
     }
-    __syncwarp();
-    if (trace && lane == 0) {
-        const size_t o = (size_t)slot * P.nT + k;
-        P.tr_n_pre[o] = n_pre;
-        P.tr_flip2a[o] = flipped;
-        P.tr_seed[o] = seed >= 0 ? (int)S.pos2site[seed] : -1;
-        P.tr_csize[o] = csize;
-        P.tr_eb[o] = esum_before;
-        P.tr_ea[o] = (float)(E[ra] + E[ra + 1]);
-    }
+    __syncthreads();
+    ICM_SUB(10);
 }
 
 // ---------------------------------------------------------------------------
@@ -473,9 +684,11 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
         for (int p = half + threadIdx.x; p < N; p += blockDim.x) {
             const uint32_t w = sg[p];
             const uint32_t qp = (w ^ (w >> 1)) & 0x55555555u;
+            int qn[Z];
+            load_nbrs<Z>(S.nbr, p, qn);
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                const int q = S.nbr[p * Z + d];
+                const int q = qn[d];
                 if (q == p) continue;
                 const uint32_t wq = sg[q];
                 vadd(pd, qp ^ ((wq ^ (wq >> 1)) & 0x55555555u));
@@ -509,23 +722,22 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
 
 // ---------------------------------------------------------------------------
 template <bool GAUSS, int Z>
-__global__ void __launch_bounds__(kMaxThreads, 4) fused_kernel(const KParams P, uint32_t n_sweeps)
+__global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, uint32_t n_sweeps)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     const Sm S = make_sm(smem, P.sm);
-    const int tid = threadIdx.x, nth = blockDim.x, nwarps = nth >> 5, warp = tid >> 5;
+    PHASE_INIT();
+    const int tid = threadIdx.x, nth = blockDim.x, nwarps = nth >> 5;
     const int N = P.N, R = P.R, nT = P.nT, G = P.G;
 
     for (int i = tid; i < N * Z; i += nth) S.nbr[i] = P.nbr[i];
-    for (int i = tid; i < N; i += nth) {
-        S.pos2site[i] = P.pos2site[i];
-        if (!GAUSS && !P.const_z) S.zdeg[i] = P.zdeg[i];
-    }
+    if (!GAUSS && !P.const_z)
+        for (int i = tid; i < N; i += nth) S.zdeg[i] = P.zdeg[i];
     if constexpr (GAUSS) {
-        for (int r = tid; r < R; r += nth) S.b2l[r] = P.b2l[r];
+        for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
     } else {
-        for (int i = tid; i < R * 8; i += nth) S.thr[i] = P.thr_metro[i];
+        for (int i = tid; i < 32 * G * 8; i += nth) S.thr[i] = i < R * 8 ? P.thr_metro[i] : 0u;
     }
     if (tid < 32) {
         S.cnt_n[tid] = 0;
@@ -553,6 +765,7 @@ __global__ void __launch_bounds__(kMaxThreads, 4) fused_kernel(const KParams P, 
         uint32_t t = P.tsweep[slot];
         __syncthreads();
 
+        PHASE_MARK(5);
         for (uint32_t step = 0; step < n_sweeps; ++step, ++t) {
             const bool trace = P.trace && step + 1 == n_sweeps;
             if (trace) {
@@ -580,15 +793,18 @@ __global__ void __launch_bounds__(kMaxThreads, 4) fused_kernel(const KParams P, 
                 }
                 __syncthreads();
             }
-            if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0) {  // steps 2a, 2b
-                for (int k = warp; k < P.n_icm; k += nwarps) cluster_move<GAUSS, Z>(P, S, k, t, inst, slot, trace);
-                __syncthreads();
-            }
+            PHASE_MARK(0);
+            if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)  // steps 2a, 2b
+                cluster_moves<GAUSS, Z>(P, S, t, inst, slot, trace);
+            PHASE_MARK(1);
             if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1)  // step 3
                 pt_pass<GAUSS>(P, S, t, inst, slot, trace);
+            PHASE_MARK(2);
             if ((long long)t >= P.t_meas) measure<GAUSS, Z>(P, S, slot);
+            PHASE_MARK(3);
         }
 
+        PHASE_MARK(4);
         uint32_t *gd = P.spins + (size_t)slot * G * N;
         for (int i = tid; i < G * N; i += nth) gd[i] = S.s[i];
         for (int r = tid; r < R; r += nth) {
@@ -604,7 +820,9 @@ __global__ void __launch_bounds__(kMaxThreads, 4) fused_kernel(const KParams P, 
             P.tsweep[slot] = t;
         }
         __syncthreads();
+        PHASE_MARK(5);
     }
+    PHASE_FLUSH();
 }
 
 // ---------------------------------------------------------------------------
@@ -746,7 +964,7 @@ cudaError_t occupancy_t(int threads, int smem, int *ctas)
 // ---------------------------------------------------------------------------
 static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
-SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int nwarps, bool gauss)
+SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss)
 {
     SmemLayout L{};
     const int NW = (N + 31) / 32;
@@ -761,17 +979,17 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int nwarps, bool gaus
     L.spins = take(G * N * 4, 16);
     L.nbr = take(N * Z * 2, 16);
     L.zdeg = take(N, 16);
-    L.pos2site = take(N * 2, 16);
     L.E = take(R * 4, 16);
     L.Epart = take(nwarps * R * 4, 16);
-    L.rtab = take(gauss ? R * 4 : R * 8 * 4, 16);
-    L.icm_mask = take(nwarps * NW * 4, 16);
-    L.icm_C = take(nwarps * NW * 4, 16);
-    L.icm_queue = take(nwarps * N * 2, 16);
-    L.icm_tail = take(nwarps * 4, 16);
+    L.rtab = take(gauss ? G * 32 * 4 : G * 32 * 8 * 4, 16);   // every bit of the G words
+    L.icm_mask = take(n_icm * NW * 4, 16);
+    L.icm_C = take(G * N * 4, 16);
     L.swap_x = take(2 * 32 * 4, 16);
     L.swap_list = take(2 * 32 * 4, 16);
     L.swap_n = take(2 * 4, 16);
+    L.flipw = take(2 * 4, 16);
+    L.icm_seed = take(32 * 4, 16);
+    L.next_pair = take(4, 16);
     L.cnt_n = take(32 * 4, 16);
     L.cnt_d = take(32 * 4, 16);
     L.accE = take(nT * 8, 16);
@@ -848,3 +1066,17 @@ cudaError_t launch_energies_to_double(const KParams &P, bool gauss, double *out,
 }
 
 }  // namespace icm
+
+#ifdef ICM_PHASE_TIMERS
+// Cycles per phase summed over CTAs: 0 sweep + energies, 1 ICM, 2 PT, 3 observables,
+// 4 between the last step and the store, 5 load/store and instance changes.
+extern "C" int icm_debug_phase_cycles(unsigned long long *out, int reset)
+{
+    if (cudaMemcpyFromSymbol(out, g_icm_phase_cycles, sizeof(unsigned long long) * 16) != cudaSuccess) return -4;
+    if (reset) {
+        unsigned long long z[16] = {};
+        if (cudaMemcpyToSymbol(g_icm_phase_cycles, z, sizeof(z)) != cudaSuccess) return -4;
+    }
+    return 0;
+}
+#endif
