@@ -433,6 +433,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     icm::KParams &P = b->kp;
     P.N = N; P.Nb = g.Nb; P.nT = n_T; P.R = R; P.G = G; P.Z = Z; P.n_inst = n_inst; P.n_icm = n_icm;
     P.half = half; P.NW = (N + 31) / 32; P.const_z = uniform ? Z : 0;
+    P.small_counts = (((half + threads - 1) / threads) * Z < 16 && (N + threads - 1) / threads < 16) ? 1 : 0;
     P.seed_lo = (uint32_t)(seed & 0xffffffffu);
     P.seed_hi = (uint32_t)(seed >> 32);
     P.sm = sm;

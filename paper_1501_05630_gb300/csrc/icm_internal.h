@@ -18,7 +18,7 @@ struct SmemLayout {
     int zdeg;       // uint8  [N]      degree (+-J only)
     int coup;       // float [N][Z] (Gaussian) or uint8 [N] bit d = (J < 0) (+-J)
     int E;          // float or int32 [R]
-    int Epart;      // float or int32 [nwarps][R]
+    int Epart;      // float or int32 [nwarps][max(R, 32)]
     int rtab;       // uint32 [R][8] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
     int icm_mask;   // uint32 [n_icm][NW] overlap masks per ICM pair
     int icm_C;      // uint32 [G][N]     cluster bits (bit 2k: site in pair k's cluster)
@@ -27,7 +27,7 @@ struct SmemLayout {
     int swap_n;     // int32 [2]
     int flipw;      // uint32 [2]      step-2a reversal masks of the two words
     int icm_seed;   // int32 [32]      seed position per ICM pair (-1: none)
-    int next_pair;  // int32 [1]       dynamic pair counter
+    int icm_esum;   // float or int32 [32]  E_a + E_b of each ICM pair before the move
     int cnt_n;      // int32 [32]
     int cnt_d;      // int32 [32]
     int accE;       // double [nT]
@@ -40,6 +40,7 @@ struct SmemLayout {
 struct KParams {
     int N, Nb, nT, R, G, Z, n_inst, n_icm, half, NW;
     int const_z;                  // degree when uniform (lattices), 0 = per-site table
+    int small_counts;             // per-thread observable counts fit 4 bit-planes
     // geometry, shared by all instances of the batch
     const uint16_t *nbr;          // [N][Z]
     const uint8_t *zdeg;          // [N]

@@ -147,22 +147,24 @@ __device__ __forceinline__ T warp_sum_lane0(T v)
     return v;
 }
 
-// Add one word to 8 bit-planes of per-bit counters.
-__device__ __forceinline__ void vadd(uint32_t (&pl)[kPlanes], uint32_t w)
+// Add one word to NPL bit-planes of per-bit counters (vertical counters).
+template <int NPL>
+__device__ __forceinline__ void vadd(uint32_t (&pl)[NPL], uint32_t w)
 {
 #pragma unroll
-    for (int i = 0; i < kPlanes; ++i) {
+    for (int i = 0; i < NPL; ++i) {
         const uint32_t c = pl[i] & w;
         pl[i] ^= w;
         w = c;
     }
 }
 
-__device__ __forceinline__ int vget(const uint32_t (&pl)[kPlanes], int bit)
+template <int NPL>
+__device__ __forceinline__ int vget(const uint32_t (&pl)[NPL], int bit)
 {
     int v = 0;
 #pragma unroll
-    for (int i = 0; i < kPlanes; ++i) v |= (int)((pl[i] >> bit) & 1u) << i;
+    for (int i = 0; i < NPL; ++i) v |= (int)((pl[i] >> bit) & 1u) << i;
     return v;
 }
 
@@ -183,7 +185,7 @@ struct Sm {
     int *swap_n;
     uint32_t *flipw;
     int *icm_seed;
-    int *next_pair;
+    void *icm_esum_raw;
     int *cnt_n;
     int *cnt_d;
     double *accE;
@@ -210,7 +212,7 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.swap_n = (int *)(base + L.swap_n);
     S.flipw = (uint32_t *)(base + L.flipw);
     S.icm_seed = (int *)(base + L.icm_seed);
-    S.next_pair = (int *)(base + L.next_pair);
+    S.icm_esum_raw = base + L.icm_esum;
     S.cnt_n = (int *)(base + L.cnt_n);
     S.cnt_d = (int *)(base + L.cnt_d);
     S.accE = (double *)(base + L.accE);
@@ -345,13 +347,83 @@ __device__ __forceinline__ void half_sweep(const KParams &P, const Sm &S, uint32
 }
 
 // ---------------------------------------------------------------------------
+// Energies of the copy-a replicas (bit 2k) of the pairs flagged in act0/act1,
+// from the spins: +-J via bit-sliced unsatisfied-bond counts (E = 2U - N_b),
+// Gaussian via per-bit fp32 local fields; summed in a fixed order.  Every
+// thread ends with partial sums in S.Epart[warp][k]; the caller adds warps.
+template <bool GAUSS, int Z>
+__device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uint32_t act0, uint32_t act1)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int N = P.N, half = P.half, nth = blockDim.x;
+    ET *part = (ET *)S.Epart;
+    for (int g = 0; g < P.G; ++g) {
+        const uint32_t act = g ? act1 : act0;
+        if (!act) continue;                      // uniform
+        const uint32_t *sg = S.s + g * N;
+        ET acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = ET(0);
+        for (int i = threadIdx.x; i < half; i += nth) {
+            const int p = half + i;              // colour-1 sites: every bond once
+            const uint32_t sw = sg[p];
+            int q[Z];
+            load_nbrs<Z>(S.nbr, p, q);
+            if constexpr (GAUSS) {
+                float Jv[Z];
+                uint32_t nw[Z];
+#pragma unroll
+                for (int d = 0; d < Z; ++d) {
+                    nw[d] = sg[q[d]];
+                    Jv[d] = S.Jd[p * Z + d];
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    if (!((act >> (2 * j)) & 1u)) continue;   // uniform
+                    const int b = 2 * j;
+                    float h = 0.f;
+#pragma unroll
+                    for (int d = 0; d < Z; ++d)
+                        h += __uint_as_float(__float_as_uint(Jv[d]) ^ ((nw[d] << (31 - b)) & 0x80000000u));
+                    // e = -s_p h_p
+                    acc[j] -= __uint_as_float(__float_as_uint(h) ^ ((sw << (31 - b)) & 0x80000000u));
+                }
+            } else {
+                uint32_t c0 = 0, c1 = 0, c2 = 0;
+                const uint32_t jb = S.Jb[p];
+#pragma unroll
+                for (int d = 0; d < Z; ++d) {
+                    const uint32_t u = sw ^ sg[q[d]] ^ (0u - ((jb >> d) & 1u));
+                    const uint32_t t0 = c0 & u;
+                    c0 ^= u;
+                    const uint32_t t1 = c1 & t0;
+                    c1 ^= t0;
+                    c2 |= t1;
+                }
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int b = 2 * j;
+                    acc[j] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                }
+            }
+        }
+        const ET v = transpose_reduce16(acc, lane);
+        if (!(lane & 1)) part[warp * 32 + 16 * g + (lane >> 1)] = v;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Steps 2a and 2b at every ICM temperature k < n_icm.
-//  (a) overlap masks of all pairs by warp ballots (bit 2k of s ^ (s >> 1)),
-//  (b) one thread per pair: n, the step-2a decision, the seed by rank,
-//  (c) every site word: reversal of copy 1 for the pairs that need it,
-//  (d) one warp per pair (taken dynamically): breadth-first growth of the
-//      seed's component of {q = -1}, flip in both copies by atomic XOR, and
-//      E_a's change from the cluster's boundary bonds (E_b changes by minus it).
+//  (a) overlap masks of all pairs by warp ballots (bit 2k of s ^ (s >> 1));
+//  (b) one thread per pair: n, the step-2a decision, the seed by rank;
+//  (c) copy-1 reversal of the flagged pairs, then the clusters of all pairs
+//      at once: C_p (bit 2k = site p in pair k's cluster) grows by
+//      C_p |= domain_p & OR(C of the neighbours) in rounds until a round
+//      changes nothing -- the fixed point is each seed's connected component
+//      of {q = -1};
+//  (d) flip in both copies (bits 2k, 2k+1 of C_p | C_p << 1), then E_a from
+//      the spins and E_b = (E_a + E_b)_before - E_a (the move is isoenergetic).
 template <bool GAUSS, int Z>
 __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
 {
@@ -360,9 +432,10 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     const int tid = threadIdx.x, nth = blockDim.x;
     const int N = P.N, NW = P.NW, nicm = P.n_icm, G = P.G;
     ET *E = (ET *)S.E;
+    ET *esum = (ET *)S.icm_esum_raw;
     ICM_SUB_INIT();
 
-    // (a) masks
+    // (a) masks; clear the cluster words
     for (int m = warp; m < NW; m += nwarps) {
         const int p = 32 * m + lane;
         uint32_t q0 = 0, q1 = 0;
@@ -379,11 +452,11 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             if (lane == (k & 31)) S.mask[k * NW + m] = word;
         }
     }
+    for (int i = tid; i < G * N; i += nth) S.C[i] = 0u;
     if (tid < 2) S.flipw[tid] = 0u;
-    if (tid == 0) S.next_pair[0] = 0;
     __syncthreads();
 
-    // (b) per pair: n, step 2a, seed
+    // (b) per pair: n, step 2a, seed (planted into C)
     for (int k = tid; k < nicm; k += nth) {
         uint32_t *Mk = S.mask + k * NW;
         int n = 0;
@@ -414,8 +487,10 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                 }
                 rank -= c;
             }
+            atomicOr(&S.C[(k >> 4) * N + seed], 1u << (2 * (k & 15)));
         }
         S.icm_seed[k] = seed;
+        esum[k] = E[2 * k] + E[2 * k + 1];
         if (trace) {
             const size_t o = (size_t)slot * P.nT + k;
             P.tr_n_pre[o] = n_pre;
@@ -427,167 +502,151 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         }
     }
     __syncthreads();
+    ICM_SUB(8);
 
-    // (c) step 2a: reverse copy 1 of the flagged pairs in every site word
-    const uint32_t f0 = S.flipw[0], f1 = S.flipw[1];
-    if (f0 | f1) {
-        for (int p = tid; p < N; p += nth) {
-            S.s[p] ^= f0;
-            if (G > 1) S.s[N + p] ^= f1;
-        }
-        __syncthreads();
-    }
-
-    // (d) clusters of all pairs at once.  C[g][p] holds bit 2k when site p
-    // belongs to pair k's cluster; the domain of pair k is bit 2k of
-    // s ^ (s >> 1).  Each iteration sets C_p |= domain_p & OR(C of the
-    // neighbours) over every site (in place: bits are only ever set), until an
-    // iteration changes nothing.  The fixed point is the component of each seed.
+    // (c) which pairs move, then copy-1 reversal and cluster growth
     uint32_t act0 = 0u, act1 = 0u;
     for (int k = 0; k < nicm; ++k)
         if (S.icm_seed[k] >= 0) {
             if (k < 16) act0 |= 1u << (2 * k);
             else act1 |= 1u << (2 * (k - 16));
         }
-    if ((act0 | act1) == 0u) {
-        __syncthreads();
-        return;
-    }
-    for (int i = tid; i < G * N; i += nth) S.C[i] = 0u;
-    __syncthreads();
-    for (int k = tid; k < nicm; k += nth) {
-        const int seed = S.icm_seed[k];
-        if (seed >= 0) atomicOr(&S.C[(k >> 4) * N + seed], 1u << (2 * (k & 15)));
-    }
-    __syncthreads();
-    ICM_SUB(8);
-    // Rounds over every site not yet absorbed (C != domain): C_p |= dom_p &
-    // OR(C of the neighbours), in place (bits are only ever set), until a
-    // round changes nothing.
+    const uint32_t f0 = S.flipw[0], f1 = S.flipw[1];
     int rounds = 0;
     if (N <= 4 * nth) {
-        // each thread keeps its (at most 4) sites' neighbours, domains and
-        // cluster words in registers across rounds
-        int qn[4][Z];
-        uint32_t dom[4][2], cl[4][2];
+        // each thread owns sites tid + j nth (j < 4) and keeps their
+        // neighbours, domains and cluster words in registers across rounds
+        uint32_t qn[4][Z / 2];                 // neighbour positions, two per register
+        uint32_t todo = 0u;                    // bit 2j+g: site j, word g not yet absorbed
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = tid + j * nth;
             const bool ok = p < N;
-            load_nbrs<Z>(S.nbr, ok ? p : 0, qn[j]);
+            const uint32_t *row = (const uint32_t *)(S.nbr + (ok ? p : 0) * Z);
+#pragma unroll
+            for (int i = 0; i < Z / 2; ++i) qn[j][i] = row[i];
 #pragma unroll
             for (int g = 0; g < 2; ++g) {
                 uint32_t dm = 0u, c = 0u;
                 if (ok && g < G) {
-                    const uint32_t w = S.s[g * N + p];
+                    const uint32_t w = S.s[g * N + p] ^ (g ? f1 : f0);   // step 2a
+                    S.s[g * N + p] = w;
                     dm = (w ^ (w >> 1)) & (g ? act1 : act0);
                     c = S.C[g * N + p];
                 }
-                dom[j][g] = dm;
-                cl[j][g] = c;
+                if (dm != c) todo |= 1u << (2 * j + g);
             }
         }
-        int grew;
-        do {
-            grew = 0;
+        if (act0 | act1) {
+            int grew;
+            do {
+                grew = 0;
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
+                for (int j = 0; j < 4; ++j) {
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {
+                        if (!((todo >> (2 * j + g)) & 1u)) continue;
+                        const uint32_t *Cg = S.C + g * N;
+                        const uint32_t w = S.s[g * N + tid + j * nth];
+                        const uint32_t dm = (w ^ (w >> 1)) & (g ? act1 : act0);
+                        uint32_t nb = 0u;
+#pragma unroll
+                        for (int i = 0; i < Z / 2; ++i) nb |= Cg[qn[j][i] & 0xffffu] | Cg[qn[j][i] >> 16];
+                        const uint32_t c = S.C[g * N + tid + j * nth];   // written only by this thread
+                        const uint32_t nc = c | (dm & nb);
+                        if (nc != c) {
+                            S.C[g * N + tid + j * nth] = nc;
+                            grew = 1;
+                            if (nc == dm) todo &= ~(1u << (2 * j + g));
+                        }
+                    }
+                }
+                ++rounds;
+            } while (__syncthreads_or(grew));
+            // (d) flip the owned sites
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
-                    if (dom[j][g] == cl[j][g]) continue;
-                    const uint32_t *Cg = S.C + g * N;
-                    uint32_t nb = 0u;
-#pragma unroll
-                    for (int d = 0; d < Z; ++d) nb |= Cg[qn[j][d]];
-                    const uint32_t nc = cl[j][g] | (dom[j][g] & nb);
-                    if (nc != cl[j][g]) {
-                        cl[j][g] = nc;
-                        S.C[g * N + tid + j * nth] = nc;
-                        grew = 1;
+                    const int i = g * N + tid + j * nth;
+                    if (g < G && tid + j * nth < N) {
+                        const uint32_t c = S.C[i];
+                        if (c) S.s[i] ^= c | (c << 1);
                     }
                 }
-            }
-            ++rounds;
-        } while (__syncthreads_or(grew));
+        }
     } else {
-        int grew;
-        do {
-            grew = 0;
-            for (int g = 0; g < G; ++g) {
-                const uint32_t ag = g ? act1 : act0;
-                uint32_t *Cg = S.C + g * N;
-                for (int p = tid; p < N; p += nth) {
-                    const uint32_t w = S.s[g * N + p];
-                    const uint32_t dm = (w ^ (w >> 1)) & ag;
-                    const uint32_t c = Cg[p];
-                    if (dm == c) continue;
-                    int q[Z];
-                    load_nbrs<Z>(S.nbr, p, q);
-                    uint32_t nb = 0u;
+        for (int p = tid; p < N; p += nth) {
+            S.s[p] ^= f0;
+            if (G > 1) S.s[N + p] ^= f1;
+        }
+        __syncthreads();
+        if (act0 | act1) {
+            int grew;
+            do {
+                grew = 0;
+                for (int g = 0; g < G; ++g) {
+                    const uint32_t ag = g ? act1 : act0;
+                    uint32_t *Cg = S.C + g * N;
+                    for (int p = tid; p < N; p += nth) {
+                        const uint32_t w = S.s[g * N + p];
+                        const uint32_t dm = (w ^ (w >> 1)) & ag;
+                        const uint32_t c = Cg[p];
+                        if (dm == c) continue;
+                        int q[Z];
+                        load_nbrs<Z>(S.nbr, p, q);
+                        uint32_t nb = 0u;
 #pragma unroll
-                    for (int d = 0; d < Z; ++d) nb |= Cg[q[d]];
-                    const uint32_t nc = c | (dm & nb);
-                    if (nc != c) {
-                        Cg[p] = nc;
-                        grew = 1;
+                        for (int d = 0; d < Z; ++d) nb |= Cg[q[d]];
+                        const uint32_t nc = c | (dm & nb);
+                        if (nc != c) {
+                            Cg[p] = nc;
+                            grew = 1;
+                        }
                     }
                 }
+                ++rounds;
+            } while (__syncthreads_or(grew));
+            for (int i = tid; i < G * N; i += nth) {
+                const uint32_t c = S.C[i];
+                if (c) S.s[i] ^= c | (c << 1);
             }
-            ++rounds;
-        } while (__syncthreads_or(grew));
+        }
     }
 #ifdef ICM_PHASE_TIMERS
     if (tid == 0) atomicAdd(&g_icm_phase_cycles[11], (unsigned long long)rounds);
 #endif
     ICM_SUB(9);
-
-    // (e) flip every cluster in both copies (bits 2k and 2k+1)
-    for (int i = tid; i < G * N; i += nth) {
-        const uint32_t c = S.C[i];
-        if (c) S.s[i] ^= c | (c << 1);
+    if (!(act0 | act1)) {
+        __syncthreads();
+        return;
+    }
+    if (trace) {
+        // cluster sizes: counted once per cluster site
+        for (int i = tid; i < G * N; i += nth) {
+            const uint32_t c = S.C[i];
+            for (uint32_t b = c; b; b &= b - 1u) atomicAdd(&S.cnt_d[16 * (i / N) + ((__ffs(b) - 1) >> 1)], 1);
+        }
     }
     __syncthreads();
-    // one warp per pair: E_a changes by 2 J s_p s_q (pre-flip) over the
-    // cluster's boundary bonds (p inside, q outside the domain); E_b by minus it
-    for (int k = warp; k < nicm; k += nwarps) {
+    pair_energies<GAUSS, Z>(P, S, act0, act1);
+    __syncthreads();
+    for (int k = tid; k < nicm; k += nth) {
         if (S.icm_seed[k] < 0) continue;
-        const int g = k >> 4, bit = 2 * (k & 15);
-        const uint32_t *sg = S.s + g * N, *Cg = S.C + g * N;
-        ET acc = ET(0);
-        int size = 0;
-        for (int m = 0; m < NW; ++m) {
-            const int p = 32 * m + lane;
-            const bool in = p < N && ((Cg[p] >> bit) & 1u);
-            size += __popc(__ballot_sync(kFull, in));
-            if (!in) continue;
-            const uint32_t ap = ((sg[p] >> bit) & 1u) ^ 1u;   // copy-a spin of p before the flip
-            int q[Z];
-            load_nbrs<Z>(S.nbr, p, q);
-#pragma unroll
-            for (int d = 0; d < Z; ++d) {
-                const uint32_t wq = sg[q[d]];
-                if (((wq ^ (wq >> 1)) >> bit) & 1u) continue;   // q in the domain (padding: q = p)
-                const uint32_t aq = (wq >> bit) & 1u;
-                if constexpr (GAUSS) {
-                    const float J = S.Jd[p * Z + d];
-                    acc += (ap ^ aq) ? -2.f * J : 2.f * J;
-                } else {
-                    acc += (((S.Jb[p] >> d) & 1u) ^ ap ^ aq) ? -2 : 2;
-                }
-            }
-        }
-        acc = warp_sum_lane0(acc);
-        if (lane == 0) {
-            E[2 * k] += acc;
-            E[2 * k + 1] -= acc;
-            if (trace) {
-                const size_t o = (size_t)slot * P.nT + k;
-                P.tr_csize[o] = size;
-                P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
-            }
+        ET ea = ET(0);
+        for (int w = 0; w < nwarps; ++w) ea += ((const ET *)S.Epart)[w * 32 + k];
+        if constexpr (!GAUSS) ea = 2 * ea - P.Nb;            // E = 2 U - N_b
+        E[2 * k] = ea;
+        E[2 * k + 1] = esum[k] - ea;
+        if (trace) {
+            const size_t o = (size_t)slot * P.nT + k;
+            P.tr_csize[o] = S.cnt_d[k];
+            P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
         }
     }
     __syncthreads();
+    if (trace)
+        for (int k = tid; k < 32; k += nth) S.cnt_d[k] = 0;
     ICM_SUB(10);
 }
 
@@ -665,7 +724,7 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
 
 // ---------------------------------------------------------------------------
 // Observables: per pair k, n = #{q_i = -1} and d = #{bonds, q_i q_j = -1}.
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, int NPL>
 __device__ void measure(const KParams &P, const Sm &S, int slot)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
@@ -674,9 +733,9 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
     for (int g = 0; g < P.G; ++g) {
         const int npair = min(16, nT - 16 * g);
         const uint32_t *sg = S.s + g * N;
-        uint32_t pn[kPlanes], pd[kPlanes];
+        uint32_t pn[NPL], pd[NPL];
 #pragma unroll
-        for (int i = 0; i < kPlanes; ++i) pn[i] = pd[i] = 0u;
+        for (int i = 0; i < NPL; ++i) pn[i] = pd[i] = 0u;
         for (int p = threadIdx.x; p < N; p += blockDim.x) {
             const uint32_t w = sg[p];
             vadd(pn, (w ^ (w >> 1)) & 0x55555555u);
@@ -800,7 +859,10 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
             if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1)  // step 3
                 pt_pass<GAUSS>(P, S, t, inst, slot, trace);
             PHASE_MARK(2);
-            if ((long long)t >= P.t_meas) measure<GAUSS, Z>(P, S, slot);
+            if ((long long)t >= P.t_meas) {
+                if (P.small_counts) measure<GAUSS, Z, 4>(P, S, slot);   // every per-thread count < 16
+                else measure<GAUSS, Z, kPlanes>(P, S, slot);
+            }
             PHASE_MARK(3);
         }
 
@@ -980,7 +1042,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.nbr = take(N * Z * 2, 16);
     L.zdeg = take(N, 16);
     L.E = take(R * 4, 16);
-    L.Epart = take(nwarps * R * 4, 16);
+    L.Epart = take(nwarps * (R > 32 ? R : 32) * 4, 16);
     L.rtab = take(gauss ? G * 32 * 4 : G * 32 * 8 * 4, 16);   // every bit of the G words
     L.icm_mask = take(n_icm * NW * 4, 16);
     L.icm_C = take(G * N * 4, 16);
@@ -989,7 +1051,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.swap_n = take(2 * 4, 16);
     L.flipw = take(2 * 4, 16);
     L.icm_seed = take(32 * 4, 16);
-    L.next_pair = take(4, 16);
+    L.icm_esum = take(32 * 4, 16);
     L.cnt_n = take(32 * 4, 16);
     L.cnt_d = take(32 * 4, 16);
     L.accE = take(nT * 8, 16);
