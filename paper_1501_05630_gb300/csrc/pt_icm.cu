@@ -242,13 +242,15 @@ __device__ __forceinline__ void load_nbrs(const uint16_t *nbr, int p, int (&q)[Z
 // are updated at beta = 0 and never read, so the inner loop has no guards.
 // Two Philox4x32-10 blocks are generated together (8 draws) so that their
 // dependency chains interleave.
-template <bool GAUSS, int Z, int COLOR, int H>
-__device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g)
+template <bool GAUSS, int Z>
+__device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g, int COLOR,
+                                           int H)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int N = P.N, half = P.half, nth = blockDim.x;
     const int rbase = 32 * g + 16 * H;
+    const int sh0 = 16 * H;                       // first bit of this pass inside the word
     const int npairs8 = (P.R - rbase + 7) >> 3;   // 8-bit groups holding at least one live replica (1 or 2)
     uint32_t *sg = S.s + g * N;
     ET acc[16];
@@ -256,9 +258,10 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
     for (int b = 0; b < 16; ++b) acc[b] = ET(0);
     for (int j = threadIdx.x; j < half; j += nth) {
         const int p = COLOR * half + j;
-        const uint32_t sw = sg[p];
+        const uint32_t sw0 = sg[p];
+        const uint32_t sw = sw0 >> sh0;                 // this pass's bits at 0..15: constant shifts below
         const uint32_t site = __ldg(P.pos2site + p);
-        uint32_t flip = 0;
+        uint32_t flip = 0;                              // bits 0..15 of this pass
         if constexpr (GAUSS) {
             float Jv[Z];
             uint32_t nw[Z];
@@ -266,28 +269,30 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             load_nbrs<Z>(S.nbr, p, q);
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                nw[d] = sg[q[d]];
+                nw[d] = sg[q[d]] >> sh0;
                 Jv[d] = S.Jd[p * Z + d];
             }
-            const float *b2l = S.b2l + 32 * g;
+            const float *b2l = S.b2l + rbase;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q < npairs8) {
+            for (int qq = 0; qq < 2; ++qq) {
+                if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * q, inst, P.seed_lo, P.seed_hi, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int b = 16 * H + 8 * q + i;   // bit inside the word (compile-time)
+                        const int b = 8 * qq + i;               // compile-time bit of the pass
                         float h = 0.f;
 #pragma unroll
                         for (int d = 0; d < Z; ++d)
                             h += __uint_as_float(__float_as_uint(Jv[d]) ^ ((nw[d] << (31 - b)) & 0x80000000u));
+                        // sh = s_i h_i, Delta E = 2 sh; accept iff sh <= 0 or x < 2^32 exp(-2 beta sh)
                         const float sh = __uint_as_float(__float_as_uint(h) ^ ((sw << (31 - b)) & 0x80000000u));
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
-                        const float u = __uint_as_float(0x3f800000u | (xr >> 9)) - 1.0f;
-                        const bool a = (sh <= 0.f) || (u < ex2_approx(b2l[b] * sh));
+                        const uint32_t thr = __float2uint_rz(ex2_approx(fmaf(b2l[b], sh, 32.f)));
+                        const bool a = (sh <= 0.f) || (xr < thr);
                         flip |= (uint32_t)a << b;
-                        if (COLOR == 1) acc[8 * q + i] += a ? sh : -sh;
+                        acc[b] -= sh;                           // e = -s'h: -sh, or +sh after a flip
+                        if (a) acc[b] += 2.f * sh;
                     }
                 }
             }
@@ -298,51 +303,59 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             load_nbrs<Z>(S.nbr, p, q);
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                const uint32_t u = sw ^ sg[q[d]] ^ (0u - ((jb >> d) & 1u));
+                const uint32_t u = sw0 ^ sg[q[d]] ^ (0u - ((jb >> d) & 1u));
                 const uint32_t t0 = c0 & u;
                 c0 ^= u;
                 const uint32_t t1 = c1 & t0;
                 c1 ^= t0;
                 c2 |= t1;
             }
+            c0 >>= sh0;
+            c1 >>= sh0;
+            c2 >>= sh0;
             const int z = P.const_z ? P.const_z : (int)S.zdeg[p];
             // m = z - 2u <= 0  <=>  u >= ceil(z/2): always accepted
-            const uint32_t always = (z <= 4) ? (c2 | c1) : (c2 | (c1 & c0));
-            flip = always & (0xFFFFu << (16 * H));
-            const uint32_t *thr = S.thr + 32 * g * 8;
+            flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
+            const uint32_t *thr = S.thr + rbase * 8;
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                if (q < npairs8) {
+            for (int qq = 0; qq < 2; ++qq) {
+                if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * q, inst, P.seed_lo, P.seed_hi, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
-                        const int b = 16 * H + 8 * q + i;
+                        const int b = 8 * qq + i;
                         const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
                         const int m = z - 2 * u;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
                         const uint32_t th = thr[b * 8 + (m > 0 ? m : 0)];
                         flip |= (uint32_t)(xr < th) << b;
-                        if (COLOR == 1) acc[8 * q + i] += ((flip >> b) & 1u) ? m : -m;
+                        acc[b] += ((flip >> b) & 1u) ? m : -m;
                     }
                 }
             }
         }
-        sg[p] = sw ^ flip;
+        sg[p] = sw0 ^ (flip << sh0);
     }
-    if (COLOR == 1) {
+    if (COLOR == 1) {   // energies: every bond touches exactly one colour-1 site
         const ET v = transpose_reduce16(acc, lane);
         const int r = rbase + (lane >> 1);
         if (!(lane & 1) && r < P.R) ((ET *)S.Epart)[warp * P.R + r] = v;
     }
 }
 
-template <bool GAUSS, int Z, int COLOR>
-__device__ __forceinline__ void half_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
+// Step 1 for all replicas: colour 0 then colour 1, each as 16-bit passes over
+// the site words.  One call site, so the pass body exists once in the kernel
+// (the instruction cache is shared by all CTAs of the SM).
+template <bool GAUSS, int Z>
+__device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
 {
-    for (int g = 0; g < P.G; ++g) {
-        sweep_pass<GAUSS, Z, COLOR, 0>(P, S, t, inst, g);
-        if (32 * g + 16 < P.R) sweep_pass<GAUSS, Z, COLOR, 1>(P, S, t, inst, g);
+    const int npass = (P.R + 15) >> 4;          // 16-bit passes per colour
+    for (int it = 0; it < 2 * npass; ++it) {
+        const int color = it >= npass;
+        const int pass = it - color * npass;
+        sweep_pass<GAUSS, Z>(P, S, t, inst, pass >> 1, color, pass & 1);
+        if (pass == npass - 1) __syncthreads();
     }
 }
 
@@ -841,10 +854,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
                 __syncthreads();
             }
             if (P.enable_metropolis) {  // step 1
-                half_sweep<GAUSS, Z, 0>(P, S, t, inst);
-                __syncthreads();
-                half_sweep<GAUSS, Z, 1>(P, S, t, inst);
-                __syncthreads();
+                metropolis_sweep<GAUSS, Z>(P, S, t, inst);
                 for (int r = tid; r < R; r += nth) {
                     ET e = ET(0);
                     for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + r];
