@@ -193,6 +193,27 @@ icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t
                           int32_t *csize, double *esum_before, double *esum_after,
                           uint8_t *swap_acc, uint32_t flags);
 
+/* Energies of replica configurations, computed without allocating any device
+ * memory.  The paper has no counterpart: this is a service for callers that
+ * cannot call cudaMalloc at this point -- code that runs inside a memory pool
+ * or arena that forbids outside allocations, pipelines that must not hit
+ * cudaMalloc's implicit device synchronisation, and hosts that budget every
+ * byte of HBM in advance.
+ *   couplings : device [n_inst][N_b] in bond order (int8 +-1 or float32)
+ *   spins     : device [n_inst][n_rep][N] int8 +-1, 1 <= n_rep <= 64
+ *   out       : device [n_inst][n_rep] double, H = -sum_<ij> J_ij s_i s_j
+ * Work is enqueued on the context's stream; the call returns after it ends.
+ * Scratch is one fixed 8 MiB array in the library's device image, held by
+ * every GPU that loads the library until the process exits.  Requests that
+ * need more (geometry tables + n_inst instances of packed spins, expanded
+ * couplings and energies) fail with ICM_ERR_UNSUPPORTED and a message.  The
+ * first call on a device looks up the array's address (do it before any
+ * stream capture).  All calls share the array: calls that overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Every scratch byte a call reads is written earlier in that call. */
+icm_status icm_energies_static(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
+                               int32_t n_rep, const void *couplings, const int8_t *spins, double *out);
+
 /* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
  * dynamic shared memory bytes per CTA and kernel launches issued so far. */
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,

@@ -238,6 +238,60 @@ void destroy_batch(icm_batch *b)
 
 }  // namespace
 
+namespace icm {
+
+void set_ctx_error(icm_ctx *ctx, const std::string &msg)
+{
+    if (ctx) ctx->err = msg;
+}
+cudaStream_t ctx_stream(const icm_ctx *ctx) { return ctx->stream; }
+int ctx_device(const icm_ctx *ctx) { return ctx->device; }
+
+}  // namespace icm
+
+namespace icm {
+
+// Position tables of one lattice for the layout kernels (colour-major site
+// positions, neighbour positions padded with the site itself, bond index per
+// directed edge or -1).  Returns false for a lattice this library does not
+// support.
+bool host_tables(int lattice, int L, HostTables &t)
+{
+    Geometry g;
+    if ((lattice != ICM_CHIMERA && (L < 2 || (L & 1))) || (lattice == ICM_CHIMERA && L < 1)) return false;
+    if (!build_geometry(lattice, L, g) || g.N > 65535) return false;
+    const int N = g.N, Z = g.Z;
+    t.N = N;
+    t.Nb = g.Nb;
+    t.Z = Z;
+    std::vector<int> pos(N);
+    t.pos2site.assign(N, 0);
+    int next[2] = {0, N / 2};
+    for (int i = 0; i < N; ++i) {
+        if (next[g.color[i]] >= (g.color[i] ? N : N / 2)) return false;
+        pos[i] = next[g.color[i]]++;
+        t.pos2site[pos[i]] = (uint16_t)i;
+    }
+    std::vector<std::vector<std::pair<int, int>>> inc(N);
+    for (int e = 0; e < g.Nb; ++e) {
+        inc[g.bi[e]].push_back({g.bj[e], e});
+        inc[g.bj[e]].push_back({g.bi[e], e});
+    }
+    t.nbr.assign((size_t)N * Z, 0);
+    t.edge_bond.assign((size_t)N * Z, -1);
+    for (int i = 0; i < N; ++i) {
+        const int deg = (int)inc[i].size(), p = pos[i];
+        if (deg > Z) return false;
+        for (int d = 0; d < Z; ++d) {
+            t.nbr[(size_t)p * Z + d] = (uint16_t)(d < deg ? pos[inc[i][d].first] : p);
+            t.edge_bond[(size_t)p * Z + d] = d < deg ? inc[i][d].second : -1;
+        }
+    }
+    return true;
+}
+
+}  // namespace icm
+
 extern "C" {
 
 icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream)

@@ -2,6 +2,7 @@
 // half (pt_icm.cu) of the library.  Not part of the public ABI.
 #pragma once
 #include <cstdint>
+#include <vector>
 #include <cuda_runtime.h>
 
 namespace icm {
@@ -76,6 +77,15 @@ struct KParams {
     uint8_t *tr_swap;                                    // [n_inst][2][nT-1]
     SmemLayout sm;
 };
+
+// Host-built position tables of one lattice (see host_tables in icm_api.cpp).
+struct HostTables {
+    int N = 0, Nb = 0, Z = 0;
+    std::vector<uint16_t> nbr;        // [N][Z]
+    std::vector<uint16_t> pos2site;   // [N]
+    std::vector<int32_t> edge_bond;   // [N][Z]
+};
+bool host_tables(int lattice, int L, HostTables &t);
 
 SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss);
 int fused_threads(int N);

@@ -44,7 +44,7 @@ EXPORTS = [
     "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_lattice_size", "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
-    "icm_read_trace", "icm_batch_info",
+    "icm_read_trace", "icm_batch_info", "icm_energies_static",
 ]
 
 
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_clear_observables.argtypes = [vp]
         L.icm_read_trace.argtypes = [vp] + [vp] * 7 + [u32]
         L.icm_batch_info.argtypes = [vp] + [vp] * 5
+        L.icm_energies_static.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, vp]
         for name in EXPORTS:
             if name != "icm_last_error":
                 getattr(L, name).restype = i32
@@ -142,6 +143,18 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def energies_static(ctx: Context, lattice: int, L: int, disorder: int, couplings, spins, out):
+    """Energies [n_inst][n_rep] of device spin arrays, computed on the library's
+    fixed device scratch (no device allocation; see icm_energies_static)."""
+    for a in (couplings, spins, out):
+        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
+            raise ValueError("energies_static takes contiguous CUDA tensors")
+    n_inst, n_rep = int(spins.shape[0]), int(spins.shape[1])
+    ctx.check(ctx._lib.icm_energies_static(ctx._h, int(lattice), int(L), int(disorder), n_inst, n_rep,
+                                           couplings.data_ptr(), spins.data_ptr(), out.data_ptr()))
+    return out
 
 
 @dataclass
