@@ -24,8 +24,9 @@ struct SmemLayout {
     int icm_mask;   // uint32 [n_icm][NW] overlap masks per ICM pair
     int icm_C;      // uint32 [G][N]     cluster bits (bit 2k: site in pair k's cluster)
     int swap_x;     // uint32 [2][32]
-    int swap_list;  // int32 [2][32]
-    int swap_n;     // int32 [2]
+    int swap_list;  // int32 [2][32]   per run: (source bit << 8) | destination bit
+    int swap_n;     // int32 [2]       runs per copy
+    int swap_mask;  // uint64 [2]      bits moving down one slot, per copy
     int flipw;      // uint32 [2]      step-2a reversal masks of the two words
     int icm_seed;   // int32 [32]      seed position per ICM pair (-1: none)
     int icm_esum;   // float or int32 [32]  E_a + E_b of each ICM pair before the move

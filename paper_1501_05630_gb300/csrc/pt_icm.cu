@@ -183,6 +183,7 @@ struct Sm {
     uint32_t *swap_x;
     int *swap_list;
     int *swap_n;
+    uint64_t *swap_mask;
     uint32_t *flipw;
     int *icm_seed;
     void *icm_esum_raw;
@@ -210,6 +211,7 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.swap_x = (uint32_t *)(base + L.swap_x);
     S.swap_list = (int *)(base + L.swap_list);
     S.swap_n = (int *)(base + L.swap_n);
+    S.swap_mask = (uint64_t *)(base + L.swap_mask);
     S.flipw = (uint32_t *)(base + L.flipw);
     S.icm_seed = (int *)(base + L.icm_seed);
     S.icm_esum_raw = base + L.icm_esum;
@@ -263,14 +265,19 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
         const uint32_t site = __ldg(P.pos2site + p);
         uint32_t flip = 0;                              // bits 0..15 of this pass
         if constexpr (GAUSS) {
-            float Jv[Z];
+            // h = sum_d J_d s_d = Jsum - 2 sum_{d: s_d = -1} J_d: one bit test and one
+            // predicated add per neighbour and bit
+            float J2[Z];
             uint32_t nw[Z];
             int q[Z];
             load_nbrs<Z>(S.nbr, p, q);
+            float Jsum = 0.f;
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
                 nw[d] = sg[q[d]] >> sh0;
-                Jv[d] = S.Jd[p * Z + d];
+                const float J = S.Jd[p * Z + d];
+                Jsum += J;
+                J2[d] = 2.f * J;
             }
             const float *b2l = S.b2l + rbase;
 #pragma unroll
@@ -281,12 +288,12 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;               // compile-time bit of the pass
-                        float h = 0.f;
+                        float h = Jsum;
 #pragma unroll
                         for (int d = 0; d < Z; ++d)
-                            h += __uint_as_float(__float_as_uint(Jv[d]) ^ ((nw[d] << (31 - b)) & 0x80000000u));
+                            if ((nw[d] >> b) & 1u) h -= J2[d];
                         // sh = s_i h_i, Delta E = 2 sh; accept iff sh <= 0 or x < 2^32 exp(-2 beta sh)
-                        const float sh = __uint_as_float(__float_as_uint(h) ^ ((sw << (31 - b)) & 0x80000000u));
+                        const float sh = ((sw >> b) & 1u) ? -h : h;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
                         const uint32_t thr = __float2uint_rz(ex2_approx(fmaf(b2l[b], sh, 32.f)));
                         const bool a = (sh <= 0.f) || (xr < thr);
@@ -681,13 +688,18 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
     if (threadIdx.x == 0 || threadIdx.x == second) {
         ET *E = (ET *)S.E;
         const int c = threadIdx.x == 0 ? 0 : 1;
-        {
-            int ns = 0;
-            for (int k = 0; k < np; ++k) {
+        // Accepted swaps (k,k+1), (k+1,k+2), ..., (m,m+1) in a row form a run:
+        // the configuration at k bubbles up to m+1 and those at k+1..m+1 move
+        // down one slot.  Record, per copy, the bits that move down (D) and one
+        // (source, destination) bit pair per run.
+        uint64_t D = 0;
+        int nrun = 0, run_start = -1;
+        for (int k = 0; k <= np; ++k) {
+            bool acc = false;
+            if (k < np) {
                 const int ra = 2 * k + c, rb = ra + 2;
                 const ET ek = E[ra], ek1 = E[rb];
                 const uint32_t x = S.swap_x[c * 32 + k];
-                bool acc;
                 if constexpr (GAUSS) {
                     // log2(e) (beta_k - beta_{k+1}) (E_k - E_{k+1}); accept iff >= 0 or u < 2^delta
                     const float delta = P.dbeta_l2e[k] * (ek - ek1);
@@ -704,32 +716,41 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
                 if (acc) {
                     E[ra] = ek1;
                     E[rb] = ek;
-                    S.swap_list[c * 32 + ns++] = k;
+                    D |= 1ull << (rb);
+                    if (run_start < 0) run_start = k;
                 }
                 if (trace) P.tr_swap[((size_t)slot * 2 + c) * np + k] = (uint8_t)acc;
             }
-            S.swap_n[c] = ns;
+            if (!acc && run_start >= 0) {   // run [run_start, k-1] ends
+                S.swap_list[c * 32 + nrun++] = ((2 * run_start + c) << 8) | (2 * k + c);
+                run_start = -1;
+            }
         }
+        S.swap_n[c] = nrun;
+        S.swap_mask[c] = D;
     }
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {
+        const uint64_t D = S.swap_mask[0] | S.swap_mask[1];
+        uint64_t U = 0;
+        for (int j = 0; j < n0; ++j) U |= 1ull << (S.swap_list[j] >> 8);
+        for (int j = 0; j < n1; ++j) U |= 1ull << (S.swap_list[32 + j] >> 8);
+        const uint64_t keep = ~(D | U);
         const bool two = P.G > 1;
         for (int p = threadIdx.x; p < N; p += blockDim.x) {
-            uint32_t w0 = S.s[p], w1 = two ? S.s[N + p] : 0u;
-            for (int c = 0; c < 2; ++c) {
-                const int nc = c ? n1 : n0;
-                for (int j = 0; j < nc; ++j) {
-                    const int r1 = 2 * S.swap_list[c * 32 + j] + c, r2 = r1 + 2;
-                    const uint32_t b1 = (r1 < 32 ? (w0 >> r1) : (w1 >> (r1 - 32))) & 1u;
-                    const uint32_t b2 = (r2 < 32 ? (w0 >> r2) : (w1 >> (r2 - 32))) & 1u;
-                    const uint32_t dlt = b1 ^ b2;
-                    if (r1 < 32) w0 ^= dlt << r1; else w1 ^= dlt << (r1 - 32);
-                    if (r2 < 32) w0 ^= dlt << r2; else w1 ^= dlt << (r2 - 32);
-                }
+            const uint64_t x = (uint64_t)S.s[p] | (two ? (uint64_t)S.s[N + p] << 32 : 0ull);
+            uint64_t y = (x & keep) | ((x & D) >> 2);
+            for (int j = 0; j < n0; ++j) {
+                const int mv = S.swap_list[j];
+                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
             }
-            S.s[p] = w0;
-            if (two) S.s[N + p] = w1;
+            for (int j = 0; j < n1; ++j) {
+                const int mv = S.swap_list[32 + j];
+                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
+            }
+            S.s[p] = (uint32_t)y;
+            if (two) S.s[N + p] = (uint32_t)(y >> 32);
         }
     }
     __syncthreads();
@@ -1059,6 +1080,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.swap_x = take(2 * 32 * 4, 16);
     L.swap_list = take(2 * 32 * 4, 16);
     L.swap_n = take(2 * 4, 16);
+    L.swap_mask = take(2 * 8, 16);
     L.flipw = take(2 * 4, 16);
     L.icm_seed = take(32 * 4, 16);
     L.icm_esum = take(32 * 4, 16);
