@@ -22,7 +22,7 @@ struct SmemLayout {
     int Epart;      // float or int32 [nwarps][max(R, 32)]
     int rtab;       // uint32 [R][8] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
     int icm_mask;   // uint32 [n_icm][NW] overlap masks per ICM pair
-    int icm_C;      // uint32 [G][N]     cluster bits (bit 2k: site in pair k's cluster)
+    int icm_C;      // uint2 [N]         cluster bits of both words (bit 2k: site in pair k's cluster)
     int swap_x;     // uint32 [2][32]
     int swap_list;  // int32 [2][32]   per run: (source bit << 8) | destination bit
     int swap_n;     // int32 [2]       runs per copy

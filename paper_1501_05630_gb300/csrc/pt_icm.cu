@@ -391,23 +391,25 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
             int q[Z];
             load_nbrs<Z>(S.nbr, p, q);
             if constexpr (GAUSS) {
-                float Jv[Z];
+                float J2[Z];
                 uint32_t nw[Z];
+                float Jsum = 0.f;
 #pragma unroll
                 for (int d = 0; d < Z; ++d) {
                     nw[d] = sg[q[d]];
-                    Jv[d] = S.Jd[p * Z + d];
+                    const float J = S.Jd[p * Z + d];
+                    Jsum += J;
+                    J2[d] = 2.f * J;
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     if (!((act >> (2 * j)) & 1u)) continue;   // uniform
                     const int b = 2 * j;
-                    float h = 0.f;
+                    float h = Jsum;                            // h = sum_d J_d s_d
 #pragma unroll
                     for (int d = 0; d < Z; ++d)
-                        h += __uint_as_float(__float_as_uint(Jv[d]) ^ ((nw[d] << (31 - b)) & 0x80000000u));
-                    // e = -s_p h_p
-                    acc[j] -= __uint_as_float(__float_as_uint(h) ^ ((sw << (31 - b)) & 0x80000000u));
+                        if ((nw[d] >> b) & 1u) h -= J2[d];
+                    acc[j] += ((sw >> b) & 1u) ? h : -h;       // e = -s_p h_p
                 }
             } else {
                 uint32_t c0 = 0, c1 = 0, c2 = 0;
@@ -472,7 +474,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             if (lane == (k & 31)) S.mask[k * NW + m] = word;
         }
     }
-    for (int i = tid; i < G * N; i += nth) S.C[i] = 0u;
+    for (int i = tid; i < 2 * N; i += nth) S.C[i] = 0u;
     if (tid < 2) S.flipw[tid] = 0u;
     __syncthreads();
 
@@ -507,7 +509,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                 }
                 rank -= c;
             }
-            atomicOr(&S.C[(k >> 4) * N + seed], 1u << (2 * (k & 15)));
+            atomicOr(&S.C[2 * seed + (k >> 4)], 1u << (2 * (k & 15)));
         }
         S.icm_seed[k] = seed;
         esum[k] = E[2 * k] + E[2 * k + 1];
@@ -532,12 +534,15 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             else act1 |= 1u << (2 * (k - 16));
         }
     const uint32_t f0 = S.flipw[0], f1 = S.flipw[1];
+    // cluster words of both replica words of a site side by side: one 64-bit
+    // load per neighbour serves the pairs of both words
+    uint2 *C2 = (uint2 *)S.C;
     int rounds = 0;
     if (N <= 4 * nth) {
         // each thread owns sites tid + j nth (j < 4) and keeps their
-        // neighbours, domains and cluster words in registers across rounds
+        // neighbour positions in registers across rounds
         uint32_t qn[4][Z / 2];                 // neighbour positions, two per register
-        uint32_t todo = 0u;                    // bit 2j+g: site j, word g not yet absorbed
+        uint32_t todo = 0u;                    // bit j: site j not yet absorbed
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = tid + j * nth;
@@ -545,16 +550,16 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             const uint32_t *row = (const uint32_t *)(S.nbr + (ok ? p : 0) * Z);
 #pragma unroll
             for (int i = 0; i < Z / 2; ++i) qn[j][i] = row[i];
-#pragma unroll
-            for (int g = 0; g < 2; ++g) {
-                uint32_t dm = 0u, c = 0u;
-                if (ok && g < G) {
-                    const uint32_t w = S.s[g * N + p] ^ (g ? f1 : f0);   // step 2a
-                    S.s[g * N + p] = w;
-                    dm = (w ^ (w >> 1)) & (g ? act1 : act0);
-                    c = S.C[g * N + p];
+            if (ok) {
+                const uint32_t w0 = S.s[p] ^ f0;             // step 2a
+                S.s[p] = w0;
+                uint32_t w1 = 0u;
+                if (G > 1) {
+                    w1 = S.s[N + p] ^ f1;
+                    S.s[N + p] = w1;
                 }
-                if (dm != c) todo |= 1u << (2 * j + g);
+                const uint2 c = C2[p];
+                if (((w0 ^ (w0 >> 1)) & act0) != c.x || ((w1 ^ (w1 >> 1)) & act1) != c.y) todo |= 1u << j;
             }
         }
         if (act0 | act1) {
@@ -563,37 +568,37 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                 grew = 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
+                    if (!((todo >> j) & 1u)) continue;
+                    const int p = tid + j * nth;
+                    const uint32_t w0 = S.s[p], w1 = G > 1 ? S.s[N + p] : 0u;
+                    const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
+                    uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
-                    for (int g = 0; g < 2; ++g) {
-                        if (!((todo >> (2 * j + g)) & 1u)) continue;
-                        const uint32_t *Cg = S.C + g * N;
-                        const uint32_t w = S.s[g * N + tid + j * nth];
-                        const uint32_t dm = (w ^ (w >> 1)) & (g ? act1 : act0);
-                        uint32_t nb = 0u;
-#pragma unroll
-                        for (int i = 0; i < Z / 2; ++i) nb |= Cg[qn[j][i] & 0xffffu] | Cg[qn[j][i] >> 16];
-                        const uint32_t c = S.C[g * N + tid + j * nth];   // written only by this thread
-                        const uint32_t nc = c | (dm & nb);
-                        if (nc != c) {
-                            S.C[g * N + tid + j * nth] = nc;
-                            grew = 1;
-                            if (nc == dm) todo &= ~(1u << (2 * j + g));
-                        }
+                    for (int i = 0; i < Z / 2; ++i) {
+                        const uint2 a = C2[qn[j][i] & 0xffffu], b = C2[qn[j][i] >> 16];
+                        nb0 |= a.x | b.x;
+                        nb1 |= a.y | b.y;
+                    }
+                    const uint2 c = C2[p];                    // written only by this thread
+                    const uint32_t n0 = c.x | (d0 & nb0), n1 = c.y | (d1 & nb1);
+                    if (n0 != c.x || n1 != c.y) {
+                        C2[p] = make_uint2(n0, n1);
+                        grew = 1;
+                        if (n0 == d0 && n1 == d1) todo &= ~(1u << j);
                     }
                 }
                 ++rounds;
             } while (__syncthreads_or(grew));
             // (d) flip the owned sites
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const int i = g * N + tid + j * nth;
-                    if (g < G && tid + j * nth < N) {
-                        const uint32_t c = S.C[i];
-                        if (c) S.s[i] ^= c | (c << 1);
-                    }
+            for (int j = 0; j < 4; ++j) {
+                const int p = tid + j * nth;
+                if (p < N) {
+                    const uint2 c = C2[p];
+                    if (c.x) S.s[p] ^= c.x | (c.x << 1);
+                    if (c.y) S.s[N + p] ^= c.y | (c.y << 1);
                 }
+            }
         }
     } else {
         for (int p = tid; p < N; p += nth) {
@@ -605,31 +610,32 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             int grew;
             do {
                 grew = 0;
-                for (int g = 0; g < G; ++g) {
-                    const uint32_t ag = g ? act1 : act0;
-                    uint32_t *Cg = S.C + g * N;
-                    for (int p = tid; p < N; p += nth) {
-                        const uint32_t w = S.s[g * N + p];
-                        const uint32_t dm = (w ^ (w >> 1)) & ag;
-                        const uint32_t c = Cg[p];
-                        if (dm == c) continue;
-                        int q[Z];
-                        load_nbrs<Z>(S.nbr, p, q);
-                        uint32_t nb = 0u;
+                for (int p = tid; p < N; p += nth) {
+                    const uint32_t w0 = S.s[p], w1 = G > 1 ? S.s[N + p] : 0u;
+                    const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
+                    const uint2 c = C2[p];
+                    if (d0 == c.x && d1 == c.y) continue;
+                    int q[Z];
+                    load_nbrs<Z>(S.nbr, p, q);
+                    uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
-                        for (int d = 0; d < Z; ++d) nb |= Cg[q[d]];
-                        const uint32_t nc = c | (dm & nb);
-                        if (nc != c) {
-                            Cg[p] = nc;
-                            grew = 1;
-                        }
+                    for (int d = 0; d < Z; ++d) {
+                        const uint2 a = C2[q[d]];
+                        nb0 |= a.x;
+                        nb1 |= a.y;
+                    }
+                    const uint32_t n0 = c.x | (d0 & nb0), n1 = c.y | (d1 & nb1);
+                    if (n0 != c.x || n1 != c.y) {
+                        C2[p] = make_uint2(n0, n1);
+                        grew = 1;
                     }
                 }
                 ++rounds;
             } while (__syncthreads_or(grew));
-            for (int i = tid; i < G * N; i += nth) {
-                const uint32_t c = S.C[i];
-                if (c) S.s[i] ^= c | (c << 1);
+            for (int p = tid; p < N; p += nth) {
+                const uint2 c = C2[p];
+                if (c.x) S.s[p] ^= c.x | (c.x << 1);
+                if (c.y) S.s[N + p] ^= c.y | (c.y << 1);
             }
         }
     }
@@ -643,9 +649,9 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     }
     if (trace) {
         // cluster sizes: counted once per cluster site
-        for (int i = tid; i < G * N; i += nth) {
-            const uint32_t c = S.C[i];
-            for (uint32_t b = c; b; b &= b - 1u) atomicAdd(&S.cnt_d[16 * (i / N) + ((__ffs(b) - 1) >> 1)], 1);
+        for (int i = tid; i < 2 * N; i += nth) {
+            const uint32_t c = S.C[i];   // word i & 1 of site i >> 1
+            for (uint32_t b = c; b; b &= b - 1u) atomicAdd(&S.cnt_d[16 * (i & 1) + ((__ffs(b) - 1) >> 1)], 1);
         }
     }
     __syncthreads();
@@ -1076,7 +1082,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.Epart = take(nwarps * (R > 32 ? R : 32) * 4, 16);
     L.rtab = take(gauss ? G * 32 * 4 : G * 32 * 8 * 4, 16);   // every bit of the G words
     L.icm_mask = take(n_icm * NW * 4, 16);
-    L.icm_C = take(G * N * 4, 16);
+    L.icm_C = take(2 * N * 4, 16);
     L.swap_x = take(2 * 32 * 4, 16);
     L.swap_list = take(2 * 32 * 4, 16);
     L.swap_n = take(2 * 4, 16);
