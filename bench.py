@@ -198,19 +198,125 @@ def run_reference(args, wl, rank):
     }))
 
 
+SERVING_MENU = [
+    # (lattice, L, disorder, (T_min, T_max), T_icm)
+    (I.SQUARE2D, 16, I.PM_J, (0.2, 1.5), 1.0), (I.SQUARE2D, 32, I.PM_J, (0.2, 1.5), 1.0),
+    (I.SQUARE2D, 64, I.PM_J, (0.2, 1.5), 1.0),
+    (I.CUBIC3D, 6, I.GAUSS, (0.2, 2.0), 1.0), (I.CUBIC3D, 8, I.GAUSS, (0.2, 2.0), 1.0),
+    (I.CUBIC3D, 12, I.GAUSS, (0.2, 2.0), 1.0),
+    (I.CHIMERA, 8, I.PM_J, (0.2, 3.0), 1.5), (I.CHIMERA, 12, I.PM_J, (0.2, 3.0), 1.5),
+]
+
+
+def serving_requests(n, rate, seed, n_T_choices):
+    """Poisson arrivals (mean `rate`/s) of instances drawn uniformly from the menu."""
+    from paper_1501_05630_gb300 import icmpt
+    from paper_1501_05630_gb300.serve import Request
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    reqs = []
+    for i in range(n):
+        lat, L, dis, (tl, th), ticm = SERVING_MENU[rng.integers(len(SERVING_MENU))]
+        nT = int(rng.choice(n_T_choices))
+        N, Nb = icmpt.lattice_size(lat, L)
+        inst = 5000 + i
+        reqs.append(Request(lat, L, dis, I.ladder(tl, th, nT), ticm, seed, inst,
+                            I.couplings(Nb, dis, seed, [inst])[0], I.initial_spins(N, 2 * nT, seed, [inst])[0],
+                            arrival=float(t[i])))
+    return reqs
+
+
+def run_serving(args):
+    import torch
+    from paper_1501_05630_gb300 import build
+    from paper_1501_05630_gb300.serve import Server
+    torch.cuda.set_device(0)
+    build.build()
+    n_T = tuple(int(x) for x in args.serving_nT.split(","))
+    reqs = serving_requests(args.requests, args.rate, 0x150105630000005, n_T)
+    kw = dict(quantum=args.quantum, max_sweeps=args.max_sweeps, eps_e=0.005, eps_ql=0.01, need=2)
+    srv = Server(slots_per_class=args.slots, **kw)
+    pending = sorted(reqs, key=lambda r: r.arrival)
+    tickets = {}
+    i = 0
+    with ClockSampler(0) as clk:
+        start = time.perf_counter()
+        while i < len(pending) or not srv.idle():
+            now = time.perf_counter() - start
+            while i < len(pending) and pending[i].arrival <= now:
+                r = pending[i]
+                r.arrival = start + r.arrival
+                tickets[srv.submit(r)] = r
+                i += 1
+            if srv.idle():
+                time.sleep(max(0.0, min(0.002, pending[i].arrival - (time.perf_counter() - start))))
+                continue
+            srv.step()
+        wall = time.perf_counter() - start
+    res = [srv.poll(t) for t in tickets]
+    lat = np.array([r.latency for r in res])
+    therm = sum(r.status == "thermalized" for r in res)
+    srv.close()
+    # one instance at a time (the plain form), same criterion, on a sample
+    sample = pending[: args.alone_sample]
+    a0 = time.perf_counter()
+    alone_therm = 0
+    for r in sample:
+        one = Server(slots_per_class=1, **kw)
+        r2 = dataclasses_replace(r)
+        tk = one.submit(r2)
+        one.run_until_idle()
+        alone_therm += one.poll(tk).status == "thermalized"
+        one.close()
+    alone_s = time.perf_counter() - a0
+    out = {
+        "metric": "instances_thermalized_per_s", "value": therm / wall, "unit": "instances/s", "n_gpus": 1,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
+        "dtype": "u32/f32", "config": {"workload": "serving", "requests": len(res), "rate_per_s": args.rate,
+                                       "menu": [f"{['2D', '3D', 'chimera'][m[0]]} L={m[1]} {['pmJ', 'gauss'][m[2]]}"
+                                                for m in SERVING_MENU], "n_T": n_T, "quantum": args.quantum,
+                                       "max_sweeps": args.max_sweeps, "slots_per_class": args.slots,
+                                       "criterion": "block means of e and q_l at T_min agree (|de|<=0.005, "
+                                                    "|dq_l|<=0.01) on 2 consecutive doubling windows"},
+        "thermalized": int(therm), "not_thermalized": int(len(res) - therm), "wall_s": wall,
+        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+        "mean_sweeps": float(np.mean([r.sweeps for r in res])),
+        "one_at_a_time": {"requests": len(sample), "thermalized": int(alone_therm), "wall_s": alone_s,
+                          "value": alone_therm / alone_s, "unit": "instances/s"},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(out))
+
+
+def dataclasses_replace(r):
+    import dataclasses
+    return dataclasses.replace(r, arrival=0.0)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--rate", type=float, default=200.0)
+    ap.add_argument("--quantum", type=int, default=64)
+    ap.add_argument("--max-sweeps", type=int, default=1 << 14)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--serving-nT", default="16,24,32")
+    ap.add_argument("--alone-sample", type=int, default=8)
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--ref-sweeps", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
+    if args.workload == "serving":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_serving(args)
+        return
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

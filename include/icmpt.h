@@ -193,6 +193,47 @@ icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t
                           int32_t *csize, double *esum_before, double *esum_after,
                           uint8_t *swap_acc, uint32_t flags);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching: a batch is a table of slots.  One slot can be
+ * replaced while the others keep their state; free slots are skipped by the
+ * kernel; each slot has its own measurement window.                       */
+
+/* Load one instance into `slot`: couplings [N_b], spins [2 n_T][N] (NULL =
+ * all +1), its RNG instance id; the slot's sweep counter restarts at 0, its
+ * observables are cleared, its window starts at t = 0 and it becomes active.
+ * The other slots are untouched.                                          */
+icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings, const int8_t *spins,
+                              uint32_t instance_id, uint32_t flags);
+/* Mark a slot active (1) or free (0: the kernel skips it); slot -1 = all. */
+icm_status icm_batch_set_active(icm_batch *b, int32_t slot, int32_t active);
+/* Clear the slot's observables and accumulate them from sweep t_start on. */
+icm_status icm_batch_start_window(icm_batch *b, int32_t slot, int64_t t_start);
+
+/* Thermalization test of one instance over doubling windows [2^(b-1), 2^b)
+ * at the lowest temperature ("Benchmark model and observables", Eq. 1 and
+ * Eq. 2).  Eq. 1 is an identity of disorder averages, so for one instance
+ * the test is the stability of the block means: the newest block's e and
+ * q_l agree with the previous block's within eps_e / eps_ql for `need`
+ * consecutive blocks.  delta = E(q_l) - e of the newest block is reported.
+ * Host only; no device work.                                              */
+typedef struct {
+    int32_t blocks;       /* windows seen */
+    int32_t stable;       /* consecutive windows agreeing with their predecessor */
+    double e[3], ql[3];   /* newest first */
+    double delta;         /* -(N_b/N)(1 - q_l)/T - e of the newest window */
+} icm_therm_state;
+typedef struct {
+    double eps_e, eps_ql;
+    int32_t need;
+} icm_therm_criterion;
+icm_status icm_therm_update(icm_therm_state *st, const icm_therm_criterion *c, double e, double q_l,
+                            double T_min, double bonds_per_site, int32_t *thermalized);
+
+/* Eq. 2 over the batch: the mean over measured (active) instances of
+ * E(q_l) - e at temperature position k from the current accumulators, with
+ * its standard error over instances.                                      */
+icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *delta_se, int32_t *n_used);
+
 /* Energies of replica configurations, computed without allocating any device
  * memory.  The paper has no counterpart: this is a service for callers that
  * cannot call cudaMalloc at this point -- code that runs inside a memory pool

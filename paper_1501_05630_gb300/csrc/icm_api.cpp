@@ -6,6 +6,7 @@
 // the kernels of pt_icm.cu on the context's stream.
 #include "icmpt.h"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -141,6 +142,11 @@ struct icm_batch {
     int8_t *raw_spins = nullptr;  // [n_inst][R][N]
     double *raw_E = nullptr;      // [n_inst][R]
     int32_t *edge_bond = nullptr; // [N][Z]
+    // per-slot control (serving), allocated on first use
+    uint8_t *d_active = nullptr;      // [n_inst]
+    long long *d_tmeas = nullptr;     // [n_inst]
+    std::vector<uint8_t> h_active;
+    std::vector<long long> h_tmeas;
 };
 
 namespace {
@@ -618,6 +624,8 @@ icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps)
     P.enable_metropolis = b->sched.enable_metropolis;
     P.trace = b->sched.trace;
     P.t_meas = b->sched.t_meas;
+    P.active = b->d_active;
+    P.t_meas_inst = b->d_tmeas;
     ICM_CUDA(b->ctx, icm::launch_fused(P, b->gauss, b->threads, b->grid, n_sweeps, b->ctx->stream));
     b->launches += 1;
     return ICM_OK;
@@ -699,6 +707,175 @@ icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t
         if (esum_before) esum_before[i] = eb[i];
         if (esum_after) esum_after[i] = ea[i];
     }
+    return ICM_OK;
+}
+
+// ---------------------------------------------------------------- per-slot control
+
+static icm_status ensure_slot_arrays(icm_batch *b)
+{
+    if (b->d_active) return ICM_OK;
+    icm_status st;
+    if ((st = dalloc(b, &b->d_active, b->n_inst)) || (st = dalloc(b, &b->d_tmeas, b->n_inst))) return st;
+    b->h_active.assign(b->n_inst, 1);
+    b->h_tmeas.assign(b->n_inst, b->sched.t_meas);
+    ICM_CUDA(b->ctx, cudaMemcpyAsync(b->d_active, b->h_active.data(), b->n_inst, cudaMemcpyHostToDevice,
+                                     b->ctx->stream));
+    ICM_CUDA(b->ctx, cudaMemcpyAsync(b->d_tmeas, b->h_tmeas.data(), b->n_inst * sizeof(long long),
+                                     cudaMemcpyHostToDevice, b->ctx->stream));
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+static icm_status clear_slot_observables(icm_batch *b, int slot)
+{
+    icm_ctx *ctx = b->ctx;
+    icm::KParams &P = b->kp;
+    const size_t nT = P.nT, nk = (size_t)b->n_inst * nT;
+    ICM_CUDA(ctx, cudaMemsetAsync(P.accE + slot * nT, 0, nT * sizeof(double), ctx->stream));
+    for (int a = 0; a < 4; ++a)
+        ICM_CUDA(ctx, cudaMemsetAsync(P.acc64 + a * nk + slot * nT, 0, nT * sizeof(long long), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.hist + slot * nT * (P.N + 1), 0, nT * (P.N + 1) * sizeof(unsigned long long),
+                                  ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.n_meas + slot, 0, sizeof(long long), ctx->stream));
+    return ICM_OK;
+}
+
+static icm_status set_slot_flags(icm_batch *b, int slot)
+{
+    ICM_CUDA(b->ctx, cudaMemcpyAsync(b->d_active + slot, &b->h_active[slot], 1, cudaMemcpyHostToDevice,
+                                     b->ctx->stream));
+    ICM_CUDA(b->ctx, cudaMemcpyAsync(b->d_tmeas + slot, &b->h_tmeas[slot], sizeof(long long),
+                                     cudaMemcpyHostToDevice, b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings, const int8_t *spins,
+                              uint32_t instance_id, uint32_t flags)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (slot < 0 || slot >= b->n_inst) return fail(b->ctx, ICM_ERR_ARG, "slot out of range");
+    if (!couplings) return fail(b->ctx, ICM_ERR_ARG, "couplings are required");
+    if (instance_id >= (1u << 24)) return fail(b->ctx, ICM_ERR_ARG, "instance ids must be < 2^24");
+    icm_status st;
+    if ((st = ensure_slot_arrays(b))) return st;
+    icm_ctx *ctx = b->ctx;
+    icm::KParams &P = b->kp;
+    const size_t esz = b->gauss ? 4 : 1;
+    unsigned char *raw_c = (unsigned char *)b->raw_coup + (size_t)slot * P.Nb * esz;
+    if ((st = copy_in(ctx, raw_c, couplings, (size_t)P.Nb * esz, flags))) return st;
+    float *Jd = b->gauss ? const_cast<float *>(P.Jd) + (size_t)slot * P.N * P.Z : nullptr;
+    uint8_t *Jb = b->gauss ? nullptr : const_cast<uint8_t *>(P.Jb) + (size_t)slot * P.N;
+    ICM_CUDA(ctx, icm::launch_expand_couplings(raw_c, b->gauss, b->edge_bond, 1, P.N, P.Z, P.Nb, Jd, Jb, ctx->stream));
+    uint32_t *sp = P.spins + (size_t)slot * P.G * P.N;
+    if (spins) {
+        int8_t *raw_s = b->raw_spins + (size_t)slot * P.R * P.N;
+        if ((st = copy_in(ctx, raw_s, spins, (size_t)P.R * P.N, flags))) return st;
+        ICM_CUDA(ctx, icm::launch_pack_spins(raw_s, sp, P.pos2site, 1, P.R, P.G, P.N, ctx->stream));
+    } else {
+        ICM_CUDA(ctx, cudaMemsetAsync(sp, 0, (size_t)P.G * P.N * 4, ctx->stream));
+    }
+    icm::KParams Q = P;                        // the same kernels on this one slot
+    Q.n_inst = 1;
+    Q.spins = sp;
+    Q.Jd = Jd;
+    Q.Jb = Jb;
+    Q.Ef = P.Ef + (size_t)slot * P.R;
+    Q.Ei = P.Ei + (size_t)slot * P.R;
+    ICM_CUDA(ctx, icm::launch_init_energies(Q, b->gauss, ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.tsweep + slot, 0, 4, ctx->stream));
+    ICM_CUDA(ctx, cudaMemcpyAsync(const_cast<uint32_t *>(P.inst_id) + slot, &instance_id, 4, cudaMemcpyHostToDevice,
+                                  ctx->stream));
+    if ((st = clear_slot_observables(b, slot))) return st;
+    b->h_active[slot] = 1;
+    b->h_tmeas[slot] = 0;
+    if ((st = set_slot_flags(b, slot))) return st;
+    ICM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));   // host values above are read by the copies
+    return ICM_OK;
+}
+
+icm_status icm_batch_set_active(icm_batch *b, int32_t slot, int32_t active)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (slot < -1 || slot >= b->n_inst) return fail(b->ctx, ICM_ERR_ARG, "slot out of range");
+    icm_status st;
+    if ((st = ensure_slot_arrays(b))) return st;
+    if (slot == -1) {                                     // every slot
+        std::fill(b->h_active.begin(), b->h_active.end(), (uint8_t)(active ? 1 : 0));
+        ICM_CUDA(b->ctx, cudaMemcpyAsync(b->d_active, b->h_active.data(), b->n_inst, cudaMemcpyHostToDevice,
+                                         b->ctx->stream));
+        ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+        return ICM_OK;
+    }
+    b->h_active[slot] = active ? 1 : 0;
+    if ((st = set_slot_flags(b, slot))) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_batch_start_window(icm_batch *b, int32_t slot, int64_t t_start)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (slot < 0 || slot >= b->n_inst) return fail(b->ctx, ICM_ERR_ARG, "slot out of range");
+    icm_status st;
+    if ((st = ensure_slot_arrays(b))) return st;
+    if ((st = clear_slot_observables(b, slot))) return st;
+    b->h_tmeas[slot] = t_start;
+    if ((st = set_slot_flags(b, slot))) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
+icm_status icm_therm_update(icm_therm_state *st, const icm_therm_criterion *c, double e, double q_l,
+                            double T_min, double bonds_per_site, int32_t *thermalized)
+{
+    if (!st || !c || !thermalized || !(T_min > 0.0)) return ICM_ERR_ARG;
+    for (int i = 2; i > 0; --i) {
+        st->e[i] = st->e[i - 1];
+        st->ql[i] = st->ql[i - 1];
+    }
+    st->e[0] = e;
+    st->ql[0] = q_l;
+    st->delta = -(bonds_per_site / T_min) * (1.0 - q_l) - e;   // Eq. 1 minus <H>/N (Eq. 2, one instance)
+    st->blocks += 1;
+    const bool agree = st->blocks >= 2 && std::fabs(st->e[0] - st->e[1]) <= c->eps_e &&
+                       std::fabs(st->ql[0] - st->ql[1]) <= c->eps_ql;
+    st->stable = agree ? st->stable + 1 : 0;
+    *thermalized = st->stable >= c->need ? 1 : 0;
+    return ICM_OK;
+}
+
+icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *delta_se, int32_t *n_used)
+{
+    if (!b || !delta_mean) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    if (k < 0 || k >= P.nT) return fail(b->ctx, ICM_ERR_ARG, "temperature index out of range");
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    std::vector<double> accE(nk);
+    std::vector<long long> accd(nk), nm(b->n_inst);
+    icm_status st;
+    if ((st = copy_out(b->ctx, accE.data(), P.accE, nk * 8, 0)) ||
+        (st = copy_out(b->ctx, accd.data(), P.acc64 + 3 * nk, nk * 8, 0)) ||
+        (st = copy_out(b->ctx, nm.data(), P.n_meas, (size_t)b->n_inst * 8, 0)))
+        return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    const double N = P.N, Nb = P.Nb, T = b->T[k];
+    double s1 = 0, s2 = 0;
+    int n = 0;
+    for (int i = 0; i < b->n_inst; ++i) {
+        if (nm[i] <= 0 || (!b->h_active.empty() && !b->h_active[i])) continue;
+        const double m = (double)nm[i];
+        const double e = accE[(size_t)i * P.nT + k] / (2.0 * N * m);
+        const double ql = 1.0 - 2.0 * (double)accd[(size_t)i * P.nT + k] / (Nb * m);
+        const double d = -(Nb / N) * (1.0 - ql) / T - e;
+        s1 += d;
+        s2 += d * d;
+        ++n;
+    }
+    if (n == 0) return fail(b->ctx, ICM_ERR_STATE, "no measured instance");
+    *delta_mean = s1 / n;
+    if (delta_se) *delta_se = n > 1 ? std::sqrt(std::fmax(s2 / n - (s1 / n) * (s1 / n), 0.0) / (n - 1)) : 0.0;
+    if (n_used) *n_used = n;
     return ICM_OK;
 }
 

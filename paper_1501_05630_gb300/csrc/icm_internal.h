@@ -66,6 +66,8 @@ struct KParams {
     // schedule
     int icm_every, swap_every, enable_2a, enable_metropolis, trace;
     long long t_meas;
+    const long long *t_meas_inst;  // [n_inst] per-instance measurement start, or null (t_meas for all)
+    const uint8_t *active;         // [n_inst] 0 = free slot (skipped), or null (all active)
     uint32_t seed_lo, seed_hi;
     // observables
     double *accE;                 // [n_inst][nT]

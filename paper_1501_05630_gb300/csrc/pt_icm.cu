@@ -844,6 +844,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
     }
 
     for (int slot = blockIdx.x; slot < P.n_inst; slot += gridDim.x) {
+        if (P.active && !P.active[slot]) continue;   // free slot of a serving batch
         const uint32_t *gs = P.spins + (size_t)slot * G * N;
         for (int i = tid; i < G * N; i += nth) S.s[i] = gs[i];
         if constexpr (GAUSS) {
@@ -861,6 +862,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
         }
         if (tid == 0) S.nmeas[0] = P.n_meas[slot];
         const uint32_t inst = P.inst_id[slot];
+        const long long t_meas = P.t_meas_inst ? P.t_meas_inst[slot] : P.t_meas;
         uint32_t t = P.tsweep[slot];
         __syncthreads();
 
@@ -896,7 +898,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
             if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1)  // step 3
                 pt_pass<GAUSS>(P, S, t, inst, slot, trace);
             PHASE_MARK(2);
-            if ((long long)t >= P.t_meas) {
+            if ((long long)t >= t_meas) {
                 if (P.small_counts) measure<GAUSS, Z, 4>(P, S, slot);   // every per-thread count < 16
                 else measure<GAUSS, Z, kPlanes>(P, S, slot);
             }

@@ -44,8 +44,18 @@ EXPORTS = [
     "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_lattice_size", "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
-    "icm_read_trace", "icm_batch_info", "icm_energies_static",
+    "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
+    "icm_batch_start_window", "icm_therm_update", "icm_batch_delta",
 ]
+
+
+class ThermState(ctypes.Structure):
+    _fields_ = [("blocks", ctypes.c_int32), ("stable", ctypes.c_int32), ("e", ctypes.c_double * 3),
+                ("ql", ctypes.c_double * 3), ("delta", ctypes.c_double)]
+
+
+class ThermCriterion(ctypes.Structure):
+    _fields_ = [("eps_e", ctypes.c_double), ("eps_ql", ctypes.c_double), ("need", ctypes.c_int32)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -79,6 +89,13 @@ def load_library(path: str = LIB_PATH):
         L.icm_read_trace.argtypes = [vp] + [vp] * 7 + [u32]
         L.icm_batch_info.argtypes = [vp] + [vp] * 5
         L.icm_energies_static.argtypes = [vp, i32, i32, i32, i32, i32, vp, vp, vp]
+        L.icm_batch_set_slot.argtypes = [vp, i32, vp, vp, u32, u32]
+        L.icm_batch_set_active.argtypes = [vp, i32, i32]
+        L.icm_batch_start_window.argtypes = [vp, i32, i64]
+        L.icm_therm_update.argtypes = [ctypes.POINTER(ThermState), ctypes.POINTER(ThermCriterion),
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(i32)]
+        L.icm_batch_delta.argtypes = [vp, i32, vp, vp, vp]
         for name in EXPORTS:
             if name != "icm_last_error":
                 getattr(L, name).restype = i32
@@ -143,6 +160,18 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def therm_update(state: ThermState, crit: ThermCriterion, e: float, q_l: float, T_min: float,
+                 bonds_per_site: float) -> bool:
+    """One window of the per-instance thermalization test (host only)."""
+    lib = load_library()
+    out = ctypes.c_int32()
+    rc = lib.icm_therm_update(ctypes.byref(state), ctypes.byref(crit), float(e), float(q_l), float(T_min),
+                              float(bonds_per_site), ctypes.byref(out))
+    if rc:
+        raise IcmError(rc, "icm_therm_update")
+    return bool(out.value)
 
 
 def energies_static(ctx: Context, lattice: int, L: int, disorder: int, couplings, spins, out):
@@ -217,6 +246,25 @@ class Batch:
 
     def clear_observables(self):
         self.ctx.check(self._lib.icm_clear_observables(self._h))
+
+    # -- serving: per-slot control
+    def set_slot(self, slot: int, couplings, spins=None, instance_id: int = 0):
+        cp, cf = _ptr(couplings)
+        sp, sf = _ptr(spins)
+        self.ctx.check(self._lib.icm_batch_set_slot(self._h, int(slot), cp, sp, int(instance_id), cf | sf))
+
+    def set_active(self, slot: int, active: bool):
+        self.ctx.check(self._lib.icm_batch_set_active(self._h, int(slot), int(bool(active))))
+
+    def start_window(self, slot: int, t_start: int):
+        self.ctx.check(self._lib.icm_batch_start_window(self._h, int(slot), int(t_start)))
+
+    def delta(self, k: int = 0):
+        """Eq. 2 over the batch at temperature position k: (mean, standard error, instances)."""
+        m, se, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32()
+        self.ctx.check(self._lib.icm_batch_delta(self._h, int(k), ctypes.byref(m), ctypes.byref(se),
+                                                 ctypes.byref(n)))
+        return m.value, se.value, n.value
 
     # -- reads
     def read_spins(self, out=None):
