@@ -293,13 +293,68 @@ def dataclasses_replace(r):
     return dataclasses.replace(r, arrival=0.0)
 
 
+MIXED = dict(sizes=(4, 6, 8, 10, 12), counts=(4096, 2048, 1024, 512, 256), T=(0.2, 2.0, 24), T_icm=1.0,
+             seed=0x1501056300000004,
+             desc="3D EA Gaussian, L in {4,6,8,10,12} x {4096,2048,1024,512,256} instances, 24 T geometric "
+                  "[0.2,2.0], ICM T<=1.0, one CUDA graph per step (one kernel per size on forked streams), "
+                  "CTA width autotuned per size")
+
+
+def run_mixed(args):
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    torch.cuda.set_device(0)
+    build.build()
+    stream = torch.cuda.current_stream()
+    ctx = icmpt.Context(0, stream.cuda_stream)
+    T = I.ladder(*MIXED["T"])
+    batches, updates, tuned = [], 0, {}
+    for L, n in zip(MIXED["sizes"], MIXED["counts"]):
+        N, Nb = icmpt.lattice_size(I.CUBIC3D, L)
+        ids = np.arange(n, dtype=np.uint32)
+        J = torch.from_numpy(I.couplings(Nb, I.GAUSS, MIXED["seed"] + L, ids)).cuda()
+        s0 = torch.from_numpy(I.initial_spins(N, 2 * len(T), MIXED["seed"] + L, ids)).cuda()
+        b = icmpt.Batch(ctx, I.CUBIC3D, L, I.GAUSS, J, T, MIXED["T_icm"], MIXED["seed"] + L, spins=s0)
+        th, ms = b.autotune(sweeps=8)
+        tuned[f"L{L}"] = {"threads": th, "ctas_per_sm": b.info()["ctas_per_sm"]}
+        batches.append(b)
+        updates += n * 2 * len(T) * N
+    S = args.sweeps_per_step
+    g = icmpt.Group(ctx, batches, S)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        g.run(1)
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.run(1)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+    ms = float(np.sum(times))
+    value = updates * S * args.steps / (ms * 1e6)
+    print(json.dumps({
+        "metric": "spin_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "3d_gauss_mixed", "desc": MIXED["desc"], "sweeps_per_step": S, "tuned": tuned,
+                   "l2": "flushed between steps (256 MB write)"},
+        "gpu_launches": args.steps, "clocks": clk.summary()}))
+    g.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving"])
+    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -316,6 +371,10 @@ def main():
     if args.workload == "serving":
         if int(os.environ.get("RANK", "0")) == 0:
             run_serving(args)
+        return
+    if args.workload == "3d_gauss_mixed":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_mixed(args)
         return
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))

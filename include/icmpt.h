@@ -255,6 +255,29 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
 icm_status icm_energies_static(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
                                int32_t n_rep, const void *couplings, const int8_t *spins, double *out);
 
+/* ---------------------------------------------------------------- launch shape
+ * The threads per CTA of a batch's kernel (32, 64, 96 or 128; one CTA runs one
+ * instance).  Gaussian results depend on it through the summation order of
+ * the fp32 energies; +-J results do not.                                   */
+icm_status icm_batch_set_threads(icm_batch *b, int32_t threads);
+/* Time every valid CTA width on `sweeps` sweeps of this batch and keep the
+ * fastest.  The batch's state (spins, energies, sweep counters, observables)
+ * is restored afterwards, so tuning does not advance the chain.  Allocates a
+ * temporary snapshot.                                                      */
+icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threads, float *best_ms);
+
+/* A group runs several batches (e.g. one per lattice size of a mixed-size
+ * workload) as one CUDA graph: each batch's kernel on its own forked stream,
+ * joined back into the context stream.  The graph is captured at creation
+ * with the batches' current schedules and launch shapes and `sweeps_per_launch`;
+ * icm_group_run replays it.  Create a group after the batches are set up
+ * and re-create it after changing a schedule or the threads of a batch.   */
+typedef struct icm_group icm_group;
+icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, uint32_t sweeps_per_launch,
+                            icm_group **out);
+icm_status icm_group_run(icm_group *g, uint32_t n_launches);
+icm_status icm_group_destroy(icm_group *g);
+
 /* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
  * dynamic shared memory bytes per CTA and kernel launches issued so far. */
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,

@@ -134,7 +134,7 @@ struct icm_batch {
     std::vector<double> T;
     icm_schedule sched{};
     icm::KParams kp{};
-    int threads = 0, grid = 0, ctas_per_sm = 0;
+    int threads = 0, grid = 0, ctas_per_sm = 0, n_icm = 0;
     int64_t launches = 0;
     std::vector<void *> allocs;
     // staging buffers for loads and reads
@@ -459,6 +459,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     }
     b->threads = threads;
     b->ctas_per_sm = ctas;
+    b->n_icm = n_icm;
     const int slots = ctx->num_sms * ctas;
     b->grid = n_inst < slots ? n_inst : slots;
 
@@ -876,6 +877,208 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
     *delta_mean = s1 / n;
     if (delta_se) *delta_se = n > 1 ? std::sqrt(std::fmax(s2 / n - (s1 / n) * (s1 / n), 0.0) / (n - 1)) : 0.0;
     if (n_used) *n_used = n;
+    return ICM_OK;
+}
+
+// ---------------------------------------------------------------- launch shape, groups, autotuning
+
+static icm_status apply_threads(icm_batch *b, int threads)
+{
+    icm::KParams &P = b->kp;
+    if (threads < 32 || threads > icm::kMaxThreads || threads % 32)
+        return fail(b->ctx, ICM_ERR_ARG, "threads per CTA must be 32, 64, 96 or 128");
+    const int half = P.N / 2;
+    if (((half + threads - 1) / threads) * P.Z >= 256 || (P.N + threads - 1) / threads >= 256)
+        return fail(b->ctx, ICM_ERR_UNSUPPORTED, "too many sites per thread for the observable counters");
+    const icm::SmemLayout sm = icm::smem_layout(P.N, P.Z, P.R, P.G, P.nT, b->n_icm, threads / 32, b->gauss);
+    if (sm.total > b->ctx->max_smem_optin) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "shared memory");
+    int ctas = 0;
+    cudaError_t e = icm::fused_occupancy(b->gauss, P.Z, threads, sm.total, &ctas);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "occupancy");
+    if (ctas < 1) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "kernel does not fit");
+    P.sm = sm;
+    P.small_counts = (((half + threads - 1) / threads) * P.Z < 16 && (P.N + threads - 1) / threads < 16) ? 1 : 0;
+    b->threads = threads;
+    b->ctas_per_sm = ctas;
+    const int slots = b->ctx->num_sms * ctas;
+    b->grid = b->n_inst < slots ? b->n_inst : slots;
+    return ICM_OK;
+}
+
+icm_status icm_batch_set_threads(icm_batch *b, int32_t threads)
+{
+    if (!b) return ICM_ERR_ARG;
+    return apply_threads(b, threads);
+}
+
+icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threads, float *best_ms)
+{
+    if (!b || sweeps == 0) return ICM_ERR_ARG;
+    icm_ctx *ctx = b->ctx;
+    icm::KParams &P = b->kp;
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    // snapshot of everything a launch changes, restored after the trials
+    struct Piece { void *dst; size_t bytes; void *save; };
+    Piece pieces[] = {
+        {P.spins, (size_t)b->n_inst * P.G * P.N * 4, nullptr},
+        {b->gauss ? (void *)P.Ef : (void *)P.Ei, (size_t)b->n_inst * P.R * 4, nullptr},
+        {P.tsweep, (size_t)b->n_inst * 4, nullptr},
+        {P.accE, nk * 8, nullptr},
+        {P.acc64, 4 * nk * 8, nullptr},
+        {P.hist, nk * (P.N + 1) * 8, nullptr},
+        {P.n_meas, (size_t)b->n_inst * 8, nullptr},
+    };
+    icm_status st = ICM_OK;
+    for (auto &pc : pieces) {
+        if (cudaMalloc(&pc.save, pc.bytes) != cudaSuccess) {
+            (void)cudaGetLastError();
+            st = fail(ctx, ICM_ERR_OOM, "autotune snapshot");
+            break;
+        }
+        if (cudaMemcpyAsync(pc.save, pc.dst, pc.bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+            st = fail(ctx, ICM_ERR_CUDA, "autotune snapshot copy");
+            break;
+        }
+    }
+    const int original = b->threads;
+    int best = original;
+    float best_t = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        st = fail(ctx, ICM_ERR_CUDA, "events");
+    for (int th = 32; !st && th <= icm::kMaxThreads; th += 32) {
+        if (apply_threads(b, th) != ICM_OK) continue;
+        if ((st = icm_run_sweeps(b, sweeps))) break;               // warm-up
+        cudaEventRecord(e0, ctx->stream);
+        if ((st = icm_run_sweeps(b, sweeps))) break;
+        cudaEventRecord(e1, ctx->stream);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_t) {
+            best_t = ms;
+            best = th;
+        }
+        b->launches -= 2;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    for (auto &pc : pieces)
+        if (pc.save) {
+            cudaMemcpyAsync(pc.dst, pc.save, pc.bytes, cudaMemcpyDeviceToDevice, ctx->stream);
+        }
+    cudaStreamSynchronize(ctx->stream);
+    for (auto &pc : pieces)
+        if (pc.save) cudaFree(pc.save);
+    icm_status st2 = apply_threads(b, st ? original : best);
+    if (st) return st;
+    if (st2) return st2;
+    if (best_threads) *best_threads = best;
+    if (best_ms) *best_ms = best_t;
+    return ICM_OK;
+}
+
+}  // extern "C"
+
+struct icm_group {
+    icm_ctx *ctx = nullptr;
+    std::vector<icm_batch *> batches;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint32_t sweeps = 0;
+    int64_t launches = 0;
+};
+
+static void destroy_group(icm_group *g)
+{
+    if (!g) return;
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
+    for (auto e : g->events) cudaEventDestroy(e);
+    for (auto s : g->streams) cudaStreamDestroy(s);
+    delete g;
+}
+
+extern "C" {
+
+icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, uint32_t sweeps_per_launch,
+                            icm_group **out)
+{
+    if (!ctx || !batches || n < 1 || !out || sweeps_per_launch == 0) return ICM_ERR_ARG;
+    *out = nullptr;
+    for (int i = 0; i < n; ++i)
+        if (!batches[i] || batches[i]->ctx != ctx) return fail(ctx, ICM_ERR_ARG, "batches must belong to the context");
+    icm_group *g = new (std::nothrow) icm_group();
+    if (!g) return ICM_ERR_OOM;
+    g->ctx = ctx;
+    g->batches.assign(batches, batches + n);
+    g->sweeps = sweeps_per_launch;
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        cudaStream_t s;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) g->streams.push_back(s);
+    }
+    for (int i = 0; i < n + 1 && e == cudaSuccess; ++i) {
+        cudaEvent_t ev;
+        e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) g->events.push_back(ev);
+    }
+    // capture: fork one stream per batch from the context stream, join back
+    cudaStream_t origin = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(g->events[n], origin);
+    for (int i = 0; i < n && e == cudaSuccess; ++i) {
+        icm_batch *b = g->batches[i];
+        e = cudaStreamWaitEvent(g->streams[i], g->events[n], 0);
+        if (e != cudaSuccess) break;
+        icm::KParams P = b->kp;
+        P.icm_every = b->sched.icm_every;
+        P.swap_every = b->sched.swap_every;
+        P.enable_2a = b->sched.enable_2a;
+        P.enable_metropolis = b->sched.enable_metropolis;
+        P.trace = b->sched.trace;
+        P.t_meas = b->sched.t_meas;
+        P.active = b->d_active;
+        P.t_meas_inst = b->d_tmeas;
+        e = icm::launch_fused(P, b->gauss, b->threads, b->grid, sweeps_per_launch, g->streams[i]);
+        if (e == cudaSuccess) e = cudaEventRecord(g->events[i], g->streams[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, g->events[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+    if (e == cudaSuccess) e = ec;
+    g->graph = graph;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (origin) cudaStreamDestroy(origin);
+    if (e != cudaSuccess) {
+        destroy_group(g);
+        return cuda_fail(ctx, e, "group capture");
+    }
+    *out = g;
+    return ICM_OK;
+}
+
+icm_status icm_group_run(icm_group *g, uint32_t n_launches)
+{
+    if (!g) return ICM_ERR_ARG;
+    for (uint32_t i = 0; i < n_launches; ++i) {
+        ICM_CUDA(g->ctx, cudaGraphLaunch(g->exec, g->ctx->stream));
+        g->launches += 1;
+        for (auto *b : g->batches) b->launches += 1;
+    }
+    return ICM_OK;
+}
+
+icm_status icm_group_destroy(icm_group *g)
+{
+    if (!g) return ICM_ERR_ARG;
+    cudaStreamSynchronize(g->ctx->stream);
+    destroy_group(g);
     return ICM_OK;
 }
 

@@ -45,7 +45,8 @@ EXPORTS = [
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
-    "icm_batch_start_window", "icm_therm_update", "icm_batch_delta",
+    "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
+    "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy",
 ]
 
 
@@ -96,6 +97,11 @@ def load_library(path: str = LIB_PATH):
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(i32)]
         L.icm_batch_delta.argtypes = [vp, i32, vp, vp, vp]
+        L.icm_batch_set_threads.argtypes = [vp, i32]
+        L.icm_batch_autotune.argtypes = [vp, u32, vp, vp]
+        L.icm_group_create.argtypes = [vp, vp, i32, u32, ctypes.POINTER(vp)]
+        L.icm_group_run.argtypes = [vp, u32]
+        L.icm_group_destroy.argtypes = [vp]
         for name in EXPORTS:
             if name != "icm_last_error":
                 getattr(L, name).restype = i32
@@ -305,6 +311,15 @@ class Batch:
             "n_pre", "flip2a", "seed_site", "csize", "esum_before", "esum_after", "swap_acc")], 0))
         return tr
 
+    def set_threads(self, threads: int):
+        self.ctx.check(self._lib.icm_batch_set_threads(self._h, int(threads)))
+
+    def autotune(self, sweeps: int = 16):
+        """Pick the fastest CTA width; the batch's state is left unchanged."""
+        th, ms = ctypes.c_int32(), ctypes.c_float()
+        self.ctx.check(self._lib.icm_batch_autotune(self._h, int(sweeps), ctypes.byref(th), ctypes.byref(ms)))
+        return th.value, ms.value
+
     def info(self) -> dict:
         t, c, g, s = (ctypes.c_int32() for _ in range(4))
         la = ctypes.c_int64()
@@ -315,6 +330,33 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and getattr(self.ctx, "_h", None):
             self._lib.icm_batch_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Group:
+    """Several batches replayed as one CUDA graph (one forked stream per batch)."""
+
+    def __init__(self, ctx: Context, batches, sweeps_per_launch: int):
+        self.ctx, self._lib, self.batches = ctx, ctx._lib, list(batches)
+        arr = (ctypes.c_void_p * len(self.batches))(*[b._h for b in self.batches])
+        h = ctypes.c_void_p()
+        ctx.check(self._lib.icm_group_create(ctx._h, arr, len(self.batches), int(sweeps_per_launch),
+                                             ctypes.byref(h)))
+        self._h = h
+        self.sweeps = int(sweeps_per_launch)
+
+    def run(self, n_launches: int = 1):
+        self.ctx.check(self._lib.icm_group_run(self._h, int(n_launches)))
+
+    def close(self):
+        if getattr(self, "_h", None) and getattr(self.ctx, "_h", None):
+            self._lib.icm_group_destroy(self._h)
         self._h = None
 
     def __del__(self):
