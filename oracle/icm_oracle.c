@@ -420,3 +420,42 @@ int orc_run(const orc_problem *P, orc_state *S, uint32_t n_sweeps, const orc_tra
 
 /* Energy of one configuration, for tests. */
 double orc_energy(const orc_problem *P, const int8_t *s) { return energy(P, s); }
+
+/* ------------------------------------------------------------------------ */
+/* Site percolation (Supplemental Material): size of the largest connected
+ * cluster of occupied sites of each mask, by breadth-first search over the
+ * bond list.  masks: [n][N] bytes (nonzero = occupied); smax: [n].          */
+int orc_largest_clusters(int32_t N, int32_t Nb, const int32_t *bi, const int32_t *bj, int32_t n,
+                         const uint8_t *masks, int32_t *smax)
+{
+    orc_problem P;
+    memset(&P, 0, sizeof P);
+    P.N = N; P.Nb = Nb; P.bi = bi; P.bj = bj;
+    adjacency A;
+    if (build_adjacency(&P, &A)) return -2;
+    int32_t *queue = malloc(sizeof(int32_t) * (size_t)(N > 0 ? N : 1));
+    uint8_t *seen = malloc((size_t)(N > 0 ? N : 1));
+    for (int m = 0; m < n; ++m) {
+        const uint8_t *occ = masks + (size_t)m * N;
+        memset(seen, 0, (size_t)N);
+        int best = 0;
+        for (int s = 0; s < N; ++s) {
+            if (!occ[s] || seen[s]) continue;
+            int head = 0, tail = 0;
+            queue[tail++] = s;
+            seen[s] = 1;
+            while (head < tail) {
+                int i = queue[head++];
+                for (int e = A.start[i]; e < A.start[i + 1]; ++e) {
+                    int j = A.nbr[e];
+                    if (occ[j] && !seen[j]) { seen[j] = 1; queue[tail++] = j; }
+                }
+            }
+            if (tail > best) best = tail;
+        }
+        smax[m] = best;
+    }
+    free(queue); free(seen);
+    free_adjacency(&A);
+    return 0;
+}

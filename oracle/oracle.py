@@ -72,6 +72,8 @@ def lib():
             L.orc_geometry.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 3
             L.orc_run.argtypes = [ctypes.POINTER(_Problem), ctypes.POINTER(_State), ctypes.c_uint32,
                                   ctypes.POINTER(_Trace)]
+            L.orc_largest_clusters.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p,
+                                               ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]
             L.orc_energy.argtypes = [ctypes.POINTER(_Problem), ctypes.c_void_p]
             L.orc_energy.restype = ctypes.c_double
             _lib = L
@@ -174,3 +176,18 @@ class Instance:
             P_n=self.hist / float(m),
             n_meas=int(self.n_meas[0]),
         )
+
+
+def largest_clusters(geom: Geometry, masks) -> np.ndarray:
+    """Largest occupied cluster of every mask (site percolation), int32 [n]."""
+    m = np.ascontiguousarray(masks, dtype=np.uint8).reshape(-1, geom.N)
+    out = np.zeros(m.shape[0], dtype=np.int32)
+    if lib().orc_largest_clusters(geom.N, geom.Nb, _p(geom.bi), _p(geom.bj), m.shape[0], _p(m), _p(out)):
+        raise RuntimeError("orc_largest_clusters failed")
+    return out
+
+
+def binder_ratio(smax_fraction) -> float:
+    """g = (1/2)(3 - <s^4>/<s^2>^2) of the largest-cluster fraction (Supplemental Material)."""
+    s = np.asarray(smax_fraction, dtype=np.float64)
+    return 0.5 * (3.0 - np.mean(s ** 4) / np.mean(s ** 2) ** 2)

@@ -329,3 +329,56 @@ def test_bimodal_keeps_clusters_at_low_temperature():
     g, J, obs = _chains(O.SQUARE2D, 6, I.PM_J, I.ladder(0.1, 1.5, 8), T_icm=1.0,
                         n_chains=6, sweeps=1500)
     assert np.mean([o["p"][0] for o in obs]) > 0.01
+
+
+# ----------------------------------------------------------------------------- site percolation
+def _thresholds():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "percolation_thresholds.txt")
+    out = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f = line.split()
+            out[f[0]] = (float(f[1]), float(f[2]))
+    return out
+
+
+@pytest.mark.parametrize("kind,L", [(O.SQUARE2D, 6), (O.CUBIC3D, 4), (O.CHIMERA, 3), (O.CHIMERA, 1)])
+def test_largest_cluster_matches_scipy(kind, L):
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    g = O.Geometry(kind, L)
+    masks = np.concatenate([I.site_masks(g.N, p, 17, 40) for p in (0.0, 0.2, 0.4, 0.6, 1.0)])
+    got = O.largest_clusters(g, masks)
+    for m, s in zip(masks, got):
+        occ = m.astype(bool)
+        keep = occ[g.bi] & occ[g.bj]
+        A = coo_matrix((np.ones(keep.sum()), (g.bi[keep], g.bj[keep])), shape=(g.N, g.N))
+        _, lab = connected_components(A, directed=False)
+        want = np.bincount(lab[occ]).max() if occ.any() else 0
+        assert s == want
+
+
+@pytest.mark.parametrize("name,kind,sizes,half_window,tol", [
+    ("square2d", O.SQUARE2D, (8, 16), 0.05, 0.02),
+    ("cubic3d", O.CUBIC3D, (4, 8), 0.05, 0.03),
+    ("chimera", O.CHIMERA, (8, 16), 0.03, 0.012),
+])
+def test_binder_crossing_near_printed_threshold(name, kind, sizes, half_window, tol):
+    """The Binder ratios g = (3 - <s^4>/<s^2>^2)/2 of the largest-cluster
+    fraction of two sizes cross near the threshold the paper prints (Fig. 1
+    caption, Supplemental Material).  The sizes are small, so a finite-size
+    shift of the crossing (toward lower p here) is part of the tolerance."""
+    pc, _ = _thresholds()[name]
+    ps = np.linspace(pc - half_window, pc + half_window, 9)
+    curves = []
+    for L in sizes:
+        g = O.Geometry(kind, L)
+        curves.append([O.binder_ratio(O.largest_clusters(g, I.site_masks(g.N, p, 100 + L, 6000)) / g.N)
+                       for p in ps])
+    d = np.array(curves[1]) - np.array(curves[0])
+    i = np.flatnonzero(np.diff(np.sign(d)) != 0)
+    assert len(i) >= 1
+    cross = [ps[j] - d[j] * (ps[j + 1] - ps[j]) / (d[j + 1] - d[j]) for j in i]
+    best = min(cross, key=lambda c: abs(c - pc))
+    assert abs(best - pc) < tol, (cross, pc)
