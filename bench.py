@@ -348,13 +348,50 @@ def run_mixed(args):
     g.close()
 
 
+def run_percolation(args):
+    """Binder ratio of the largest-cluster fraction on chimera C_8, C_16, C_32
+    (device-drawn masks) and the crossing estimate of p_c (Supplemental
+    Material prints p_c = 0.3866(3))."""
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = icmpt.Context(0)
+    sizes, n = (8, 16, 32), args.masks
+    ps = np.round(np.linspace(0.370, 0.400, 7), 4)
+    g = {}
+    total_sites, t0 = 0, time.perf_counter()
+    for M in sizes:
+        N, _ = icmpt.lattice_size(I.CHIMERA, M)
+        row = []
+        for p in ps:
+            s = icmpt.largest_clusters_random(ctx, I.CHIMERA, M, float(p), 0x1501056300000005 + M, n) / N
+            row.append(0.5 * (3.0 - np.mean(s ** 4) / np.mean(s ** 2) ** 2))
+            total_sites += n * N
+        g[M] = np.array(row)
+    wall = time.perf_counter() - t0
+
+    def cross(a, b):
+        d = b - a
+        i = np.flatnonzero(np.diff(np.sign(d)) != 0)
+        return [float(ps[j] - d[j] * (ps[j + 1] - ps[j]) / (d[j + 1] - d[j])) for j in i]
+    out = {"metric": "percolation_sites_per_ns", "value": total_sites / wall / 1e9, "unit": "sites/ns",
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "percolation", "lattice": "chimera", "sizes": list(sizes), "masks_per_p": n,
+                      "p": ps.tolist()},
+           "binder": {f"C{M}": [round(float(x), 4) for x in g[M]] for M in sizes},
+           "crossing_C8_C16": cross(g[8], g[16]), "crossing_C16_C32": cross(g[16], g[32]),
+           "paper_pc": 0.3866, "wall_s": wall}
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed"])
+    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -362,6 +399,7 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--serving-nT", default="16,24,32")
     ap.add_argument("--alone-sample", type=int, default=8)
+    ap.add_argument("--masks", type=int, default=40000)
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--ref-sweeps", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -371,6 +409,10 @@ def main():
     if args.workload == "serving":
         if int(os.environ.get("RANK", "0")) == 0:
             run_serving(args)
+        return
+    if args.workload == "percolation":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_percolation(args)
         return
     if args.workload == "3d_gauss_mixed":
         if int(os.environ.get("RANK", "0")) == 0:

@@ -255,6 +255,22 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
 icm_status icm_energies_static(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
                                int32_t n_rep, const void *couplings, const int8_t *spins, double *out);
 
+/* ---------------------------------------------------------------- site percolation
+ * Largest cluster of occupied sites (Supplemental Material: the relative
+ * size s_max of the largest cluster, whose Binder ratio
+ * g = (3 - <s_max^4>/<s_max^2>^2)/2 locates the percolation threshold).
+ * Clusters are connected through the lattice's bonds (icm_lattice).
+ *   masks : [n_masks][N] bytes in site order, nonzero = occupied
+ *   smax  : [n_masks] int32, number of sites of the largest cluster
+ * Host or device buffers (ICM_DEVICE_PTR).  The call waits for its work.  */
+icm_status icm_percolation(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t n_masks, const uint8_t *masks,
+                           int32_t *smax, uint32_t flags);
+/* The same on random masks drawn on the device: site i of mask m is
+ * occupied iff word 0 of Philox4x32-10(ctr {i, m, 0, 5 << 24}, key = seed)
+ * is below floor(p 2^32) (p = 1: every site).                             */
+icm_status icm_percolation_random(icm_ctx *ctx, int32_t lattice, int32_t L, double p, uint64_t seed,
+                                  int32_t n_masks, int32_t *smax, uint32_t flags);
+
 /* ---------------------------------------------------------------- launch shape
  * The threads per CTA of a batch's kernel (32, 64, 96 or 128; one CTA runs one
  * instance).  Gaussian results depend on it through the summation order of

@@ -46,7 +46,8 @@ EXPORTS = [
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
-    "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy",
+    "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
+    "icm_percolation_random",
 ]
 
 
@@ -102,6 +103,8 @@ def load_library(path: str = LIB_PATH):
         L.icm_group_create.argtypes = [vp, vp, i32, u32, ctypes.POINTER(vp)]
         L.icm_group_run.argtypes = [vp, u32]
         L.icm_group_destroy.argtypes = [vp]
+        L.icm_percolation.argtypes = [vp, i32, i32, i32, vp, vp, u32]
+        L.icm_percolation_random.argtypes = [vp, i32, i32, ctypes.c_double, u64, i32, vp, u32]
         for name in EXPORTS:
             if name != "icm_last_error":
                 getattr(L, name).restype = i32
@@ -166,6 +169,30 @@ class Context:
             self.close()
         except Exception:
             pass
+
+
+def largest_clusters(ctx: Context, lattice: int, L: int, masks) -> np.ndarray:
+    """Largest occupied cluster of each mask [n][N] (site percolation)."""
+    N, _ = lattice_size(lattice, L)
+    m = masks if hasattr(masks, "data_ptr") else np.ascontiguousarray(masks, dtype=np.uint8).reshape(-1, N)
+    n = int(m.shape[0])
+    mp, f = _ptr(m)
+    if f:
+        import torch
+        out_t = torch.empty(n, dtype=torch.int32, device=m.device)
+        ctx.check(ctx._lib.icm_percolation(ctx._h, int(lattice), int(L), n, mp, out_t.data_ptr(), f))
+        return out_t.cpu().numpy()
+    out = np.empty(n, dtype=np.int32)
+    ctx.check(ctx._lib.icm_percolation(ctx._h, int(lattice), int(L), n, mp, out.ctypes.data, 0))
+    return out
+
+
+def largest_clusters_random(ctx: Context, lattice: int, L: int, p: float, seed: int, n_masks: int) -> np.ndarray:
+    """Largest cluster of n_masks random masks (occupation p) drawn on the device."""
+    out = np.empty(int(n_masks), dtype=np.int32)
+    ctx.check(ctx._lib.icm_percolation_random(ctx._h, int(lattice), int(L), float(p),
+                                              int(seed) & 0xFFFFFFFFFFFFFFFF, int(n_masks), out.ctypes.data, 0))
+    return out
 
 
 def therm_update(state: ThermState, crit: ThermCriterion, e: float, q_l: float, T_min: float,
