@@ -348,6 +348,50 @@ def run_mixed(args):
     g.close()
 
 
+THERMO = [
+    # Table I (geometric ladders; N_c lowest temperatures get cluster moves), reduced instance counts
+    dict(name="2D N=256", lattice=I.SQUARE2D, L=16, T=(0.2120, 1.6325, 30), n_c=30),
+    dict(name="chimera N=288", lattice=I.CHIMERA, L=6, T=(0.2120, 1.6325, 30), n_c=19),
+    dict(name="3D N=216", lattice=I.CUBIC3D, L=6, T=(0.4200, 1.8000, 26), n_c=13),
+]
+
+
+def run_thermalization(args):
+    """Delta(t) of Eq. 2 for PT, PT+ICM and HCA on reduced Table I systems and
+    the automated thermalization-time ratio PT / PT+ICM (Fig. 2, Fig. 3)."""
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    from paper_1501_05630_gb300.experiments import delta_curve, thermalization_time
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = icmpt.Context(0)
+    out = {"metric": "thermalization_speedup", "unit": "PT sweeps / PT+ICM sweeps", "higher_is_better": True,
+           "n_gpus": 1, "data": "synthetic", "config": {"workload": "thermalization", "instances": args.instances,
+                                                       "log2_sweeps": [4, args.log2_max]}, "systems": {}}
+    t0 = time.perf_counter()
+    ratios = []
+    for sysd in THERMO:
+        T = I.ladder(*sysd["T"])
+        T_icm = float(T[sysd["n_c"] - 1]) + 1e-9
+        N, Nb = icmpt.lattice_size(sysd["lattice"], sysd["L"])
+        seed = 0x1501056300000006 + sysd["L"]
+        J = I.couplings(Nb, I.GAUSS, seed, range(args.instances))
+        s0 = I.initial_spins(N, 2 * len(T), seed, range(args.instances))
+        res = {}
+        for m in ("pt", "icm", "hca"):
+            c = delta_curve(ctx, sysd["lattice"], sysd["L"], I.GAUSS, J, s0, T, T_icm, seed, m, 4, args.log2_max)
+            res[m] = {"t": c.t.tolist(), "delta": [round(float(x), 5) for x in c.delta],
+                      "se": [round(float(x), 5) for x in c.se], "t_therm": thermalization_time(c, nsig=2.0)}
+        tp, ti = res["pt"]["t_therm"], res["icm"]["t_therm"]
+        res["ratio_pt_over_icm"] = (tp / ti) if (tp and ti) else None
+        if res["ratio_pt_over_icm"]:
+            ratios.append(res["ratio_pt_over_icm"])
+        out["systems"][sysd["name"]] = res
+    out["value"] = float(np.exp(np.mean(np.log(ratios)))) if ratios else None
+    out["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 def run_percolation(args):
     """Binder ratio of the largest-cluster fraction on chimera C_8, C_16, C_32
     (device-drawn masks) and the crossing estimate of p_c (Supplemental
@@ -391,7 +435,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation"])
+    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation", "thermalization"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -400,6 +444,8 @@ def main():
     ap.add_argument("--serving-nT", default="16,24,32")
     ap.add_argument("--alone-sample", type=int, default=8)
     ap.add_argument("--masks", type=int, default=40000)
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--log2-max", type=int, default=17)
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--ref-sweeps", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -409,6 +455,10 @@ def main():
     if args.workload == "serving":
         if int(os.environ.get("RANK", "0")) == 0:
             run_serving(args)
+        return
+    if args.workload == "thermalization":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_thermalization(args)
         return
     if args.workload == "percolation":
         if int(os.environ.get("RANK", "0")) == 0:

@@ -1,0 +1,78 @@
+"""Thermalization experiments of the paper at reduced scale (Fig. 2, Fig. 3).
+
+For one method -- plain parallel tempering (no cluster moves), PT with the
+isoenergetic cluster moves (ICM at T_k <= T_icm, with step 2a), or the
+Houdayer algorithm (HCA: cluster moves at every temperature, no step 2a) --
+a batch of disorder instances is run in doubling windows [2^(b-1), 2^b) and
+Delta(t) of Eq. 2 (disorder average of E(q_l) - <H>/N at the lowest
+temperature, with its standard error) is recorded at t = 2^b.  The paper
+read thermalization times "by eye"; here the thermalization time is the
+first t = 2^b from which |Delta| stays within `nsig` standard errors (and
+`floor`) for every later window of the run.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import icmpt
+
+METHODS = ("pt", "icm", "hca")
+
+
+@dataclass
+class DeltaCurve:
+    method: str
+    t: np.ndarray          # window ends 2^b
+    delta: np.ndarray      # Eq. 2 at the lowest temperature
+    se: np.ndarray         # standard error over instances
+
+
+def method_schedule(method: str, T_icm: float):
+    """(T_icm, icm_every, enable_2a) of a method."""
+    if method == "pt":
+        return T_icm, 0, 1
+    if method == "icm":
+        return T_icm, 1, 1
+    if method == "hca":
+        return float("inf"), 1, 0
+    raise ValueError(method)
+
+
+def delta_curve(ctx, lattice: int, L: int, disorder: int, couplings, spins, T, T_icm: float, seed: int,
+                method: str, log2_min: int, log2_max: int, instance_ids=None) -> DeltaCurve:
+    ticm, every, two_a = method_schedule(method, T_icm)
+    b = icmpt.Batch(ctx, lattice, L, disorder, couplings, T, min(ticm, 1e300), seed, spins=spins,
+                    instance_ids=instance_ids)
+    b.set_schedule(icm_every=every, enable_2a=two_a, t_meas=1 << 62)
+    ts, ds, ses = [], [], []
+    t = 0
+    start = 1 << (log2_min - 1)
+    if start > 0:
+        b.run(start)
+        t = start
+    for k in range(log2_min, log2_max + 1):
+        b.clear_observables()
+        b.set_schedule(t_meas=t)
+        end = 1 << k
+        b.run(end - t)
+        t = end
+        m, se, _ = b.delta(0)
+        ts.append(t)
+        ds.append(m)
+        ses.append(se)
+    b.close()
+    return DeltaCurve(method, np.array(ts), np.array(ds), np.array(ses))
+
+
+def thermalization_time(curve: DeltaCurve, nsig: float = 2.0, floor: float = 0.0):
+    """First window end from which |Delta| <= max(nsig * se, floor) holds for
+    every later window; None if the last window does not satisfy it."""
+    ok = np.abs(curve.delta) <= np.maximum(nsig * curve.se, floor)
+    if not ok[-1]:
+        return None
+    i = len(ok) - 1
+    while i > 0 and ok[i - 1]:
+        i -= 1
+    return int(curve.t[i])

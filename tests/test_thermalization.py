@@ -1,0 +1,79 @@
+"""Reduced-scale thermalization experiments (Fig. 2 / Fig. 3 of the paper).
+
+CPU: the automated thermalization time of a Delta(t) curve.
+GPU: Delta(t) of Eq. 2 from the library for +-J couplings equals the value
+computed from the oracle's accumulators of the same windows (exact
+integers), for plain PT, PT+ICM and HCA; with Gaussian couplings PT+ICM
+drives Delta to zero within errors on a small lattice."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1501_05630_gb300 import inputs as I
+
+
+def test_thermalization_time_rule():
+    from paper_1501_05630_gb300.experiments import DeltaCurve, thermalization_time
+    t = np.array([16, 32, 64, 128, 256])
+    c = DeltaCurve("x", t, np.array([-0.5, -0.1, 0.01, -0.2, 0.0]), np.array([0.05] * 5))
+    assert thermalization_time(c) == 256                      # a later excursion resets it
+    c2 = DeltaCurve("x", t, np.array([-0.5, -0.09, 0.01, 0.02, 0.0]), np.array([0.05] * 5))
+    assert thermalization_time(c2) == 32
+    c3 = DeltaCurve("x", t, np.array([-0.5, -0.3, -0.2, -0.2, -0.2]), np.array([0.01] * 5))
+    assert thermalization_time(c3) is None
+    assert thermalization_time(c3, floor=0.25) == 64
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA GPU")
+    from paper_1501_05630_gb300 import build, icmpt
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = icmpt.Context(0)
+    yield icmpt, ctx
+    ctx.close()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("method", ["pt", "icm", "hca"])
+def test_delta_curve_equals_oracle_windows(env, method):
+    icmpt, ctx = env
+    from paper_1501_05630_gb300.experiments import delta_curve, method_schedule
+    g = O.Geometry(O.SQUARE2D, 8)
+    T = I.ladder(0.3, 1.6, 8)
+    n, seed = 8, 123
+    J = I.couplings(g.Nb, I.PM_J, seed, range(n))
+    s0 = I.initial_spins(g.N, 16, seed, range(n))
+    c = delta_curve(ctx, O.SQUARE2D, 8, I.PM_J, J, s0, T, 1.0, seed, method, 3, 7)
+    ticm, every, two_a = method_schedule(method, 1.0)
+    for w, t_end in enumerate(c.t):
+        d = []
+        for a in range(n):
+            r = O.Instance(g, J[a].astype(np.float64), T, s0[a], pm=True, T_icm=ticm, seed=seed, inst=a,
+                           icm_every=every, enable_2a=bool(two_a), t_meas=t_end // 2)
+            r.run(int(t_end))
+            m = r.n_meas[0]
+            e = r.accE[0] / (2 * g.N * m)
+            ql = 1 - 2 * r.acc_d[0] / (g.Nb * m)
+            d.append(-(g.Nb / g.N) * (1 - ql) / T[0] - e)
+        d = np.array(d)
+        assert c.delta[w] == pytest.approx(d.mean(), rel=1e-12, abs=1e-12)
+        assert c.se[w] == pytest.approx(d.std() / np.sqrt(n - 1), rel=1e-9, abs=1e-12)
+
+
+@pytest.mark.gpu
+def test_icm_drives_delta_to_zero_gaussian(env):
+    icmpt, ctx = env
+    from paper_1501_05630_gb300.experiments import delta_curve, thermalization_time
+    N, Nb = icmpt.lattice_size(I.SQUARE2D, 8)
+    T = I.ladder(0.3, 1.6, 16)
+    n = 256
+    J = I.couplings(Nb, I.GAUSS, 9, range(n))
+    s0 = I.initial_spins(N, 32, 9, range(n))
+    c = delta_curve(ctx, I.SQUARE2D, 8, I.GAUSS, J, s0, T, 2.0, 9, "icm", 4, 13)
+    assert c.delta[0] < -3 * c.se[0]                          # far from equilibrium at first
+    assert abs(c.delta[-1]) <= 3 * c.se[-1] + 2e-3            # Eq. 1 holds at the end
+    assert thermalization_time(c, nsig=3.0) is not None
