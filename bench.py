@@ -392,6 +392,43 @@ def run_thermalization(args):
     print(json.dumps(out))
 
 
+def run_annealing(args):
+    """Simulated annealing with and without isoenergetic cluster moves at
+    equal sweeps (the ground-state use the paper proposes): mean final energy
+    per spin and how often each variant reaches the lowest energy found."""
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    from paper_1501_05630_gb300.experiments import anneal
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = icmpt.Context(0)
+    out = {"metric": "annealing_residual_energy_per_spin", "unit": "energy/spin", "higher_is_better": False,
+           "n_gpus": 1, "data": "synthetic", "config": {"workload": "annealing", "instances": args.instances,
+                                                       "schedule": "T 3.0 -> 0.05 geometric, 64 steps x 32 sweeps"},
+           "systems": {}}
+    t0 = time.perf_counter()
+    for name, lat, L in (("3D L=6 Gaussian", I.CUBIC3D, 6), ("chimera C_6 Gaussian", I.CHIMERA, 6),
+                         ("2D L=16 Gaussian", I.SQUARE2D, 16)):
+        N, Nb = icmpt.lattice_size(lat, L)
+        seed = 0x1501056300000007 + L
+        J = I.couplings(Nb, I.GAUSS, seed, range(args.instances))
+        s0 = I.initial_spins(N, 2, seed, range(args.instances))
+        e = {}
+        for icm in (False, True):
+            b = anneal(ctx, lat, L, I.GAUSS, J, s0, 3.0, 0.05, 64, 32, icm, seed)
+            e[icm] = b.read_energies().min(axis=1) / N
+            b.close()
+        best = np.minimum(e[False], e[True])
+        out["systems"][name] = {
+            "mean_e_sa": float(e[False].mean()), "mean_e_sa_icm": float(e[True].mean()),
+            "residual_sa": float((e[False] - best).mean()), "residual_sa_icm": float((e[True] - best).mean()),
+            "frac_best_sa": float(np.mean(e[False] <= best + 1e-6)),
+            "frac_best_sa_icm": float(np.mean(e[True] <= best + 1e-6))}
+    out["value"] = float(np.mean([v["residual_sa_icm"] for v in out["systems"].values()]))
+    out["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 def run_percolation(args):
     """Binder ratio of the largest-cluster fraction on chimera C_8, C_16, C_32
     (device-drawn masks) and the crossing estimate of p_c (Supplemental
@@ -435,7 +472,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation", "thermalization"])
+    ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation", "thermalization",
+                                                                   "annealing"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -459,6 +497,10 @@ def main():
     if args.workload == "thermalization":
         if int(os.environ.get("RANK", "0")) == 0:
             run_thermalization(args)
+        return
+    if args.workload == "annealing":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_annealing(args)
         return
     if args.workload == "percolation":
         if int(os.environ.get("RANK", "0")) == 0:

@@ -129,7 +129,7 @@ icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_
  *   instance_ids : [n_inst] uint32 < 2^24, the instance's RNG key.
  *               NULL = 0 .. n_inst-1.
  *   T         : [n_T] temperatures, strictly ascending, > 0 (position k = 0
- *               is the lowest temperature); 2 <= n_T <= 32.
+ *               is the lowest temperature); 1 <= n_T <= 32.
  *   T_icm     : steps 2a/2b run at every k with T_k <= T_icm.
  *   seed      : 64-bit Philox key.
  * The schedule starts at its defaults; the sweep counter of every instance
@@ -147,6 +147,13 @@ icm_status icm_batch_destroy(icm_batch *b);
  * Layouts as in icm_batch_create.                                          */
 icm_status icm_batch_load(icm_batch *b, const void *couplings, const int8_t *spins,
                           uint32_t t0, uint32_t flags);
+
+/* Replace the temperature ladder (same n_T; ascending, > 0) and T_icm, e.g.
+ * between the steps of an annealing schedule ("convergence of simulated
+ * annealing ... improved by adding isoenergetic cluster moves at each
+ * temperature step").  Takes effect from the next icm_run_sweeps; the
+ * configurations, energies and sweep counters are kept.                   */
+icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, double T_icm);
 
 icm_status icm_set_schedule(icm_batch *b, const icm_schedule *s);
 icm_status icm_get_schedule(const icm_batch *b, icm_schedule *s);

@@ -118,6 +118,53 @@ uint32_t acceptance_threshold(double a)
     return (uint32_t)v;
 }
 
+// Temperature-dependent tables of a ladder T[0..n_T-1] (ascending):
+//  thr_metro[r][m] = floor(exp((-2m) beta_k) 2^32) for the +-J Metropolis
+//    test at replica position r = 2k + c and m = s_i h_i = 1..6;
+//  b2l[r] = -2 beta_k log2(e) for the Gaussian test;
+//  dbeta_l2e[k] = (beta_k - beta_{k+1}) log2(e) for Gaussian PT decisions;
+//  thr_swap (per pair k, d = 1..len_k) = floor(exp((-2d)(beta_k - beta_{k+1})) 2^32)
+//    for +-J PT decisions, cut where it reaches 0.
+struct TempTables {
+    std::vector<double> beta;
+    std::vector<uint32_t> thr_metro;
+    std::vector<float> b2l, dbeta_l2e;
+    std::vector<uint32_t> thr_swap;
+    std::vector<int32_t> swap_off, swap_len;
+};
+
+void temperature_tables(const double *T, int n_T, int Nb, TempTables &t)
+{
+    const int R = 2 * n_T;
+    t.beta.assign(n_T, 0.0);
+    for (int k = 0; k < n_T; ++k) t.beta[k] = 1.0 / T[k];
+    t.thr_metro.assign((size_t)R * 8, 0u);
+    t.b2l.assign(R, 0.f);
+    for (int r = 0; r < R; ++r) {
+        const double bk = t.beta[r / 2];
+        for (int m = 1; m <= 6; ++m) t.thr_metro[(size_t)r * 8 + m] = acceptance_threshold((double)(-2 * m) * bk);
+        t.b2l[r] = (float)(-2.0 * bk * 1.4426950408889634);
+    }
+    t.dbeta_l2e.assign(n_T > 1 ? n_T - 1 : 0, 0.f);
+    for (int k = 0; k + 1 < n_T; ++k) t.dbeta_l2e[k] = (float)((t.beta[k] - t.beta[k + 1]) * 1.4426950408889634);
+    t.thr_swap.clear();
+    t.swap_off.assign(n_T > 1 ? n_T - 1 : 0, 0);
+    t.swap_len.assign(n_T > 1 ? n_T - 1 : 0, 0);
+    for (int k = 0; k + 1 < n_T; ++k) {
+        const double db = t.beta[k] - t.beta[k + 1];
+        t.swap_off[k] = (int32_t)t.thr_swap.size();
+        int len = 0;
+        for (int d = 1; d <= Nb; ++d) {
+            const uint32_t v = acceptance_threshold((double)(-2 * d) * db);
+            if (v == 0u) break;
+            t.thr_swap.push_back(v);
+            ++len;
+        }
+        t.swap_len[k] = len;
+    }
+    if (t.thr_swap.empty()) t.thr_swap.push_back(0u);
+}
+
 struct DevBuf {
     void *p = nullptr;
 };
@@ -135,6 +182,7 @@ struct icm_batch {
     icm_schedule sched{};
     icm::KParams kp{};
     int threads = 0, grid = 0, ctas_per_sm = 0, n_icm = 0;
+    size_t thr_swap_cap = 0;      // entries allocated for the +-J swap thresholds
     int64_t launches = 0;
     std::vector<void *> allocs;
     // staging buffers for loads and reads
@@ -360,7 +408,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     if (lattice == ICM_CHIMERA && L < 1) return fail(ctx, ICM_ERR_ARG, "chimera needs M >= 1");
     if (n_inst < 1) return fail(ctx, ICM_ERR_ARG, "n_inst must be >= 1");
     if (!couplings) return fail(ctx, ICM_ERR_ARG, "couplings are required");
-    if (!T || n_T < 2 || n_T > 32) return fail(ctx, ICM_ERR_ARG, "need 2 <= n_T <= 32 temperatures");
+    if (!T || n_T < 1 || n_T > 32) return fail(ctx, ICM_ERR_ARG, "need 1 <= n_T <= 32 temperatures");
     for (int k = 0; k < n_T; ++k) {
         if (!(T[k] > 0.0) || !std::isfinite(T[k])) return fail(ctx, ICM_ERR_ARG, "temperatures must be finite and > 0");
         if (k && !(T[k] > T[k - 1])) return fail(ctx, ICM_ERR_ARG, "temperatures must be strictly ascending");
@@ -464,32 +512,14 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     b->grid = n_inst < slots ? n_inst : slots;
 
     // temperature tables
-    std::vector<double> beta(n_T);
-    for (int k = 0; k < n_T; ++k) beta[k] = 1.0 / T[k];
-    std::vector<uint32_t> thr_metro((size_t)R * 8, 0u);
-    std::vector<float> b2l(R);
-    for (int r = 0; r < R; ++r) {
-        const double bk = beta[r / 2];
-        for (int m = 1; m <= 6; ++m) thr_metro[(size_t)r * 8 + m] = acceptance_threshold((double)(-2 * m) * bk);
-        b2l[r] = (float)(-2.0 * bk * 1.4426950408889634);
-    }
-    std::vector<float> dbeta_l2e(n_T - 1);
-    for (int k = 0; k + 1 < n_T; ++k) dbeta_l2e[k] = (float)((beta[k] - beta[k + 1]) * 1.4426950408889634);
-    std::vector<uint32_t> thr_swap;
-    std::vector<int32_t> swap_off(n_T - 1), swap_len(n_T - 1);
-    for (int k = 0; k + 1 < n_T; ++k) {
-        const double db = beta[k] - beta[k + 1];
-        swap_off[k] = (int32_t)thr_swap.size();
-        int len = 0;
-        for (int d = 1; d <= g.Nb; ++d) {
-            const uint32_t v = acceptance_threshold((double)(-2 * d) * db);
-            if (v == 0u) break;
-            thr_swap.push_back(v);
-            ++len;
-        }
-        swap_len[k] = len;
-    }
-    if (thr_swap.empty()) thr_swap.push_back(0u);
+    TempTables tt;
+    temperature_tables(T, n_T, g.Nb, tt);
+    std::vector<double> &beta = tt.beta;
+    std::vector<uint32_t> &thr_metro = tt.thr_metro;
+    std::vector<float> &b2l = tt.b2l, &dbeta_l2e = tt.dbeta_l2e;
+    std::vector<uint32_t> &thr_swap = tt.thr_swap;
+    std::vector<int32_t> &swap_off = tt.swap_off, &swap_len = tt.swap_len;
+    b->thr_swap_cap = thr_swap.size();
 
     icm::KParams &P = b->kp;
     P.N = N; P.Nb = g.Nb; P.nT = n_T; P.R = R; P.G = G; P.Z = Z; P.n_inst = n_inst; P.n_icm = n_icm;
@@ -1080,6 +1110,44 @@ icm_status icm_group_destroy(icm_group *g)
     cudaStreamSynchronize(g->ctx->stream);
     destroy_group(g);
     return ICM_OK;
+}
+
+icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, double T_icm)
+{
+    if (!b || !T) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    if (n_T != P.nT) return fail(b->ctx, ICM_ERR_ARG, "a batch keeps its number of temperatures");
+    for (int k = 0; k < n_T; ++k) {
+        if (!(T[k] > 0.0) || !std::isfinite(T[k])) return fail(b->ctx, ICM_ERR_ARG, "temperatures must be finite and > 0");
+        if (k && !(T[k] > T[k - 1])) return fail(b->ctx, ICM_ERR_ARG, "temperatures must be strictly ascending");
+    }
+    TempTables tt;
+    temperature_tables(T, n_T, P.Nb, tt);
+    icm_status st;
+    if (tt.thr_swap.size() > b->thr_swap_cap) {
+        uint32_t *d = nullptr;
+        if ((st = dalloc(b, &d, tt.thr_swap.size()))) return st;
+        P.thr_swap = d;
+        b->thr_swap_cap = tt.thr_swap.size();
+    }
+    cudaStream_t s = b->ctx->stream;
+#define UPV(dst, vec) cudaMemcpyAsync((void *)(dst), (vec).data(), (vec).size() * sizeof((vec)[0]), cudaMemcpyHostToDevice, s)
+    ICM_CUDA(b->ctx, UPV(P.thr_metro, tt.thr_metro));
+    ICM_CUDA(b->ctx, UPV(P.b2l, tt.b2l));
+    ICM_CUDA(b->ctx, UPV(P.beta, tt.beta));
+    ICM_CUDA(b->ctx, UPV(P.dbeta_l2e, tt.dbeta_l2e));
+    ICM_CUDA(b->ctx, UPV(P.thr_swap, tt.thr_swap));
+    ICM_CUDA(b->ctx, UPV(P.swap_off, tt.swap_off));
+    ICM_CUDA(b->ctx, UPV(P.swap_len, tt.swap_len));
+#undef UPV
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(s));   // the host tables are read by the copies
+    int n_icm = 0;
+    while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
+    b->T.assign(T, T + n_T);
+    b->T_icm = T_icm;
+    b->n_icm = n_icm;
+    P.n_icm = n_icm;
+    return apply_threads(b, b->threads);          // the shared-memory layout depends on n_icm
 }
 
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *grid,

@@ -76,3 +76,21 @@ def thermalization_time(curve: DeltaCurve, nsig: float = 2.0, floor: float = 0.0
     while i > 0 and ok[i - 1]:
         i -= 1
     return int(curve.t[i])
+
+
+def anneal(ctx, lattice: int, L: int, disorder: int, couplings, spins, T_hi: float, T_lo: float, steps: int,
+           sweeps_per_step: int, icm: bool, seed: int, instance_ids=None):
+    """Simulated annealing of two replicas per instance (one temperature,
+    geometric from T_hi down to T_lo over `steps` values, `sweeps_per_step`
+    simulation steps each).  With icm=True every sweep is followed by the
+    cluster move of the pair (steps 2a and 2b) -- the variant the paper
+    proposes for ground-state searches.  Returns the batch (caller reads it)."""
+    ts = T_hi * (T_lo / T_hi) ** (np.arange(steps) / max(steps - 1, 1))
+    T_icm = float("inf") if icm else 0.0
+    b = icmpt.Batch(ctx, lattice, L, disorder, couplings, ts[:1], min(T_icm, 1e300), seed, spins=spins,
+                    instance_ids=instance_ids)
+    b.set_schedule(icm_every=1 if icm else 0, swap_every=0, t_meas=1 << 62)
+    for T in ts:
+        b.set_temperatures([T], min(T_icm, 1e300))
+        b.run(sweeps_per_step)
+    return b

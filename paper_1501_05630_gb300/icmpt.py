@@ -47,7 +47,7 @@ EXPORTS = [
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
-    "icm_percolation_random",
+    "icm_percolation_random", "icm_set_temperatures",
 ]
 
 
@@ -105,6 +105,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_group_destroy.argtypes = [vp]
         L.icm_percolation.argtypes = [vp, i32, i32, i32, vp, vp, u32]
         L.icm_percolation_random.argtypes = [vp, i32, i32, ctypes.c_double, u64, i32, vp, u32]
+        L.icm_set_temperatures.argtypes = [vp, vp, i32, ctypes.c_double]
         for name in EXPORTS:
             if name != "icm_last_error":
                 getattr(L, name).restype = i32
@@ -268,6 +269,11 @@ class Batch:
         for k, v in kw.items():
             setattr(s, k, int(v))
         self.ctx.check(self._lib.icm_set_schedule(self._h, ctypes.byref(s)))
+
+    def set_temperatures(self, T, T_icm: float):
+        T = np.ascontiguousarray(T, dtype=np.float64)
+        self.ctx.check(self._lib.icm_set_temperatures(self._h, T.ctypes.data, len(T), float(T_icm)))
+        self.T = T
 
     def run(self, n_sweeps: int):
         self.ctx.check(self._lib.icm_run_sweeps(self._h, int(n_sweeps)))

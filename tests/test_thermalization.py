@@ -77,3 +77,28 @@ def test_icm_drives_delta_to_zero_gaussian(env):
     assert c.delta[0] < -3 * c.se[0]                          # far from equilibrium at first
     assert abs(c.delta[-1]) <= 3 * c.se[-1] + 2e-3            # Eq. 1 holds at the end
     assert thermalization_time(c, nsig=3.0) is not None
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("icm", [False, True])
+def test_annealing_equals_oracle(env, icm):
+    """+-J annealing with a changing temperature: spins and energies of the
+    library equal the oracle's run with the same temperatures, bit for bit."""
+    icmpt, ctx = env
+    from paper_1501_05630_gb300.experiments import anneal
+    g = O.Geometry(O.SQUARE2D, 8)
+    n, seed, steps, sw = 6, 55, 12, 5
+    J = I.couplings(g.Nb, I.PM_J, seed, range(n))
+    s0 = I.initial_spins(g.N, 2, seed, range(n))
+    b = anneal(ctx, O.SQUARE2D, 8, I.PM_J, J, s0, 3.0, 0.1, steps, sw, icm, seed)
+    spins, E = b.read_spins(), b.read_energies()
+    ts = 3.0 * (0.1 / 3.0) ** (np.arange(steps) / (steps - 1))
+    for a in range(n):
+        r = O.Instance(g, J[a].astype(np.float64), ts[:1].copy(), s0[a], pm=True, T_icm=1e300 if icm else 0.0,
+                       seed=seed, inst=a, icm_every=1 if icm else 0, swap_every=0, t_meas=1 << 62)
+        for T in ts:
+            r.T[0] = T
+            r.run(sw)
+        assert np.array_equal(spins[a], r.s)
+        assert np.array_equal(E[a], r.E)
+    b.close()
