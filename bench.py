@@ -46,13 +46,13 @@ WORKLOADS = {
                       desc="2D EA L=8 periodic (64 spins), +-J, 1 instance, 16 T geometric [0.2,1.5], ICM T<=1.0"),
 }
 
-# Algorithmic thread-operations per spin update of the fused kernel's sweep
-# (Philox4x32-10 share: 10 rounds x (2 wide multiplies + 2 three-input XORs)
-# / 4 draws = 10; local field: z sign injections + z adds; acceptance:
-# uniform, scale, exp2, compare, flip = 5; energy accumulation 1).
-ALG_OPS = {I.GAUSS: lambda z: 10 + 2 * z + 5 + 1,
-           # +-J bit-sliced: field ~1 per bit; extract 3, index 1, load 1, compare 1, flip 1, energy 1
-           I.PM_J: lambda z: 10 + 1 + 8}
+# Algorithmic integer/fp operations per spin update (the per-unit figure of the
+# method's cost model): Philox4x32-10 = 98 integer ops per call of 4 draws
+# (10 rounds x 4 mul.lo/hi + 4 xor, 9 x 2 key increments) -> 24.5 per update;
+# local field and acceptance 10..15 (midpoint 12.5) -> 37 for +-J; Gaussian
+# couplings add z fp32 multiply-adds and one exponential.
+ALG_OPS = {I.PM_J: lambda z: 24.5 + 12.5,
+           I.GAUSS: lambda z: 24.5 + 12.5 + z + 1}
 
 
 def kernel_source_digest() -> str:
