@@ -301,6 +301,17 @@ icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, 
 icm_status icm_group_run(icm_group *g, uint32_t n_launches);
 icm_status icm_group_destroy(icm_group *g);
 
+/* ---------------------------------------------------------------- checkpoint / resume
+ * The state of a batch -- spins, energies, sweep counters, instance ids,
+ * observables, slot flags, ladder and schedule -- as one versioned blob.
+ * The random numbers are counter-based (Philox keyed by seed, instance,
+ * sweep, site), so no generator state is needed: loading a checkpoint into
+ * a batch of the same shape and seed and running n more sweeps gives the
+ * same result as running on without the checkpoint.
+ * icm_save with buf = NULL stores the required size in *len.             */
+icm_status icm_save(icm_batch *b, void *buf, size_t *len);
+icm_status icm_load(icm_batch *b, const void *buf, size_t len);
+
 /* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
  * dynamic shared memory bytes per CTA and kernel launches issued so far. */
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,

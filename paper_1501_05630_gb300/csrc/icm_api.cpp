@@ -1150,6 +1150,121 @@ icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, doub
     return apply_threads(b, b->threads);          // the shared-memory layout depends on n_icm
 }
 
+// ---------------------------------------------------------------- checkpoint / resume
+
+namespace {
+struct BlobHeader {
+    char magic[8];            // "ICMPTCK1"
+    uint32_t version;         // 1
+    int32_t lattice, L, disorder, n_inst, nT, N, R, G;
+    int32_t has_slots;
+    uint64_t seed;
+    double T_icm;
+    icm_schedule sched;
+};
+
+struct BlobPart {
+    void *dev;
+    size_t bytes;
+};
+
+std::vector<BlobPart> blob_parts(icm_batch *b)
+{
+    icm::KParams &P = b->kp;
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    std::vector<BlobPart> v = {
+        {b->raw_coup, (size_t)b->n_inst * P.Nb * (b->gauss ? 4 : 1)},
+        {P.spins, (size_t)b->n_inst * P.G * P.N * 4},
+        {b->gauss ? (void *)P.Ef : (void *)P.Ei, (size_t)b->n_inst * P.R * 4},
+        {P.tsweep, (size_t)b->n_inst * 4},
+        {const_cast<uint32_t *>(P.inst_id), (size_t)b->n_inst * 4},
+        {P.accE, nk * 8},
+        {P.acc64, 4 * nk * 8},
+        {P.hist, nk * (P.N + 1) * 8},
+        {P.n_meas, (size_t)b->n_inst * 8},
+    };
+    if (b->d_active) {
+        v.push_back({b->d_active, (size_t)b->n_inst});
+        v.push_back({b->d_tmeas, (size_t)b->n_inst * 8});
+    }
+    return v;
+}
+}  // namespace
+
+icm_status icm_save(icm_batch *b, void *buf, size_t *len)
+{
+    if (!b || !len) return ICM_ERR_ARG;
+    const std::vector<BlobPart> parts = blob_parts(b);
+    size_t need = sizeof(BlobHeader) + b->nT * sizeof(double);
+    for (const auto &pt : parts) need += pt.bytes;
+    if (!buf) {
+        *len = need;
+        return ICM_OK;
+    }
+    if (*len < need) return fail(b->ctx, ICM_ERR_ARG, "checkpoint buffer too small");
+    BlobHeader h{};
+    std::memcpy(h.magic, "ICMPTCK1", 8);
+    h.version = 1;
+    h.lattice = b->lattice; h.L = b->L; h.disorder = b->disorder; h.n_inst = b->n_inst; h.nT = b->nT;
+    h.N = b->kp.N; h.R = b->kp.R; h.G = b->kp.G; h.has_slots = b->d_active ? 1 : 0;
+    h.seed = b->seed; h.T_icm = b->T_icm; h.sched = b->sched;
+    unsigned char *o = (unsigned char *)buf;
+    std::memcpy(o, &h, sizeof h);
+    o += sizeof h;
+    std::memcpy(o, b->T.data(), b->nT * sizeof(double));
+    o += b->nT * sizeof(double);
+    for (const auto &pt : parts) {
+        ICM_CUDA(b->ctx, cudaMemcpyAsync(o, pt.dev, pt.bytes, cudaMemcpyDeviceToHost, b->ctx->stream));
+        o += pt.bytes;
+    }
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    *len = need;
+    return ICM_OK;
+}
+
+icm_status icm_load(icm_batch *b, const void *buf, size_t len)
+{
+    if (!b || !buf) return ICM_ERR_ARG;
+    BlobHeader h;
+    if (len < sizeof h) return fail(b->ctx, ICM_ERR_ARG, "checkpoint too short");
+    std::memcpy(&h, buf, sizeof h);
+    if (std::memcmp(h.magic, "ICMPTCK1", 8) || h.version != 1) return fail(b->ctx, ICM_ERR_ARG, "not a checkpoint of this library");
+    if (h.lattice != b->lattice || h.L != b->L || h.disorder != b->disorder || h.n_inst != b->n_inst ||
+        h.nT != b->nT || h.N != b->kp.N || h.R != b->kp.R || h.G != b->kp.G)
+        return fail(b->ctx, ICM_ERR_ARG, "checkpoint of a batch with another shape");
+    if (h.seed != b->seed) return fail(b->ctx, ICM_ERR_ARG, "checkpoint of a batch with another seed");
+    if (h.has_slots) {
+        icm_status st;
+        if ((st = ensure_slot_arrays(b))) return st;
+    }
+    const unsigned char *in = (const unsigned char *)buf + sizeof h;
+    std::vector<double> T(h.nT);
+    std::memcpy(T.data(), in, h.nT * sizeof(double));
+    in += h.nT * sizeof(double);
+    const std::vector<BlobPart> parts = blob_parts(b);
+    size_t need = sizeof h + h.nT * sizeof(double);
+    for (const auto &pt : parts) need += pt.bytes;
+    if (len < need) return fail(b->ctx, ICM_ERR_ARG, "checkpoint truncated");
+    icm_status st;
+    if (T != b->T || h.T_icm != b->T_icm)
+        if ((st = icm_set_temperatures(b, T.data(), h.nT, h.T_icm))) return st;
+    for (const auto &pt : parts) {
+        ICM_CUDA(b->ctx, cudaMemcpyAsync(pt.dev, in, pt.bytes, cudaMemcpyHostToDevice, b->ctx->stream));
+        in += pt.bytes;
+    }
+    icm::KParams &P = b->kp;
+    ICM_CUDA(b->ctx, icm::launch_expand_couplings(b->raw_coup, b->gauss, b->edge_bond, b->n_inst, P.N, P.Z, P.Nb,
+                                                  const_cast<float *>(P.Jd), const_cast<uint8_t *>(P.Jb),
+                                                  b->ctx->stream));
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    if (h.has_slots) {
+        ICM_CUDA(b->ctx, cudaMemcpy(b->h_active.data(), b->d_active, b->n_inst, cudaMemcpyDeviceToHost));
+        ICM_CUDA(b->ctx, cudaMemcpy(b->h_tmeas.data(), b->d_tmeas, b->n_inst * 8, cudaMemcpyDeviceToHost));
+    }
+    b->sched = h.sched;
+    return ICM_OK;
+}
+
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm, int32_t *grid,
                           int32_t *smem_bytes, int64_t *launches)
 {

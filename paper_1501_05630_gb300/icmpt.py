@@ -47,7 +47,7 @@ EXPORTS = [
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
-    "icm_percolation_random", "icm_set_temperatures",
+    "icm_percolation_random", "icm_set_temperatures", "icm_save", "icm_load",
 ]
 
 
@@ -106,6 +106,8 @@ def load_library(path: str = LIB_PATH):
         L.icm_percolation.argtypes = [vp, i32, i32, i32, vp, vp, u32]
         L.icm_percolation_random.argtypes = [vp, i32, i32, ctypes.c_double, u64, i32, vp, u32]
         L.icm_set_temperatures.argtypes = [vp, vp, i32, ctypes.c_double]
+        L.icm_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+        L.icm_load.argtypes = [vp, vp, ctypes.c_size_t]
         for name in EXPORTS:
             if name != "icm_last_error":
                 getattr(L, name).restype = i32
@@ -269,6 +271,19 @@ class Batch:
         for k, v in kw.items():
             setattr(s, k, int(v))
         self.ctx.check(self._lib.icm_set_schedule(self._h, ctypes.byref(s)))
+
+    def checkpoint(self) -> bytes:
+        """Checkpoint of the batch state (a versioned blob)."""
+        n = ctypes.c_size_t()
+        self.ctx.check(self._lib.icm_save(self._h, None, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value)
+        self.ctx.check(self._lib.icm_save(self._h, buf, ctypes.byref(n)))
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes):
+        """Restore a checkpoint taken from a batch of the same shape and seed."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        self.ctx.check(self._lib.icm_load(self._h, buf, len(blob)))
 
     def set_temperatures(self, T, T_icm: float):
         T = np.ascontiguousarray(T, dtype=np.float64)
