@@ -190,6 +190,9 @@ struct icm_batch {
     int8_t *raw_spins = nullptr;  // [n_inst][R][N]
     double *raw_E = nullptr;      // [n_inst][R]
     int32_t *edge_bond = nullptr; // [N][Z]
+    // wide (global-resident) layout: per-CTA scratch, grown on demand (in allocs)
+    uint32_t *scratch = nullptr;      // [scratch_ctas][wide_scratch_words(N)]
+    int scratch_ctas = 0;
     // per-slot control (serving), allocated on first use
     uint8_t *d_active = nullptr;      // [n_inst]
     long long *d_tmeas = nullptr;     // [n_inst]
@@ -394,6 +397,8 @@ icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_
     return ICM_OK;
 }
 
+static icm_status apply_threads(icm_batch *b, int threads);
+
 icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
                             const void *couplings, const int8_t *spins, const uint32_t *instance_ids,
                             const double *T, int32_t n_T, double T_icm, uint64_t seed, uint32_t flags,
@@ -483,33 +488,15 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
             }
         }
     }
-    // launch shape and shared memory
+    // launch shape: the shared-memory layout when the instance fits one CTA,
+    // else the global-resident layout with wider CTAs (set by apply_threads)
     int n_icm = 0;
     while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
-    const int threads = icm::fused_threads(N);
-    const int nwarps = threads / 32;
-    const icm::SmemLayout sm = icm::smem_layout(N, Z, R, G, n_T, n_icm, nwarps, b->gauss);
-    if (sm.total > ctx->max_smem_optin) {
-        destroy_batch(b);
-        return fail(ctx, ICM_ERR_UNSUPPORTED, "instance needs " + std::to_string(sm.total) +
-                                                  " bytes of shared memory, more than one CTA can hold");
-    }
-    const int half = N / 2;
-    if (((half + threads - 1) / threads) * Z >= 256 || (N + threads - 1) / threads >= 256) {
-        destroy_batch(b);
-        return fail(ctx, ICM_ERR_UNSUPPORTED, "too many sites per thread for the observable counters");
-    }
-    int ctas = 0;
-    cudaError_t ce = icm::fused_occupancy(b->gauss, Z, threads, sm.total, &ctas);
-    if (ce != cudaSuccess || ctas < 1) {
-        destroy_batch(b);
-        return ce != cudaSuccess ? cuda_fail(ctx, ce, "occupancy") : fail(ctx, ICM_ERR_UNSUPPORTED, "kernel does not fit");
-    }
-    b->threads = threads;
-    b->ctas_per_sm = ctas;
+    int threads = icm::fused_threads(N);
+    if (icm::smem_layout(N, Z, R, G, n_T, n_icm, threads / 32, b->gauss, false).total > ctx->max_smem_optin)
+        threads = icm::fused_threads_wide(N);
     b->n_icm = n_icm;
-    const int slots = ctx->num_sms * ctas;
-    b->grid = n_inst < slots ? n_inst : slots;
+    const int half = N / 2;
 
     // temperature tables
     TempTables tt;
@@ -524,10 +511,15 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     icm::KParams &P = b->kp;
     P.N = N; P.Nb = g.Nb; P.nT = n_T; P.R = R; P.G = G; P.Z = Z; P.n_inst = n_inst; P.n_icm = n_icm;
     P.half = half; P.NW = (N + 31) / 32; P.const_z = uniform ? Z : 0;
-    P.small_counts = (((half + threads - 1) / threads) * Z < 16 && (N + threads - 1) / threads < 16) ? 1 : 0;
     P.seed_lo = (uint32_t)(seed & 0xffffffffu);
     P.seed_hi = (uint32_t)(seed >> 32);
-    P.sm = sm;
+    {
+        icm_status st0 = apply_threads(b, threads);
+        if (st0) {
+            destroy_batch(b);
+            return st0;
+        }
+    }
 
     icm_status st = ICM_OK;
     uint16_t *d_nbr, *d_pos2site;
@@ -912,26 +904,47 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
 
 // ---------------------------------------------------------------- launch shape, groups, autotuning
 
+// Widths up to 128 threads use the shared-memory layout; wider CTAs (up to
+// 1024 threads) use the global-resident layout, which is also the only one
+// for instances that do not fit one CTA's shared memory.
 static icm_status apply_threads(icm_batch *b, int threads)
 {
     icm::KParams &P = b->kp;
-    if (threads < 32 || threads > icm::kMaxThreads || threads % 32)
-        return fail(b->ctx, ICM_ERR_ARG, "threads per CTA must be 32, 64, 96 or 128");
+    if (threads < 32 || threads > icm::kMaxThreadsWide || threads % 32)
+        return fail(b->ctx, ICM_ERR_ARG, "threads per CTA must be a multiple of 32 in 32..1024");
     const int half = P.N / 2;
     if (((half + threads - 1) / threads) * P.Z >= 256 || (P.N + threads - 1) / threads >= 256)
         return fail(b->ctx, ICM_ERR_UNSUPPORTED, "too many sites per thread for the observable counters");
-    const icm::SmemLayout sm = icm::smem_layout(P.N, P.Z, P.R, P.G, P.nT, b->n_icm, threads / 32, b->gauss);
-    if (sm.total > b->ctx->max_smem_optin) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "shared memory");
+    const bool wide = threads > icm::kMaxThreads;
+    const icm::SmemLayout sm = icm::smem_layout(P.N, P.Z, P.R, P.G, P.nT, b->n_icm, threads / 32, b->gauss, wide);
+    if (sm.total > b->ctx->max_smem_optin)
+        return fail(b->ctx, ICM_ERR_UNSUPPORTED, "instance needs " + std::to_string(sm.total) +
+                                                     " bytes of shared memory at this width; widths above 128 "
+                                                     "threads keep it in global memory");
     int ctas = 0;
-    cudaError_t e = icm::fused_occupancy(b->gauss, P.Z, threads, sm.total, &ctas);
+    cudaError_t e = icm::fused_occupancy(b->gauss, P.Z, wide, threads, sm.total, &ctas);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "occupancy");
     if (ctas < 1) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "kernel does not fit");
+    const int slots = b->ctx->num_sms * ctas;
+    const int grid = b->n_inst < slots ? b->n_inst : slots;
+    const int words = icm::wide_scratch_words(P.N);
+    if (wide && b->scratch_ctas < grid) {
+        // a larger scratch; the old one stays allocated until the batch is
+        // destroyed, since a captured group graph may still launch with it
+        uint32_t *q = nullptr;
+        icm_status ast = dalloc(b, &q, (size_t)grid * words);
+        if (ast) return ast;
+        b->scratch = q;
+        b->scratch_ctas = grid;
+    }
     P.sm = sm;
+    P.wide = wide ? 1 : 0;
+    P.scratch = wide ? b->scratch : nullptr;
+    P.scratch_words = wide ? words : 0;
     P.small_counts = (((half + threads - 1) / threads) * P.Z < 16 && (P.N + threads - 1) / threads < 16) ? 1 : 0;
     b->threads = threads;
     b->ctas_per_sm = ctas;
-    const int slots = b->ctx->num_sms * ctas;
-    b->grid = b->n_inst < slots ? b->n_inst : slots;
+    b->grid = grid;
     return ICM_OK;
 }
 
@@ -976,7 +989,17 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!st && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         st = fail(ctx, ICM_ERR_CUDA, "events");
-    for (int th = 32; !st && th <= icm::kMaxThreads; th += 32) {
+    // the shared-memory widths when the instance fits them; wide CTAs when it
+    // does not, or when a colour has more sites than 128 threads
+    const bool fits = icm::smem_layout(P.N, P.Z, P.R, P.G, P.nT, b->n_icm, icm::kMaxThreads / 32, b->gauss,
+                                       false).total <= ctx->max_smem_optin;
+    std::vector<int> cand;
+    if (fits)
+        for (int th : {32, 64, 96, 128}) cand.push_back(th);
+    if (!fits || P.N / 2 > icm::kMaxThreads)
+        for (int th : {256, 512, 1024}) cand.push_back(th);
+    for (size_t ci = 0; !st && ci < cand.size(); ++ci) {
+        const int th = cand[ci];
         if (apply_threads(b, th) != ICM_OK) continue;
         if ((st = icm_run_sweeps(b, sweeps))) break;               // warm-up
         cudaEventRecord(e0, ctx->stream);

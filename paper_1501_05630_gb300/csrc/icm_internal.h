@@ -9,10 +9,13 @@ namespace icm {
 
 constexpr int kMaxZ = 6;          // largest degree of the supported graphs
 constexpr int kMaxR = 64;         // replicas per instance (2 N_T, N_T <= 32)
-constexpr int kMaxThreads = 128;  // threads per CTA of the fused kernel
+constexpr int kMaxThreads = 128;  // threads per CTA of the fused kernel, shared-memory layout
+constexpr int kMaxThreadsWide = 1024;  // threads per CTA of the fused kernel, global-resident layout
 constexpr int kPlanes = 8;        // bit-planes of the vertical counters (counts < 256 per thread)
 
-// Byte offsets into the fused kernel's dynamic shared memory.
+// Byte offsets into the fused kernel's dynamic shared memory.  In the
+// global-resident ("wide") layout the spins, couplings, neighbour table,
+// overlap masks and cluster words stay in global memory (size 0 here).
 struct SmemLayout {
     int spins;      // uint32 [G][N]
     int nbr;        // uint16 [N][Z]   neighbour positions, padding = self
@@ -42,6 +45,9 @@ struct SmemLayout {
 struct KParams {
     int N, Nb, nT, R, G, Z, n_inst, n_icm, half, NW;
     int const_z;                  // degree when uniform (lattices), 0 = per-site table
+    int wide;                     // 1: global-resident layout (instances too large for shared memory)
+    int scratch_words;            // wide layout: uint32 words of scratch per CTA (cluster words, masks)
+    uint32_t *scratch;            // wide layout: [grid][scratch_words]
     int small_counts;             // per-thread observable counts fit 4 bit-planes
     // geometry, shared by all instances of the batch
     const uint16_t *nbr;          // [N][Z]
@@ -90,11 +96,15 @@ struct HostTables {
 };
 bool host_tables(int lattice, int L, HostTables &t);
 
-SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss);
+SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss, bool wide);
 int fused_threads(int N);
+int fused_threads_wide(int N);
+// uint32 words of per-CTA scratch of the wide layout (2 N cluster words, 32
+// overlap-mask rows of NW words), rounded to 16 bytes.
+int wide_scratch_words(int N);
 
 // Host-callable launchers (pt_icm.cu).  Return a cudaError_t.
-cudaError_t fused_occupancy(bool gauss, int Z, int threads, int smem, int *ctas_per_sm);
+cudaError_t fused_occupancy(bool gauss, int Z, bool wide, int threads, int smem, int *ctas_per_sm);
 cudaError_t launch_fused(const KParams &P, bool gauss, int threads, int grid, uint32_t n_sweeps,
                          cudaStream_t st);
 cudaError_t launch_pack_spins(const int8_t *src, uint32_t *dst, const uint16_t *pos2site, int n_inst,

@@ -4,7 +4,10 @@
 //
 // Design (one CTA per disorder instance, whole instance resident in shared
 // memory for all sweeps of a launch; nothing here is a dense contraction, so
-// no tensor cores are used):
+// no tensor cores are used).  Instances too large for one CTA's shared memory
+// run the same code in a global-resident layout with wider CTAs (up to 1024
+// threads): their spins and couplings are updated in place in global memory
+// (L1/L2-resident), the small per-instance tables stay in shared memory.
 //
 //  * Spins are multispin-coded across replicas: the word of site position p
 //    holds one bit per replica position r = 2k + c (bit set = spin -1), two
@@ -18,9 +21,11 @@
 //    summed in fp32 from sign-injected couplings, accept via ex2.
 //    The energies of all replicas fall out of the colour-1 half-sweep
 //    (every bond touches exactly one colour-1 site).
-//  * Steps 2a/2b: one warp per ICM temperature: overlap mask by warp ballot,
-//    optional spin reversal of copy 1, seed by rank, breadth-first cluster
-//    growth with shared-memory atomics, flip by atomic XOR, boundary energy.
+//  * Steps 2a/2b: overlap masks of all ICM pairs by warp ballots; one thread
+//    per pair counts, decides the copy-1 reversal and picks the seed by rank;
+//    the clusters of all pairs grow at once, bit-parallel (bit 2k of a site's
+//    cluster word = member of pair k's cluster), until a round adds nothing;
+//    both copies flip by XOR, E_a is recomputed and E_b = (E_a+E_b) - E_a.
 //  * Step 3: one thread runs each copy's sequential PT pass on the energies;
 //    accepted swaps are then applied to every site word as bit transpositions.
 //  * Observables: vertical (bit-sliced) counters of q_i = -1 sites and of
@@ -244,7 +249,7 @@ __device__ __forceinline__ void load_nbrs(const uint16_t *nbr, int p, int (&q)[Z
 // are updated at beta = 0 and never read, so the inner loop has no guards.
 // Two Philox4x32-10 blocks are generated together (8 draws) so that their
 // dependency chains interleave.
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool WIDE>
 __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g, int COLOR,
                                            int H)
 {
@@ -354,14 +359,14 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 // Step 1 for all replicas: colour 0 then colour 1, each as 16-bit passes over
 // the site words.  One call site, so the pass body exists once in the kernel
 // (the instruction cache is shared by all CTAs of the SM).
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool WIDE>
 __device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
 {
     const int npass = (P.R + 15) >> 4;          // 16-bit passes per colour
     for (int it = 0; it < 2 * npass; ++it) {
         const int color = it >= npass;
         const int pass = it - color * npass;
-        sweep_pass<GAUSS, Z>(P, S, t, inst, pass >> 1, color, pass & 1);
+        sweep_pass<GAUSS, Z, WIDE>(P, S, t, inst, pass >> 1, color, pass & 1);
         if (pass == npass - 1) __syncthreads();
     }
 }
@@ -371,7 +376,7 @@ __device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, 
 // from the spins: +-J via bit-sliced unsatisfied-bond counts (E = 2U - N_b),
 // Gaussian via per-bit fp32 local fields; summed in a fixed order.  Every
 // thread ends with partial sums in S.Epart[warp][k]; the caller adds warps.
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool WIDE>
 __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uint32_t act0, uint32_t act1)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
@@ -446,7 +451,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
 //      of {q = -1};
 //  (d) flip in both copies (bits 2k, 2k+1 of C_p | C_p << 1), then E_a from
 //      the spins and E_b = (E_a + E_b)_before - E_a (the move is isoenergetic).
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool WIDE>
 __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
@@ -655,7 +660,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         }
     }
     __syncthreads();
-    pair_energies<GAUSS, Z>(P, S, act0, act1);
+    pair_energies<GAUSS, Z, WIDE>(P, S, act0, act1);
     __syncthreads();
     for (int k = tid; k < nicm; k += nth) {
         if (S.icm_seed[k] < 0) continue;
@@ -678,7 +683,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
 
 // ---------------------------------------------------------------------------
 // Step 3: sequential PT pass per copy, then the configuration swaps.
-template <bool GAUSS>
+template <bool GAUSS, bool WIDE>
 __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
@@ -764,7 +769,7 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
 
 // ---------------------------------------------------------------------------
 // Observables: per pair k, n = #{q_i = -1} and d = #{bonds, q_i q_j = -1}.
-template <bool GAUSS, int Z, int NPL>
+template <bool GAUSS, int Z, int NPL, bool WIDE>
 __device__ void measure(const KParams &P, const Sm &S, int slot)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
@@ -820,19 +825,31 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
 }
 
 // ---------------------------------------------------------------------------
-template <bool GAUSS, int Z>
-__global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, uint32_t n_sweeps)
+// The fused step loop.  WIDE = false: the whole instance lives in shared
+// memory for the launch.  WIDE = true (instances too large for one CTA's
+// shared memory): spins and couplings are updated in place in global memory,
+// the neighbour table is read from global memory, and the cluster words and
+// overlap masks use a per-CTA global scratch; the arithmetic is the same.
+template <bool GAUSS, int Z, bool WIDE>
+__device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     extern __shared__ __align__(16) unsigned char smem[];
-    const Sm S = make_sm(smem, P.sm);
+    Sm S = make_sm(smem, P.sm);
     PHASE_INIT();
     const int tid = threadIdx.x, nth = blockDim.x, nwarps = nth >> 5;
     const int N = P.N, R = P.R, nT = P.nT, G = P.G;
 
-    for (int i = tid; i < N * Z; i += nth) S.nbr[i] = P.nbr[i];
-    if (!GAUSS && !P.const_z)
-        for (int i = tid; i < N; i += nth) S.zdeg[i] = P.zdeg[i];
+    if constexpr (WIDE) {
+        S.nbr = const_cast<uint16_t *>(P.nbr);
+        S.zdeg = const_cast<uint8_t *>(P.zdeg);
+        S.C = P.scratch + (size_t)blockIdx.x * P.scratch_words;
+        S.mask = S.C + 2 * N;
+    } else {
+        for (int i = tid; i < N * Z; i += nth) S.nbr[i] = P.nbr[i];
+        if (!GAUSS && !P.const_z)
+            for (int i = tid; i < N; i += nth) S.zdeg[i] = P.zdeg[i];
+    }
     if constexpr (GAUSS) {
         for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
     } else {
@@ -845,15 +862,24 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
 
     for (int slot = blockIdx.x; slot < P.n_inst; slot += gridDim.x) {
         if (P.active && !P.active[slot]) continue;   // free slot of a serving batch
-        const uint32_t *gs = P.spins + (size_t)slot * G * N;
-        for (int i = tid; i < G * N; i += nth) S.s[i] = gs[i];
+        if constexpr (WIDE) {
+            S.s = P.spins + (size_t)slot * G * N;
+            S.Jd = const_cast<float *>(P.Jd) + (size_t)slot * N * Z;
+            S.Jb = const_cast<uint8_t *>(P.Jb) + (size_t)slot * N;
+        } else {
+            const uint32_t *gs = P.spins + (size_t)slot * G * N;
+            for (int i = tid; i < G * N; i += nth) S.s[i] = gs[i];
+            if constexpr (GAUSS) {
+                const float4 *src = (const float4 *)(P.Jd + (size_t)slot * N * Z);
+                float4 *dst = (float4 *)S.Jd;
+                for (int i = tid; i < (N * Z) / 4; i += nth) dst[i] = src[i];
+            } else {
+                for (int i = tid; i < N; i += nth) S.Jb[i] = P.Jb[(size_t)slot * N + i];
+            }
+        }
         if constexpr (GAUSS) {
-            const float4 *src = (const float4 *)(P.Jd + (size_t)slot * N * Z);
-            float4 *dst = (float4 *)S.Jd;
-            for (int i = tid; i < (N * Z) / 4; i += nth) dst[i] = src[i];
             for (int r = tid; r < R; r += nth) ((float *)S.E)[r] = P.Ef[(size_t)slot * R + r];
         } else {
-            for (int i = tid; i < N; i += nth) S.Jb[i] = P.Jb[(size_t)slot * N + i];
             for (int r = tid; r < R; r += nth) ((int *)S.E)[r] = P.Ei[(size_t)slot * R + r];
         }
         for (int k = tid; k < nT; k += nth) {
@@ -883,7 +909,7 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
                 __syncthreads();
             }
             if (P.enable_metropolis) {  // step 1
-                metropolis_sweep<GAUSS, Z>(P, S, t, inst);
+                metropolis_sweep<GAUSS, Z, WIDE>(P, S, t, inst);
                 for (int r = tid; r < R; r += nth) {
                     ET e = ET(0);
                     for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + r];
@@ -893,21 +919,23 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
             }
             PHASE_MARK(0);
             if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)  // steps 2a, 2b
-                cluster_moves<GAUSS, Z>(P, S, t, inst, slot, trace);
+                cluster_moves<GAUSS, Z, WIDE>(P, S, t, inst, slot, trace);
             PHASE_MARK(1);
             if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1)  // step 3
-                pt_pass<GAUSS>(P, S, t, inst, slot, trace);
+                pt_pass<GAUSS, WIDE>(P, S, t, inst, slot, trace);
             PHASE_MARK(2);
             if ((long long)t >= t_meas) {
-                if (P.small_counts) measure<GAUSS, Z, 4>(P, S, slot);   // every per-thread count < 16
-                else measure<GAUSS, Z, kPlanes>(P, S, slot);
+                if (P.small_counts) measure<GAUSS, Z, 4, WIDE>(P, S, slot);   // every per-thread count < 16
+                else measure<GAUSS, Z, kPlanes, WIDE>(P, S, slot);
             }
             PHASE_MARK(3);
         }
 
         PHASE_MARK(4);
-        uint32_t *gd = P.spins + (size_t)slot * G * N;
-        for (int i = tid; i < G * N; i += nth) gd[i] = S.s[i];
+        if constexpr (!WIDE) {
+            uint32_t *gd = P.spins + (size_t)slot * G * N;
+            for (int i = tid; i < G * N; i += nth) gd[i] = S.s[i];
+        }
         for (int r = tid; r < R; r += nth) {
             if constexpr (GAUSS) P.Ef[(size_t)slot * R + r] = ((float *)S.E)[r];
             else P.Ei[(size_t)slot * R + r] = ((int *)S.E)[r];
@@ -924,6 +952,18 @@ __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, 
         PHASE_MARK(5);
     }
     PHASE_FLUSH();
+}
+
+template <bool GAUSS, int Z>
+__global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, uint32_t n_sweeps)
+{
+    fused_body<GAUSS, Z, false>(P, n_sweeps);
+}
+
+template <bool GAUSS, int Z>
+__global__ void __launch_bounds__(kMaxThreadsWide, 1) fused_wide_kernel(const KParams P, uint32_t n_sweeps)
+{
+    fused_body<GAUSS, Z, true>(P, n_sweeps);
 }
 
 // ---------------------------------------------------------------------------
@@ -1045,19 +1085,22 @@ inline int grid_for(size_t n, int threads)
 template <bool GAUSS, int Z>
 cudaError_t launch_fused_t(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<GAUSS, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         P.sm.total);
+    if (P.wide && (threads > kMaxThreadsWide || !P.scratch)) return cudaErrorInvalidValue;
+    if (!P.wide && threads > kMaxThreads) return cudaErrorInvalidValue;
+    auto kern = P.wide ? fused_wide_kernel<GAUSS, Z> : fused_kernel<GAUSS, Z>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.sm.total);
     if (e != cudaSuccess) return e;
-    fused_kernel<GAUSS, Z><<<grid, threads, P.sm.total, st>>>(P, n_sweeps);
+    kern<<<grid, threads, P.sm.total, st>>>(P, n_sweeps);
     return cudaGetLastError();
 }
 
 template <bool GAUSS, int Z>
-cudaError_t occupancy_t(int threads, int smem, int *ctas)
+cudaError_t occupancy_t(bool wide, int threads, int smem, int *ctas)
 {
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<GAUSS, Z>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    auto kern = wide ? fused_wide_kernel<GAUSS, Z> : fused_kernel<GAUSS, Z>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, fused_kernel<GAUSS, Z>, threads, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, kern, threads, smem);
 }
 
 }  // namespace
@@ -1065,8 +1108,9 @@ cudaError_t occupancy_t(int threads, int smem, int *ctas)
 // ---------------------------------------------------------------------------
 static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
-SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss)
+SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss, bool wide)
 {
+    const int in_smem = wide ? 0 : 1;   // the large arrays stay in global memory in the wide layout
     SmemLayout L{};
     const int NW = (N + 31) / 32;
     int o = 0;
@@ -1076,15 +1120,15 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
         o += bytes;
         return at;
     };
-    L.coup = take(gauss ? N * Z * 4 : N, 16);
-    L.spins = take(G * N * 4, 16);
-    L.nbr = take(N * Z * 2, 16);
-    L.zdeg = take(N, 16);
+    L.coup = take(in_smem * (gauss ? N * Z * 4 : N), 16);
+    L.spins = take(in_smem * G * N * 4, 16);
+    L.nbr = take(in_smem * N * Z * 2, 16);
+    L.zdeg = take(in_smem * N, 16);
     L.E = take(R * 4, 16);
     L.Epart = take(nwarps * (R > 32 ? R : 32) * 4, 16);
     L.rtab = take(gauss ? G * 32 * 4 : G * 32 * 8 * 4, 16);   // every bit of the G words
-    L.icm_mask = take(n_icm * NW * 4, 16);
-    L.icm_C = take(2 * N * 4, 16);
+    L.icm_mask = take(in_smem * n_icm * NW * 4, 16);
+    L.icm_C = take(in_smem * 2 * N * 4, 16);
     L.swap_x = take(2 * 32 * 4, 16);
     L.swap_list = take(2 * 32 * 4, 16);
     L.swap_n = take(2 * 4, 16);
@@ -1110,10 +1154,26 @@ int fused_threads(int N)
     return t;
 }
 
-cudaError_t fused_occupancy(bool gauss, int Z, int threads, int smem, int *ctas)
+int fused_threads_wide(int N)
 {
-    if (gauss) return Z == 4 ? occupancy_t<true, 4>(threads, smem, ctas) : occupancy_t<true, 6>(threads, smem, ctas);
-    return Z == 4 ? occupancy_t<false, 4>(threads, smem, ctas) : occupancy_t<false, 6>(threads, smem, ctas);
+    const int half = N / 2;
+    int t = (half + 31) / 32 * 32;
+    if (t > kMaxThreadsWide) t = kMaxThreadsWide;
+    if (t < 32) t = 32;
+    return t;
+}
+
+int wide_scratch_words(int N)
+{
+    const int NW = (N + 31) / 32;
+    return (2 * N + 32 * NW + 3) / 4 * 4;
+}
+
+cudaError_t fused_occupancy(bool gauss, int Z, bool wide, int threads, int smem, int *ctas)
+{
+    if (gauss)
+        return Z == 4 ? occupancy_t<true, 4>(wide, threads, smem, ctas) : occupancy_t<true, 6>(wide, threads, smem, ctas);
+    return Z == 4 ? occupancy_t<false, 4>(wide, threads, smem, ctas) : occupancy_t<false, 6>(wide, threads, smem, ctas);
 }
 
 cudaError_t launch_fused(const KParams &P, bool gauss, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)

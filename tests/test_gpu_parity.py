@@ -46,11 +46,15 @@ def _oracle(g, J, s0, T, T_icm, seed, inst, dis, **kw):
 TRACE_KEYS = ("n_pre", "flip2a", "seed_site", "csize", "esum_before", "esum_after")
 
 
-def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, check_every=1, **sched):
+def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, check_every=1, threads=None,
+                    **sched):
     icmpt, ctx = icm
     T = I.ladder(T_lo, T_hi, nT)
     g, J, s0, ids = _setup(kind, L, I.PM_J, n_inst, T, seed)
     b = icmpt.Batch(ctx, kind, L, I.PM_J, J, T, T_icm, seed, spins=s0)
+    if threads is not None:
+        b.set_threads(threads)
+        assert b.info()["threads"] == threads
     b.set_schedule(trace=1, **sched)
     refs = [_oracle(g, J[a], s0[a], T, T_icm, seed, ids[a], I.PM_J, **sched) for a in range(n_inst)]
     done = 0
@@ -284,9 +288,120 @@ def test_gauss_eq1_identity(icm):
 
 
 # ----------------------------------------------------------------------------- limits and errors
-def test_largest_supported_instance(icm):
-    """3D L=12 (1728 sites), 48 replicas: one CTA holds the whole instance."""
+def test_largest_shared_memory_instance(icm):
+    """3D L=12 (1728 sites), 48 replicas: one CTA's shared memory holds the whole instance."""
     _compare_sweeps(icm, O.CUBIC3D, 12, 24, 0.2, 2.0, 1.0, 2, 6, 12, check_every=3)
+
+
+# ----------------------------------------------------------------------------- global-resident (wide) layout
+@pytest.mark.parametrize("kind,L,nT,T_hi,T_icm,n_inst,threads", [
+    (O.CUBIC3D, 4, 24, 2.0, 1.0, 3, 256),      # two spin words, more threads than sites per colour
+    (O.CUBIC3D, 6, 10, 2.0, 1.0, 2, 160),      # ragged against the CTA width
+    (O.CHIMERA, 3, 30, 3.0, 1.5, 2, 512),      # per-site degrees, padded neighbour lists
+    (O.SQUARE2D, 2, 4, 1.5, 1.0, 2, 1024),     # doubled bonds; widest CTA on the smallest torus
+    (O.CHIMERA, 1, 32, 3.0, 1.5, 1, 192),      # 64 replicas
+])
+def test_wide_layout_pmj_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, n_inst, threads):
+    """Widths above 128 threads keep the instance in global memory: the same
+    chain as the oracle, bit for bit, sweep by sweep."""
+    _compare_sweeps(icm, kind, L, nT, 0.2, T_hi, T_icm, n_inst, 30, 0xBEEF + L, threads=threads)
+
+
+def test_wide_layout_2d_L128_64_replicas(icm):
+    """2D L=128 (16384 sites) +-J with 32 temperatures (64 replicas), the
+    largest serving size: too large for shared memory, so the default layout
+    is the global-resident one; bit-exact with the oracle."""
+    icmpt, ctx = icm
+    _compare_sweeps(icm, O.SQUARE2D, 128, 32, 0.2, 1.5, 1.0, 1, 6, 0x1501, check_every=3)
+
+
+def test_wide_layout_default_for_large_instances(icm):
+    """The shared-memory layout while the instance fits one CTA, else the wide one."""
+    icmpt, ctx = icm
+    for kind, L, dis, nT, wide in ((O.SQUARE2D, 128, I.PM_J, 32, True), (O.SQUARE2D, 128, I.PM_J, 8, True),
+                                   (O.SQUARE2D, 64, I.PM_J, 32, False), (O.CUBIC3D, 12, I.GAUSS, 24, False),
+                                   (O.CUBIC3D, 22, I.PM_J, 16, True)):
+        T = I.ladder(0.2, 2.0, nT)
+        g = O.Geometry(kind, L)
+        b = icmpt.Batch(ctx, kind, L, dis, I.couplings(g.Nb, dis, 1, [0]), T, 1.0, 1,
+                        spins=I.initial_spins(g.N, 2 * nT, 1, [0]))
+        info = b.info()
+        assert (info["threads"] > 128) == wide, (kind, L, info)
+        b.close()
+
+
+@pytest.mark.parametrize("threads", [None, 1024])
+def test_gauss_3d_L16_conservation_and_consistency(icm, threads):
+    """3D L=16 Gaussian (4096 sites, 64 replicas), default and wide layout:
+    every cluster move keeps E_a + E_b to 1e-5 sum|J|; device energies equal
+    energies from the spins."""
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 32)
+    seed = 0x1501056300000016
+    n = 6
+    g, J, s0, ids = _setup(O.CUBIC3D, 16, I.GAUSS, n, T, seed)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 16, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    if threads:
+        b.set_threads(threads)
+    b.set_schedule(trace=1)
+    scale = np.abs(J).astype(np.float64).sum(1)
+    moves = 0
+    for rep in range(4):
+        b.run(5)
+        tr = b.read_trace()
+        icm_k = tr["n_pre"] >= 0
+        moves += int((tr["csize"] > 0).sum())
+        err = np.abs(tr["esum_after"] - tr["esum_before"])[icm_k]
+        assert np.all(err <= 1e-5 * np.repeat(scale[:, None], 32, 1)[icm_k])
+        spins, E = b.read_spins(), b.read_energies()
+        for a in range(n):
+            e_ref = -np.einsum("b,rb->r", J[a].astype(np.float64),
+                               (spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64))
+            assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a])
+    assert moves > 50
+
+
+def test_wide_layout_gauss_statistical_agreement_with_oracle(icm):
+    """3D L=4 Gaussian forced into the wide layout: per-temperature energy,
+    link overlap and <q^2> agree with the oracle's on the same instances."""
+    icmpt, ctx = icm
+    T = I.ladder(0.3, 2.0, 8)
+    seed = 4343
+    n = 64
+    g, J, s0, ids = _setup(O.CUBIC3D, 4, I.GAUSS, n, T, seed)
+    sweeps, t_meas = 3000, 1000
+    b = icmpt.Batch(ctx, O.CUBIC3D, 4, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_threads(256)
+    b.set_schedule(t_meas=t_meas)
+    b.run(sweeps)
+    o = b.read_observables()
+    m = o.n_meas[:, None].astype(np.float64)
+    gpu = dict(e=o.accE / (2 * g.N * m), q_l=1 - 2 * o.acc_d / (g.Nb * m), q2=o.acc_q2 / (g.N ** 2 * m))
+    cpu = {k: [] for k in gpu}
+    for a in range(n):
+        r = _oracle(g, J[a], s0[a], T, 1.0, seed, a, I.GAUSS, t_meas=t_meas)
+        r.run(sweeps)
+        ob = r.observables()
+        for k in cpu:
+            cpu[k].append(ob[k])
+    for k in gpu:
+        mu, se = _stats(gpu[k] - np.asarray(cpu[k]))
+        assert np.all(np.abs(mu) <= 3.5 * se + 1e-9), (k, mu, se)
+
+
+def test_wide_layout_autotune_keeps_state(icm):
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 1.5, 16)
+    g = O.Geometry(O.SQUARE2D, 128)
+    b = icmpt.Batch(ctx, O.SQUARE2D, 128, I.PM_J, I.couplings(g.Nb, I.PM_J, 2, range(3)), T, 1.0, 2,
+                    spins=I.initial_spins(g.N, 32, 2, range(3)))
+    b.run(2)
+    before = (b.read_spins(), b.read_energies(), b.read_sweeps())
+    th, ms = b.autotune(sweeps=2)
+    assert th in (256, 512, 1024) and ms > 0
+    for x, y in zip(before, (b.read_spins(), b.read_energies(), b.read_sweeps())):
+        assert np.array_equal(x, y)
+    b.close()
 
 
 def test_invalid_arguments(icm):

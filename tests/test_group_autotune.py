@@ -58,7 +58,7 @@ def test_autotune_keeps_state(env):
     b.run(5)
     before = _state(b)
     th, ms = b.autotune(sweeps=4)
-    assert th in (32, 64, 96, 128) and ms > 0
+    assert th in (32, 64, 96, 128, 256, 512, 1024) and ms > 0   # wide CTAs too: 256 sites per colour
     assert b.info()["threads"] == th
     for x, y in zip(before, _state(b)):
         assert np.array_equal(x, y)
