@@ -60,6 +60,7 @@ typedef int32_t icm_status;
 #define ICM_ERR_TIMEOUT (-5)  /* a bounded device wait expired */
 #define ICM_ERR_STATE (-6)    /* call not valid in the current state */
 #define ICM_ERR_UNSUPPORTED (-7) /* size or feature beyond this build's limits */
+#define ICM_PENDING 1          /* icm_query: work still running (not an error) */
 
 /* Lattice kinds ("Results in two and three space dimensions, as well as on
  * the nonplanar chimera topology").
@@ -114,6 +115,9 @@ icm_status icm_ctx_destroy(icm_ctx *ctx);
 const char *icm_last_error(const icm_ctx *ctx);
 /* Wait for all work enqueued on the context's stream. */
 icm_status icm_sync(icm_ctx *ctx);
+/* Non-blocking: ICM_OK when all work enqueued on the context's stream has
+ * finished, ICM_PENDING while some is still running, or an error. */
+icm_status icm_query(icm_ctx *ctx);
 
 /* Number of sites N and bonds N_b of a lattice (host only, no device work). */
 icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_t *n_bonds);

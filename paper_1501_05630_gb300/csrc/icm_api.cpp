@@ -388,6 +388,18 @@ icm_status icm_sync(icm_ctx *ctx)
     return ICM_OK;
 }
 
+icm_status icm_query(icm_ctx *ctx)
+{
+    if (!ctx) return ICM_ERR_ARG;
+    const cudaError_t e = cudaStreamQuery(ctx->stream);
+    if (e == cudaSuccess) return ICM_OK;
+    if (e == cudaErrorNotReady) {
+        (void)cudaGetLastError();
+        return ICM_PENDING;
+    }
+    return cuda_fail(ctx, e, "stream query");
+}
+
 icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_t *n_bonds)
 {
     int N, Nb;
@@ -488,13 +500,24 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
             }
         }
     }
-    // launch shape: the shared-memory layout when the instance fits one CTA,
-    // else the global-resident layout with wider CTAs (set by apply_threads)
+    // launch shape: the shared-memory layout when several instances fit one
+    // SM; the global-resident layout with wider CTAs when the instance does not
+    // fit one CTA's shared memory, or fits only one or two CTAs per SM and has
+    // more sites per colour than a shared-memory CTA has threads (there the
+    // L1-cached wide CTA keeps more warps busy per SM)
     int n_icm = 0;
     while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
     int threads = icm::fused_threads(N);
-    if (icm::smem_layout(N, Z, R, G, n_T, n_icm, threads / 32, b->gauss, false).total > ctx->max_smem_optin)
-        threads = icm::fused_threads_wide(N);
+    {
+        const icm::SmemLayout sm0 = icm::smem_layout(N, Z, R, G, n_T, n_icm, threads / 32, b->gauss, false);
+        bool wide = sm0.total > ctx->max_smem_optin;
+        int c0 = 0;
+        if (!wide && N / 2 > icm::kMaxThreads &&
+            icm::fused_occupancy(b->gauss, Z, false, threads, sm0.total, &c0) == cudaSuccess && c0 <= 2)
+            wide = true;
+        (void)cudaGetLastError();
+        if (wide) threads = icm::fused_threads_wide(N);
+    }
     b->n_icm = n_icm;
     const int half = N / 2;
 

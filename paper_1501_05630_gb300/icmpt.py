@@ -20,6 +20,7 @@ from .inputs import CHIMERA, CUBIC3D, GAUSS, PM_J, SQUARE2D  # noqa: F401  (re-e
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libicmpt.so")
 DEVICE_PTR = 1
+PENDING = 1          # icm_query: work still running
 
 _lock = threading.Lock()
 _lib = None
@@ -41,7 +42,8 @@ class Schedule(ctypes.Structure):
 
 
 EXPORTS = [
-    "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_lattice_size", "icm_batch_create",
+    "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_query", "icm_lattice_size",
+    "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
@@ -75,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_last_error.argtypes = [vp]
         L.icm_last_error.restype = ctypes.c_char_p
         L.icm_sync.argtypes = [vp]
+        L.icm_query.argtypes = [vp]
         L.icm_lattice_size.argtypes = [i32, i32, vp, vp]
         L.icm_batch_create.argtypes = [vp, i32, i32, i32, i32, vp, vp, vp, vp, i32, ctypes.c_double, u64, u32,
                                        ctypes.POINTER(vp)]
@@ -159,6 +162,14 @@ class Context:
 
     def sync(self):
         self.check(self._lib.icm_sync(self._h))
+
+    def query(self) -> bool:
+        """True when all work enqueued on the context's stream has finished."""
+        rc = self._lib.icm_query(self._h)
+        if rc == PENDING:
+            return False
+        self.check(rc)
+        return True
 
     def close(self):
         if getattr(self, "_h", None):

@@ -7,12 +7,15 @@ own CUDA stream.  A step of the loop
 
   1. admits queued requests into free slots while the memory budget allows
      (a class's batch is created when its first request arrives);
-  2. advances every class that has active slots by `quantum` simulation
-     steps (one kernel launch per class, classes overlap on their streams);
-  3. at each slot whose sweep counter reached the end of a doubling window
-     [2^(b-1) Q, 2^b Q), reads the window's block means at the lowest
-     temperature, applies the thermalization test (icm_therm_update) and
-     either finishes the request (freeing the slot) or starts the next window.
+  2. for every class whose last launch has finished (a non-blocking query of
+     its stream), advances the sweep counters of the slots in that launch and,
+     at each slot that reached the end of a doubling window [2^(b-1) Q, 2^b Q),
+     reads the window's block means at the lowest temperature, applies the
+     thermalization test (icm_therm_update) and either finishes the request
+     (freeing the slot) or starts the next window;
+  3. launches the next `quantum` simulation steps of every idle class with
+     active slots.  Classes advance independently on their own streams, so a
+     class of large lattices does not hold back the small ones.
 
 The random streams are keyed by (seed, instance id) only, so a request's
 trajectory does not depend on its slot or on the other requests in the mix.
@@ -84,6 +87,7 @@ class _Class:
         self.slots: dict[int, _Slot] = {}
         self.T_min = float(req.T[0])
         self.bytes = capacity * slot_bytes(req)
+        self.in_flight: set[int] = set()       # slots of the launch still running
 
 
 def shape_key(r: Request):
@@ -140,24 +144,34 @@ class Server:
         return not self.queue and self.active == 0
 
     def step(self) -> int:
-        """Admit, advance every busy class by one quantum, test windows.
-        Returns the number of requests that finished in this step."""
+        """Admit; collect every class whose launch finished and test its
+        windows; launch the next quantum of every idle class.  Returns the
+        number of requests that finished in this step."""
         self._admit()
-        busy = [c for c in self.classes.values() if c.slots]
-        for c in busy:
-            c.batch.run(self.quantum)
         finished = 0
-        for c in busy:
-            c.ctx.sync()
-            due = []
-            for slot, st in c.slots.items():
-                st.t += self.quantum
-                if st.t >= st.boundary:
-                    due.append(slot)
-            if due:
-                obs = c.batch.read_observables(hist=False)
-                for slot in due:
-                    finished += self._window(c, slot, obs)
+        progressed = False
+        for c in self.classes.values():
+            if c.in_flight:
+                if not c.ctx.query():
+                    continue
+                progressed = True
+                due = []
+                for slot in c.in_flight:
+                    st = c.slots[slot]
+                    st.t += self.quantum
+                    if st.t >= st.boundary:
+                        due.append(slot)
+                c.in_flight = set()
+                if due:
+                    obs = c.batch.read_observables(hist=False)
+                    for slot in due:
+                        finished += self._window(c, slot, obs)
+            if c.slots and not c.in_flight:
+                c.batch.run(self.quantum)
+                c.in_flight = set(c.slots)
+                progressed = True
+        if not progressed:
+            time.sleep(50e-6)                          # every class is busy on the device
         return finished
 
     def run_until_idle(self, max_steps: int = 1 << 30):
@@ -181,7 +195,10 @@ class Server:
                 c = _Class(self.device, req, self.capacity)
                 self.classes[key] = c
                 self.used += c.bytes
-            if not c.free:
+            if not c.free or c.in_flight:
+                # no free slot, or the class is running: its slot tables are
+                # written between launches (a copy from pageable host memory
+                # would wait for the running launch)
                 waiting.append((ticket, req))
                 continue
             slot = c.free.pop()

@@ -290,7 +290,7 @@ def test_gauss_eq1_identity(icm):
 # ----------------------------------------------------------------------------- limits and errors
 def test_largest_shared_memory_instance(icm):
     """3D L=12 (1728 sites), 48 replicas: one CTA's shared memory holds the whole instance."""
-    _compare_sweeps(icm, O.CUBIC3D, 12, 24, 0.2, 2.0, 1.0, 2, 6, 12, check_every=3)
+    _compare_sweeps(icm, O.CUBIC3D, 12, 24, 0.2, 2.0, 1.0, 2, 6, 12, check_every=3, threads=128)
 
 
 # ----------------------------------------------------------------------------- global-resident (wide) layout
@@ -316,11 +316,12 @@ def test_wide_layout_2d_L128_64_replicas(icm):
 
 
 def test_wide_layout_default_for_large_instances(icm):
-    """The shared-memory layout while the instance fits one CTA, else the wide one."""
+    """The shared-memory layout while several instances fit one SM, else the wide one."""
     icmpt, ctx = icm
     for kind, L, dis, nT, wide in ((O.SQUARE2D, 128, I.PM_J, 32, True), (O.SQUARE2D, 128, I.PM_J, 8, True),
-                                   (O.SQUARE2D, 64, I.PM_J, 32, False), (O.CUBIC3D, 12, I.GAUSS, 24, False),
-                                   (O.CUBIC3D, 22, I.PM_J, 16, True)):
+                                   (O.SQUARE2D, 64, I.PM_J, 32, True), (O.CUBIC3D, 12, I.GAUSS, 24, True),
+                                   (O.CUBIC3D, 22, I.PM_J, 16, True), (O.CUBIC3D, 8, I.GAUSS, 24, False),
+                                   (O.CHIMERA, 8, I.PM_J, 30, False), (O.SQUARE2D, 8, I.PM_J, 16, False)):
         T = I.ladder(0.2, 2.0, nT)
         g = O.Geometry(kind, L)
         b = icmpt.Batch(ctx, kind, L, dis, I.couplings(g.Nb, dis, 1, [0]), T, 1.0, 1,

@@ -136,3 +136,34 @@ def test_batch_delta_matches_host(gpu):
         mean, se, n = b.delta(k)
         assert n == 32 and mean == pytest.approx(d.mean(), rel=1e-12, abs=1e-12)
         assert se == pytest.approx(d.std() / np.sqrt(31), rel=1e-9)
+
+
+@pytest.mark.gpu
+def test_server_mixes_wide_and_shared_memory_classes(gpu):
+    """2D L=128 requests (global-resident layout, one slow class) served
+    beside small shared-memory classes: classes advance independently, and
+    every result equals the instance replayed alone."""
+    icmpt, ctx = gpu
+    from paper_1501_05630_gb300.serve import Request, Server
+    reqs = []
+    for i, (L, nT) in enumerate([(128, 8), (8, 8), (8, 12), (128, 8), (16, 8), (8, 8)]):
+        N, Nb = icmpt.lattice_size(I.SQUARE2D, L)
+        inst = 3000 + i
+        reqs.append(Request(I.SQUARE2D, L, I.PM_J, I.ladder(0.5, 1.5, nT), 1.0, 13, inst,
+                            I.couplings(Nb, I.PM_J, 13, [inst])[0], I.initial_spins(N, 2 * nT, 13, [inst])[0]))
+    srv = Server(slots_per_class=2, quantum=16, eps_e=0.02, eps_ql=0.05, need=2, max_sweeps=256)
+    tickets = [srv.submit(r) for r in reqs]
+    srv.run_until_idle()
+    res = [srv.poll(t) for t in tickets]
+    assert all(r is not None for r in res)
+    wide = [c for c in srv.classes.values() if c.batch.info()["threads"] > 128]
+    assert len(wide) == 1
+    for r, q in zip(res, reqs):
+        a = icmpt.Batch(ctx, q.lattice, q.L, q.disorder, q.couplings[None].copy(), q.T, q.T_icm, q.seed,
+                        spins=q.spins[None].copy(), instance_ids=[q.instance_id])
+        a.set_schedule(t_meas=r.sweeps // 2)
+        a.run(r.sweeps)
+        oa = a.read_observables(hist=False)
+        assert oa.accE[0, 0] == r.accE and oa.acc_d[0, 0] == r.acc_d and oa.n_meas[0] == r.n_meas
+        a.close()
+    srv.close()
