@@ -45,6 +45,20 @@
  *           d = (E_{k+1} - E_k)/2.
  *      Gaussian: accept iff Delta >= 0 or (x>>8)*2^-24 < exp(Delta).
  *   R9 Measurement after the PT pass when t >= t_meas.
+ *  R10 Dilution (the remedy the introduction cites for the cluster move in
+ *      three dimensions): a bond with J_ij = 0 is absent from the lattice.
+ *      It is no edge of the interaction graph of R7, and it is not counted
+ *      in the link overlap q_l (a sum over the bonds of the lattice, with
+ *      N_b = the number of bonds present).  It adds nothing to H or to a
+ *      local field either way.
+ *  R11 On a diluted instance (some J_ij = 0) a Metropolis proposal with
+ *      Delta E = 0 is accepted with probability 1/2 (x < 2^31) instead of
+ *      always.  Dilution creates sites of degree 0, 1 and 2; there the
+ *      checkerboard sweep with deterministic zero-energy flips is not
+ *      ergodic (on a ring of four sites, s0 != s2 and s1 != s3 flips every
+ *      site every half-sweep forever).  The acceptance ratio
+ *      a(dE)/a(-dE) = exp(-beta dE) still holds, so the chain keeps the
+ *      Boltzmann distribution.  Undiluted instances keep R4 unchanged.
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +68,7 @@
 #define ORC_SQUARE 0
 #define ORC_CUBIC 1
 #define ORC_CHIMERA 2
+#define ORC_HYPERCUBIC4 3
 
 /* ------------------------------------------------------------------------ */
 /* Philox4x32-10, from its published definition (Salmon, Moraes, Dror, Shaw,
@@ -95,13 +110,16 @@ static uint32_t draw(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint3
  * b = 16 cell + 4 k0 + k1 joins (h=0,k0)-(h=1,k1); then the vertical bonds
  * (r,c,0,k)-(r+1,c,0,k), b = 16M^2 + 4(rM + c) + k; then the horizontal
  * bonds (r,c,1,k)-(r,c+1,1,k), b = 16M^2 + 4M(M-1) + 4(r(M-1) + c) + k.
- * Open boundary; colour (r + c + h) mod 2.                                  */
+ * Open boundary; colour (r + c + h) mod 2.
+ * 4D hypercubic: i = x + L(y + L(z + L w)), b = 4i + d, periodic, colour
+ * (x+y+z+w) mod 2.                                                         */
 int orc_geometry_sizes(int kind, int L, int32_t *N, int32_t *Nb)
 {
     if (L < 1) return -1;
     if (kind == ORC_SQUARE) { *N = L * L; *Nb = 2 * L * L; return 0; }
     if (kind == ORC_CUBIC) { *N = L * L * L; *Nb = 3 * L * L * L; return 0; }
     if (kind == ORC_CHIMERA) { *N = 8 * L * L; *Nb = 16 * L * L + 8 * L * (L - 1); return 0; }
+    if (kind == ORC_HYPERCUBIC4) { *N = L * L * L * L; *Nb = 4 * L * L * L * L; return 0; }
     return -1;
 }
 
@@ -127,6 +145,18 @@ int orc_geometry(int kind, int L, int32_t *bi, int32_t *bj, uint8_t *color)
                     bi[3 * i + 1] = i; bj[3 * i + 1] = x + L * ((y + 1) % L + L * z);
                     bi[3 * i + 2] = i; bj[3 * i + 2] = x + L * (y + L * ((z + 1) % L));
                 }
+    } else if (kind == ORC_HYPERCUBIC4) {
+        for (int w = 0; w < L; ++w)
+            for (int z = 0; z < L; ++z)
+                for (int y = 0; y < L; ++y)
+                    for (int x = 0; x < L; ++x) {
+                        int i = x + L * (y + L * (z + L * w));
+                        color[i] = (uint8_t)((x + y + z + w) % 2);
+                        bi[4 * i + 0] = i; bj[4 * i + 0] = (x + 1) % L + L * (y + L * (z + L * w));
+                        bi[4 * i + 1] = i; bj[4 * i + 1] = x + L * ((y + 1) % L + L * (z + L * w));
+                        bi[4 * i + 2] = i; bj[4 * i + 2] = x + L * (y + L * ((z + 1) % L + L * w));
+                        bi[4 * i + 3] = i; bj[4 * i + 3] = x + L * (y + L * (z + L * ((w + 1) % L)));
+                    }
     } else {
         int M = L;
         for (int r = 0; r < M; ++r)
@@ -176,7 +206,7 @@ typedef struct {
     int64_t *acc_n;               /* [nT] sum of n = #{q_i = -1} */
     int64_t *acc_q2;              /* [nT] sum of (N - 2n)^2 */
     int64_t *acc_pmin;            /* [nT] sum of min(n, N - n) */
-    int64_t *acc_d;               /* [nT] sum of d = #{bonds with q_i q_j = -1} */
+    int64_t *acc_d;               /* [nT] sum of d = #{bonds present with q_i q_j = -1} */
     int64_t *hist;                /* [nT][N+1] histogram of n */
     int64_t *n_meas;              /* [1] */
     uint32_t t;                   /* sweep counter */
@@ -193,7 +223,8 @@ typedef struct {                  /* the last sweep only */
     uint8_t *swap_acc;            /* [2][nT-1] */
 } orc_trace;
 
-/* Adjacency built from the bond list: for every site its incident bonds. */
+/* Adjacency built from the bond list: for every site its incident bonds.
+ * With couplings given, bonds with J = 0 are absent (R10).                 */
 typedef struct {
     int32_t *start;   /* [N+1] */
     int32_t *nbr;     /* [2 Nb] */
@@ -207,11 +238,16 @@ static int build_adjacency(const orc_problem *P, adjacency *A)
     A->nbr = malloc(sizeof(int32_t) * 2 * (size_t)(Nb > 0 ? Nb : 1));
     A->bond = malloc(sizeof(int32_t) * 2 * (size_t)(Nb > 0 ? Nb : 1));
     if (!A->start || !A->nbr || !A->bond) return -1;
-    for (int b = 0; b < Nb; ++b) { A->start[P->bi[b] + 1]++; A->start[P->bj[b] + 1]++; }
+    for (int b = 0; b < Nb; ++b) {
+        if (P->J && P->J[b] == 0.0) continue;
+        A->start[P->bi[b] + 1]++;
+        A->start[P->bj[b] + 1]++;
+    }
     for (int i = 0; i < N; ++i) A->start[i + 1] += A->start[i];
     int32_t *fill = calloc((size_t)N, sizeof(int32_t));
     if (!fill) return -1;
     for (int b = 0; b < Nb; ++b) {
+        if (P->J && P->J[b] == 0.0) continue;
         int i = P->bi[b], j = P->bj[b];
         int pi = A->start[i] + fill[i]++, pj = A->start[j] + fill[j]++;
         A->nbr[pi] = j; A->bond[pi] = b;
@@ -242,8 +278,9 @@ static uint64_t threshold(double a)
 
 static double unit24(uint32_t x) { return (double)(x >> 8) * (1.0 / 16777216.0); }
 
-/* Step 1: one Metropolis sweep of every replica (R2, R4). */
-static void metropolis_sweep(const orc_problem *P, orc_state *S, const adjacency *A)
+/* Step 1: one Metropolis sweep of every replica (R2, R4, R11).  `tie` = 1 on
+ * a diluted instance: a zero-energy proposal is accepted with probability 1/2. */
+static void metropolis_sweep(const orc_problem *P, orc_state *S, const adjacency *A, int tie)
 {
     int N = P->N, R = 2 * P->nT;
     for (int col = 0; col < 2; ++col)
@@ -259,10 +296,14 @@ static void metropolis_sweep(const orc_problem *P, orc_state *S, const adjacency
                 int accept;
                 if (P->pm) {
                     long m = (long)s[i] * lrint(h);
-                    accept = (m <= 0) || ((uint64_t)x < threshold((double)(-2 * m) * beta));
+                    if (m < 0) accept = 1;
+                    else if (m == 0) accept = tie ? (x < 0x80000000u) : 1;
+                    else accept = (uint64_t)x < threshold((double)(-2 * m) * beta);
                 } else {
                     double dE = 2.0 * (double)s[i] * h;
-                    accept = (dE <= 0.0) || (unit24(x) < exp(-beta * dE));
+                    if (dE < 0.0) accept = 1;
+                    else if (dE == 0.0) accept = tie ? (unit24(x) < 0.5) : 1;
+                    else accept = unit24(x) < exp(-beta * dE);
                 }
                 if (accept) s[i] = (int8_t)(-s[i]);
             }
@@ -363,6 +404,7 @@ static void measure(const orc_problem *P, orc_state *S, const double *E)
         int64_t n = 0, d = 0;
         for (int i = 0; i < N; ++i) n += (sa[i] * sb[i] == -1);
         for (int b = 0; b < P->Nb; ++b) {
+            if (P->J[b] == 0.0) continue;        /* absent bond (R10) */
             int i = P->bi[b], j = P->bj[b];
             d += ((sa[i] * sb[i]) * (sa[j] * sb[j]) == -1);
         }
@@ -393,6 +435,8 @@ int orc_run(const orc_problem *P, orc_state *S, uint32_t n_sweeps, const orc_tra
         for (int i = 0; i < N; ++i)
             if (P->color[i] == col) site_order[o++] = i;
     for (int r = 0; r < R; ++r) E[r] = energy(P, S->s + (size_t)r * N);
+    int diluted = 0;                             /* R10, R11 */
+    for (int b = 0; b < P->Nb; ++b) diluted |= (P->J[b] == 0.0);
     for (uint32_t step = 0; step < n_sweeps; ++step) {
         const orc_trace *trs = (tr && step + 1 == n_sweeps) ? tr : NULL;
         if (trs) {
@@ -402,7 +446,7 @@ int orc_run(const orc_problem *P, orc_state *S, uint32_t n_sweeps, const orc_tra
             }
             for (int q = 0; q < 2 * (nT - 1); ++q) trs->swap_acc[q] = 0;
         }
-        if (P->enable_metropolis) metropolis_sweep(P, S, &A);         /* step 1 */
+        if (P->enable_metropolis) metropolis_sweep(P, S, &A, diluted); /* step 1 */
         if (P->icm_every > 0 && S->t % (uint32_t)P->icm_every == 0)   /* steps 2a, 2b */
             for (int k = 0; k < nT; ++k)
                 if (P->T[k] <= P->T_icm) cluster_move(P, S, &A, k, site_order, queue, in_cluster, trs);

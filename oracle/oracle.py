@@ -20,7 +20,7 @@ _SO = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-SQUARE2D, CUBIC3D, CHIMERA = 0, 1, 2
+SQUARE2D, CUBIC3D, CHIMERA, HYPERCUBIC4D = 0, 1, 2, 3
 
 
 def build(force: bool = False) -> str:
@@ -118,6 +118,7 @@ class Instance:
         self.g = geom
         self.pm = bool(pm)
         self.J = np.ascontiguousarray(J, dtype=np.float64)
+        self.nb_present = int(np.count_nonzero(self.J))     # bonds with J = 0 are absent (dilution)
         self.T = np.ascontiguousarray(T, dtype=np.float64)
         nT = len(self.T)
         self.nT = nT
@@ -166,7 +167,7 @@ class Instance:
     def observables(self) -> dict:
         """Per-temperature averages over the measured sweeps."""
         m = max(int(self.n_meas[0]), 1)
-        N, Nb = self.g.N, self.g.Nb
+        N, Nb = self.g.N, max(self.nb_present, 1)
         return dict(
             e=self.accE / (2.0 * N * m),
             q_l=1.0 - 2.0 * self.acc_d / (Nb * m),

@@ -9,6 +9,8 @@ starts from, so that both sides of every comparison receive identical inputs:
 * disorder: Gaussian couplings N(0, 1) ("Benchmark model and observables") or
   bimodal +-1 couplings (the paper's remark on bimodal disorder), one value
   per bond in the caller's bond order;
+* bond dilution: each bond absent (J = 0) independently with a given
+  probability, the diluted lattices the paper's introduction cites;
 * initial spins, uniformly random +-1 for every replica;
 * random site masks with occupation probability p (site percolation, as in
   the Supplemental Material).
@@ -21,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 
 #: lattice kinds, in the order used by the C ABI
-SQUARE2D, CUBIC3D, CHIMERA = 0, 1, 2
+SQUARE2D, CUBIC3D, CHIMERA, HYPERCUBIC4D = 0, 1, 2, 3
 #: disorder kinds, in the order used by the C ABI
 PM_J, GAUSS = 0, 1
 
@@ -53,6 +55,18 @@ def couplings(n_bonds: int, disorder: int, seed: int, instance_ids) -> np.ndarra
             out[a] = _rng(seed, inst, 3).standard_normal(n_bonds).astype(np.float32)
     else:
         raise ValueError(f"unknown disorder kind {disorder}")
+    return out
+
+
+def dilute(J: np.ndarray, fraction: float, seed: int, instance_ids) -> np.ndarray:
+    """Copy of J[instance][bond] with each bond set to 0 (absent) independently
+    with probability `fraction`; the pattern depends on (seed, instance id)."""
+    ids = list(instance_ids)
+    out = np.array(J, copy=True)
+    if out.shape[0] != len(ids):
+        raise ValueError("one row of couplings per instance id")
+    for a, inst in enumerate(ids):
+        out[a][_rng(seed, inst, 6).random(out.shape[1]) < fraction] = 0
     return out
 
 
