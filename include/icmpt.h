@@ -74,16 +74,27 @@ typedef int32_t icm_status;
  *                  then (r,c,0,k)-(r+1,c,0,k) at b = 16M^2 + 4(rM+c) + k;
  *                  then (r,c,1,k)-(r,c+1,1,k) at
  *                  b = 16M^2 + 4M(M-1) + 4(r(M-1)+c) + k.
+ *   ICM_HYPERCUBIC4D : L^4 periodic hypercubic lattice ("any space
+ *                  dimension"), site i = x + L(y + L(z + L w)), bond
+ *                  b = 4i + d to the +x / +y / +z / +w neighbour.
  * Lattices need an even L >= 2 (the two-colouring); L = 2 keeps the doubled
- * bonds of the torus as separate bonds.                                     */
-typedef enum { ICM_SQUARE2D = 0, ICM_CUBIC3D = 1, ICM_CHIMERA = 2 } icm_lattice;
+ * bonds of the torus as separate bonds.  At most 65535 sites.               */
+typedef enum { ICM_SQUARE2D = 0, ICM_CUBIC3D = 1, ICM_CHIMERA = 2, ICM_HYPERCUBIC4D = 3 } icm_lattice;
 
 /* Disorder ("the interactions J_ij are selected from a Gaussian distribution
  * with mean zero and variance J^2 = 1"; bimodal disorder in the discussion of
  * degenerate ground states).
  *   ICM_PM_J  : J = +-1, int8 per bond; integer arithmetic, results are
  *               bit-exact functions of the inputs.
- *   ICM_GAUSS : J real, float32 per bond; fp32 arithmetic.               */
+ *   ICM_GAUSS : J real, float32 per bond; fp32 arithmetic.
+ * Dilution (the introduction's remedy for the cluster move in three
+ * dimensions): a coupling of exactly 0 means the bond is absent.  It is no
+ * edge of the cluster graph and is not counted in the link overlap, whose
+ * normalisation is the number of bonds present (icm_read_bond_counts).  On
+ * an instance with an absent bond, a zero-energy Metropolis proposal is
+ * accepted with probability 1/2 instead of always: sites of degree 0-2 make
+ * the checkerboard sweep with deterministic zero-energy flips non-ergodic.
+ * Detection is automatic, per instance.                                  */
 typedef enum { ICM_PM_J = 0, ICM_GAUSS = 1 } icm_disorder;
 
 #define ICM_DEVICE_PTR 1u     /* flags: the buffer is a device pointer */
@@ -126,8 +137,8 @@ icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_
 
 /* Create a batch of n_inst disorder instances of one lattice and disorder
  * kind that share one temperature ladder.
- *   couplings : [n_inst][N_b] in bond order; int8 (+-1) for ICM_PM_J,
- *               float32 for ICM_GAUSS.  Required.
+ *   couplings : [n_inst][N_b] in bond order; int8 (+-1, or 0 = absent) for
+ *               ICM_PM_J, float32 (0 = absent) for ICM_GAUSS.  Required.
  *   spins     : [n_inst][2 n_T][N] int8 (+1/-1), replica r = 2k + c is copy
  *               c at temperature position k.  NULL = all spins +1.
  *   instance_ids : [n_inst] uint32 < 2^24, the instance's RNG key.
@@ -137,9 +148,10 @@ icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_
  *   T_icm     : steps 2a/2b run at every k with T_k <= T_icm.
  *   seed      : 64-bit Philox key.
  * The schedule starts at its defaults; the sweep counter of every instance
- * starts at 0.  Errors: ICM_ERR_ARG (bad sizes or values),
- * ICM_ERR_UNSUPPORTED (instance too large for one CTA's shared memory),
- * ICM_ERR_OOM, ICM_ERR_CUDA.                                                */
+ * starts at 0.  Instances too large for one CTA's shared memory run in the
+ * global-resident layout (wider CTAs).  Errors: ICM_ERR_ARG (bad sizes or
+ * values), ICM_ERR_UNSUPPORTED (more than 65535 sites), ICM_ERR_OOM,
+ * ICM_ERR_CUDA.                                                             */
 icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder,
                             int32_t n_inst, const void *couplings, const int8_t *spins,
                             const uint32_t *instance_ids, const double *T, int32_t n_T,
@@ -169,6 +181,10 @@ icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps);
 /* ---------------------------------------------------------------- reads
  * Every read waits for the batch's outstanding work.                      */
 
+/* Bonds present (coupling != 0) per instance, [n_inst] int32, host memory:
+ * N_b for an undiluted instance.  The link overlap of instance i is
+ * q_l = 1 - 2 acc_d / (bonds_i * n_meas).  No device work.               */
+icm_status icm_read_bond_counts(const icm_batch *b, int32_t *out);
 /* Spins [n_inst][2 n_T][N] int8 +-1, site order, replica r = 2k + c. */
 icm_status icm_read_spins(icm_batch *b, int8_t *out, uint32_t flags);
 /* Energies [n_inst][2 n_T] (double; exact integers for ICM_PM_J). */
@@ -251,7 +267,9 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
  * or arena that forbids outside allocations, pipelines that must not hit
  * cudaMalloc's implicit device synchronisation, and hosts that budget every
  * byte of HBM in advance.
- *   couplings : device [n_inst][N_b] in bond order (int8 +-1 or float32)
+ *   couplings : device [n_inst][N_b] in bond order (int8 +-1 or float32);
+ *               this entry point does not take diluted +-J couplings (an
+ *               int8 0 counts as +1), Gaussian zeros contribute 0
  *   spins     : device [n_inst][n_rep][N] int8 +-1, 1 <= n_rep <= 64
  *   out       : device [n_inst][n_rep] double, H = -sum_<ij> J_ij s_i s_j
  * Work is enqueued on the context's stream; the call returns after it ends.

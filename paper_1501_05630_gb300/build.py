@@ -1,6 +1,6 @@
 """Build the CUDA library libicmpt.so in-tree, for sm_103a only.
 
-Two translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_1501_05630_gb300/_build/libicmpt.so`` (the CUDA runtime is linked
 statically, so the library depends only on the driver).
 """
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libicmpt.so")
-SOURCES = ["pt_icm.cu", "icm_api.cpp", "icm_static.cu", "percolation.cu"]
+SOURCES = ["pt_icm.cu", "fused_pmj.cu", "fused_gauss.cu", "icm_api.cpp", "icm_static.cu", "percolation.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

@@ -41,6 +41,11 @@ int lattice_size(int lattice, int L, int *N, int *Nb)
     case ICM_SQUARE2D: *N = L * L; *Nb = 2 * L * L; return 0;
     case ICM_CUBIC3D: *N = L * L * L; *Nb = 3 * L * L * L; return 0;
     case ICM_CHIMERA: *N = 8 * L * L; *Nb = 16 * L * L + 8 * L * (L - 1); return 0;
+    case ICM_HYPERCUBIC4D:
+        if (L > 64) return -1;               // L^4 sites must stay an int
+        *N = L * L * L * L;
+        *Nb = 4 * L * L * L * L;
+        return 0;
     default: return -1;
     }
 }
@@ -77,6 +82,19 @@ bool build_geometry(int lattice, int L, Geometry &g)
                     g.bi[3 * i + 1] = i; g.bj[3 * i + 1] = ny;
                     g.bi[3 * i + 2] = i; g.bj[3 * i + 2] = nz;
                 }
+    } else if (lattice == ICM_HYPERCUBIC4D) {
+        g.Z = 8;
+        for (int w = 0; w < L; ++w)
+            for (int z = 0; z < L; ++z)
+                for (int y = 0; y < L; ++y)
+                    for (int x = 0; x < L; ++x) {
+                        const int i = x + L * (y + L * (z + L * w));
+                        g.color[i] = (uint8_t)((x + y + z + w) & 1);
+                        g.bi[4 * i] = i; g.bj[4 * i] = ((x + 1) % L) + L * (y + L * (z + L * w));
+                        g.bi[4 * i + 1] = i; g.bj[4 * i + 1] = x + L * (((y + 1) % L) + L * (z + L * w));
+                        g.bi[4 * i + 2] = i; g.bj[4 * i + 2] = x + L * (y + L * (((z + 1) % L) + L * w));
+                        g.bi[4 * i + 3] = i; g.bj[4 * i + 3] = x + L * (y + L * (z + L * ((w + 1) % L)));
+                    }
     } else {
         g.Z = 6;
         const int M = L;
@@ -120,7 +138,9 @@ uint32_t acceptance_threshold(double a)
 
 // Temperature-dependent tables of a ladder T[0..n_T-1] (ascending):
 //  thr_metro[r][m] = floor(exp((-2m) beta_k) 2^32) for the +-J Metropolis
-//    test at replica position r = 2k + c and m = s_i h_i = 1..6;
+//    test at replica position r = 2k + c and m = s_i h_i = 1..Z, and 2^31 at
+//    m = 0 (the zero-energy proposal of a diluted instance; the other
+//    instances accept every m <= 0 before the table); stride thr_stride(Z);
 //  b2l[r] = -2 beta_k log2(e) for the Gaussian test;
 //  dbeta_l2e[k] = (beta_k - beta_{k+1}) log2(e) for Gaussian PT decisions;
 //  thr_swap (per pair k, d = 1..len_k) = floor(exp((-2d)(beta_k - beta_{k+1})) 2^32)
@@ -133,16 +153,17 @@ struct TempTables {
     std::vector<int32_t> swap_off, swap_len;
 };
 
-void temperature_tables(const double *T, int n_T, int Nb, TempTables &t)
+void temperature_tables(const double *T, int n_T, int Nb, int Z, TempTables &t)
 {
-    const int R = 2 * n_T;
+    const int R = 2 * n_T, TS = icm::thr_stride(Z);
     t.beta.assign(n_T, 0.0);
     for (int k = 0; k < n_T; ++k) t.beta[k] = 1.0 / T[k];
-    t.thr_metro.assign((size_t)R * 8, 0u);
+    t.thr_metro.assign((size_t)R * TS, 0u);
     t.b2l.assign(R, 0.f);
     for (int r = 0; r < R; ++r) {
         const double bk = t.beta[r / 2];
-        for (int m = 1; m <= 6; ++m) t.thr_metro[(size_t)r * 8 + m] = acceptance_threshold((double)(-2 * m) * bk);
+        t.thr_metro[(size_t)r * TS] = 0x80000000u;
+        for (int m = 1; m <= Z; ++m) t.thr_metro[(size_t)r * TS + m] = acceptance_threshold((double)(-2 * m) * bk);
         t.b2l[r] = (float)(-2.0 * bk * 1.4426950408889634);
     }
     t.dbeta_l2e.assign(n_T > 1 ? n_T - 1 : 0, 0.f);
@@ -190,6 +211,10 @@ struct icm_batch {
     int8_t *raw_spins = nullptr;  // [n_inst][R][N]
     double *raw_E = nullptr;      // [n_inst][R]
     int32_t *edge_bond = nullptr; // [N][Z]
+    // dilution: bonds present per instance (host copy of nb_inst), and the
+    // degree of the undiluted lattice when uniform (0: chimera)
+    std::vector<int32_t> h_nb;
+    int uniform_z = 0;
     // wide (global-resident) layout: per-CTA scratch, grown on demand (in allocs)
     uint32_t *scratch = nullptr;      // [scratch_ctas][wide_scratch_words(N)]
     int scratch_ctas = 0;
@@ -247,6 +272,33 @@ icm_status copy_out(icm_ctx *ctx, void *dst, const void *src, size_t bytes, uint
     return ICM_OK;
 }
 
+// Per-instance dilution tables of slots [first, first + count) from the bond
+// couplings in raw_coup, then the batch flags: the batch is diluted while any
+// instance has an absent bond (the kernels then read per-instance neighbour
+// tables and degrees).  Waits for the stream (the counts come back to the host).
+icm_status refresh_dilution(icm_batch *b, int first, int count)
+{
+    icm_ctx *ctx = b->ctx;
+    icm::KParams &P = b->kp;
+    const size_t esz = b->gauss ? 4 : 1;
+    int32_t *nb = const_cast<int32_t *>(P.nb_inst) + first;
+    ICM_CUDA(ctx, cudaMemsetAsync(nb, 0, (size_t)count * sizeof(int32_t), ctx->stream));
+    ICM_CUDA(ctx, icm::launch_expand_dilution((const unsigned char *)b->raw_coup + (size_t)first * P.Nb * esz, b->gauss,
+                                              b->edge_bond, P.nbr, count, P.N, P.Z, P.Nb,
+                                              const_cast<uint16_t *>(P.nbr_inst) + (size_t)first * P.N * P.Z,
+                                              const_cast<uint8_t *>(P.zdeg_inst) + (size_t)first * P.N, nb,
+                                              ctx->stream));
+    b->h_nb.resize(b->n_inst, P.Nb);
+    ICM_CUDA(ctx, cudaMemcpyAsync(b->h_nb.data() + first, nb, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                  ctx->stream));
+    ICM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    bool diluted = false;
+    for (int32_t v : b->h_nb) diluted |= v < P.Nb;
+    P.diluted = diluted ? 1 : 0;
+    P.const_z = diluted ? 0 : b->uniform_z;
+    return ICM_OK;
+}
+
 icm_status upload_state(icm_batch *b, const void *couplings, const int8_t *spins, uint32_t flags)
 {
     icm_ctx *ctx = b->ctx;
@@ -258,6 +310,7 @@ icm_status upload_state(icm_batch *b, const void *couplings, const int8_t *spins
         ICM_CUDA(ctx, icm::launch_expand_couplings(b->raw_coup, b->gauss, b->edge_bond, b->n_inst, P.N, P.Z, P.Nb,
                                                    const_cast<float *>(P.Jd), const_cast<uint8_t *>(P.Jb),
                                                    ctx->stream));
+        if ((st = refresh_dilution(b, 0, b->n_inst))) return st;
     }
     if (spins) {
         const size_t bytes = (size_t)b->n_inst * P.R * P.N;
@@ -419,7 +472,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     if (!ctx) return ICM_ERR_ARG;
     if (!out) return fail(ctx, ICM_ERR_ARG, "out is NULL");
     *out = nullptr;
-    if (lattice < 0 || lattice > 2) return fail(ctx, ICM_ERR_ARG, "unknown lattice kind");
+    if (lattice < 0 || lattice > 3) return fail(ctx, ICM_ERR_ARG, "unknown lattice kind");
     if (disorder != ICM_PM_J && disorder != ICM_GAUSS) return fail(ctx, ICM_ERR_ARG, "unknown disorder kind");
     if (lattice != ICM_CHIMERA && (L < 2 || (L & 1))) return fail(ctx, ICM_ERR_ARG, "lattices need an even L >= 2");
     if (lattice == ICM_CHIMERA && L < 1) return fail(ctx, ICM_ERR_ARG, "chimera needs M >= 1");
@@ -485,7 +538,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         const int deg = (int)inc[i].size();
         if (deg < 4 || deg > Z) {
             destroy_batch(b);
-            return fail(ctx, ICM_ERR_UNSUPPORTED, "site degree outside 4..6");
+            return fail(ctx, ICM_ERR_UNSUPPORTED, "site degree outside 4..8");
         }
         if (deg != Z) uniform = false;
         const int p = pos[i];
@@ -523,7 +576,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
 
     // temperature tables
     TempTables tt;
-    temperature_tables(T, n_T, g.Nb, tt);
+    temperature_tables(T, n_T, g.Nb, Z, tt);
     std::vector<double> &beta = tt.beta;
     std::vector<uint32_t> &thr_metro = tt.thr_metro;
     std::vector<float> &b2l = tt.b2l, &dbeta_l2e = tt.dbeta_l2e;
@@ -534,6 +587,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     icm::KParams &P = b->kp;
     P.N = N; P.Nb = g.Nb; P.nT = n_T; P.R = R; P.G = G; P.Z = Z; P.n_inst = n_inst; P.n_icm = n_icm;
     P.half = half; P.NW = (N + 31) / 32; P.const_z = uniform ? Z : 0;
+    b->uniform_z = P.const_z;
     P.seed_lo = (uint32_t)(seed & 0xffffffffu);
     P.seed_hi = (uint32_t)(seed >> 32);
     {
@@ -555,6 +609,9 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     long long *d_acc64, *d_nmeas;
     unsigned long long *d_hist;
     uint8_t *d_trsw;
+    uint16_t *d_nbr_inst;
+    uint8_t *d_zdeg_inst;
+    int32_t *d_nb_inst;
     const size_t nk = (size_t)n_inst * n_T;
     if ((st = dalloc(b, &d_nbr, (size_t)N * Z)) || (st = dalloc(b, &d_pos2site, N)) || (st = dalloc(b, &d_zdeg, N)) ||
         (st = dalloc(b, &b->edge_bond, (size_t)N * Z)) ||
@@ -562,7 +619,9 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         (st = dalloc(b, &d_Jd, b->gauss ? (size_t)n_inst * N * Z : 1)) ||
         (st = dalloc(b, &d_spins, (size_t)n_inst * G * N)) || (st = dalloc(b, &d_Ef, (size_t)n_inst * R)) ||
         (st = dalloc(b, &d_Ei, (size_t)n_inst * R)) || (st = dalloc(b, &d_t, n_inst)) ||
-        (st = dalloc(b, &d_id, n_inst)) || (st = dalloc(b, &d_thr, (size_t)R * 8)) || (st = dalloc(b, &d_b2l, R)) ||
+        (st = dalloc(b, &d_id, n_inst)) || (st = dalloc(b, &d_thr, (size_t)R * icm::thr_stride(Z))) ||
+        (st = dalloc(b, &d_b2l, R)) || (st = dalloc(b, &d_nbr_inst, (size_t)n_inst * N * Z)) ||
+        (st = dalloc(b, &d_zdeg_inst, (size_t)n_inst * N)) || (st = dalloc(b, &d_nb_inst, n_inst)) ||
         (st = dalloc(b, &d_beta, n_T)) || (st = dalloc(b, &d_dbl, n_T - 1)) || (st = dalloc(b, &d_thrs, thr_swap.size())) ||
         (st = dalloc(b, &d_off, n_T - 1)) || (st = dalloc(b, &d_len, n_T - 1)) || (st = dalloc(b, &d_accE, nk)) ||
         (st = dalloc(b, &d_acc64, 4 * nk)) || (st = dalloc(b, &d_hist, nk * (N + 1))) ||
@@ -579,6 +638,8 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     P.beta = d_beta; P.dbeta_l2e = d_dbl; P.thr_swap = d_thrs; P.swap_off = d_off; P.swap_len = d_len; P.accE = d_accE;
     P.acc64 = d_acc64; P.hist = d_hist; P.n_meas = d_nmeas; P.tr_n_pre = d_trn; P.tr_flip2a = d_trf;
     P.tr_seed = d_trs; P.tr_csize = d_trc; P.tr_eb = d_treb; P.tr_ea = d_trea; P.tr_swap = d_trsw;
+    P.nbr_inst = d_nbr_inst; P.zdeg_inst = d_zdeg_inst; P.nb_inst = d_nb_inst;
+    b->h_nb.assign(n_inst, g.Nb);
 
     std::vector<uint32_t> ids(n_inst);
     for (int i = 0; i < n_inst; ++i) {
@@ -674,6 +735,13 @@ icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps)
     P.t_meas_inst = b->d_tmeas;
     ICM_CUDA(b->ctx, icm::launch_fused(P, b->gauss, b->threads, b->grid, n_sweeps, b->ctx->stream));
     b->launches += 1;
+    return ICM_OK;
+}
+
+icm_status icm_read_bond_counts(const icm_batch *b, int32_t *out)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    for (int i = 0; i < b->n_inst; ++i) out[i] = b->h_nb[i];
     return ICM_OK;
 }
 
@@ -813,6 +881,7 @@ icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings,
     float *Jd = b->gauss ? const_cast<float *>(P.Jd) + (size_t)slot * P.N * P.Z : nullptr;
     uint8_t *Jb = b->gauss ? nullptr : const_cast<uint8_t *>(P.Jb) + (size_t)slot * P.N;
     ICM_CUDA(ctx, icm::launch_expand_couplings(raw_c, b->gauss, b->edge_bond, 1, P.N, P.Z, P.Nb, Jd, Jb, ctx->stream));
+    if ((st = refresh_dilution(b, slot, 1))) return st;
     uint32_t *sp = P.spins + (size_t)slot * P.G * P.N;
     if (spins) {
         int8_t *raw_s = b->raw_spins + (size_t)slot * P.R * P.N;
@@ -828,6 +897,9 @@ icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings,
     Q.Jb = Jb;
     Q.Ef = P.Ef + (size_t)slot * P.R;
     Q.Ei = P.Ei + (size_t)slot * P.R;
+    Q.nbr_inst = P.nbr_inst + (size_t)slot * P.N * P.Z;
+    Q.zdeg_inst = P.zdeg_inst + (size_t)slot * P.N;
+    Q.nb_inst = P.nb_inst + slot;
     ICM_CUDA(ctx, icm::launch_init_energies(Q, b->gauss, ctx->stream));
     ICM_CUDA(ctx, cudaMemsetAsync(P.tsweep + slot, 0, 4, ctx->stream));
     ICM_CUDA(ctx, cudaMemcpyAsync(const_cast<uint32_t *>(P.inst_id) + slot, &instance_id, 4, cudaMemcpyHostToDevice,
@@ -905,11 +977,12 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
         (st = copy_out(b->ctx, nm.data(), P.n_meas, (size_t)b->n_inst * 8, 0)))
         return st;
     ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
-    const double N = P.N, Nb = P.Nb, T = b->T[k];
+    const double N = P.N, T = b->T[k];
     double s1 = 0, s2 = 0;
     int n = 0;
     for (int i = 0; i < b->n_inst; ++i) {
         if (nm[i] <= 0 || (!b->h_active.empty() && !b->h_active[i])) continue;
+        const double Nb = b->h_nb[i] > 0 ? (double)b->h_nb[i] : 1.0;   // bonds present
         const double m = (double)nm[i];
         const double e = accE[(size_t)i * P.nT + k] / (2.0 * N * m);
         const double ql = 1.0 - 2.0 * (double)accd[(size_t)i * P.nT + k] / (Nb * m);
@@ -1168,7 +1241,7 @@ icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, doub
         if (k && !(T[k] > T[k - 1])) return fail(b->ctx, ICM_ERR_ARG, "temperatures must be strictly ascending");
     }
     TempTables tt;
-    temperature_tables(T, n_T, P.Nb, tt);
+    temperature_tables(T, n_T, P.Nb, P.Z, tt);
     icm_status st;
     if (tt.thr_swap.size() > b->thr_swap_cap) {
         uint32_t *d = nullptr;
@@ -1302,7 +1375,7 @@ icm_status icm_load(icm_batch *b, const void *buf, size_t len)
     ICM_CUDA(b->ctx, icm::launch_expand_couplings(b->raw_coup, b->gauss, b->edge_bond, b->n_inst, P.N, P.Z, P.Nb,
                                                   const_cast<float *>(P.Jd), const_cast<uint8_t *>(P.Jb),
                                                   b->ctx->stream));
-    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    if ((st = refresh_dilution(b, 0, b->n_inst))) return st;
     if (h.has_slots) {
         ICM_CUDA(b->ctx, cudaMemcpy(b->h_active.data(), b->d_active, b->n_inst, cudaMemcpyDeviceToHost));
         ICM_CUDA(b->ctx, cudaMemcpy(b->h_tmeas.data(), b->d_tmeas, b->n_inst * 8, cudaMemcpyDeviceToHost));

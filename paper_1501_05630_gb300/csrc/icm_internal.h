@@ -7,11 +7,18 @@
 
 namespace icm {
 
-constexpr int kMaxZ = 6;          // largest degree of the supported graphs
+constexpr int kMaxZ = 8;          // largest degree of the supported graphs (4D hypercubic)
 constexpr int kMaxR = 64;         // replicas per instance (2 N_T, N_T <= 32)
 constexpr int kMaxThreads = 128;  // threads per CTA of the fused kernel, shared-memory layout
 constexpr int kMaxThreadsWide = 1024;  // threads per CTA of the fused kernel, global-resident layout
 constexpr int kPlanes = 8;        // bit-planes of the vertical counters (counts < 256 per thread)
+
+// Entries per replica of the +-J Metropolis threshold table, indexed by
+// m = s_i h_i = 0..Z (m = 0: the probability-1/2 entry of diluted instances).
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+constexpr int thr_stride(int Z) { return Z > 7 ? 16 : 8; }
 
 // Byte offsets into the fused kernel's dynamic shared memory.  In the
 // global-resident ("wide") layout the spins, couplings, neighbour table,
@@ -23,7 +30,7 @@ struct SmemLayout {
     int coup;       // float [N][Z] (Gaussian) or uint8 [N] bit d = (J < 0) (+-J)
     int E;          // float or int32 [R]
     int Epart;      // float or int32 [nwarps][max(R, 32)]
-    int rtab;       // uint32 [R][8] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
+    int rtab;       // uint32 [R][thr_stride(Z)] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
     int icm_mask;   // uint32 [n_icm][NW] overlap masks per ICM pair
     int icm_C;      // uint2 [N]         cluster bits of both words (bit 2k: site in pair k's cluster)
     int swap_x;     // uint32 [2][32]
@@ -46,6 +53,7 @@ struct KParams {
     int N, Nb, nT, R, G, Z, n_inst, n_icm, half, NW;
     int const_z;                  // degree when uniform (lattices), 0 = per-site table
     int wide;                     // 1: global-resident layout (instances too large for shared memory)
+    int diluted;                  // 1: some instance has absent bonds (J = 0): per-instance tables below
     int scratch_words;            // wide layout: uint32 words of scratch per CTA (cluster words, masks)
     uint32_t *scratch;            // wide layout: [grid][scratch_words]
     int small_counts;             // per-thread observable counts fit 4 bit-planes
@@ -53,6 +61,11 @@ struct KParams {
     const uint16_t *nbr;          // [N][Z]
     const uint8_t *zdeg;          // [N]
     const uint16_t *pos2site;     // [N]
+    // per instance, used when `diluted`: neighbour positions with absent bonds
+    // replaced by the site itself, degree = bonds present, bonds present
+    const uint16_t *nbr_inst;     // [n_inst][N][Z]
+    const uint8_t *zdeg_inst;     // [n_inst][N]
+    const int32_t *nb_inst;       // [n_inst]
     // per instance
     const float *Jd;              // [n_inst][N][Z]  (Gaussian)
     const uint8_t *Jb;            // [n_inst][N]     (+-J)
@@ -62,7 +75,7 @@ struct KParams {
     uint32_t *tsweep;             // [n_inst]
     const uint32_t *inst_id;      // [n_inst]
     // temperature tables
-    const uint32_t *thr_metro;    // [R][8]
+    const uint32_t *thr_metro;    // [R][thr_stride(Z)]
     const float *b2l;             // [R]
     const double *beta;           // [nT]
     const float *dbeta_l2e;       // [nT-1] (beta_k - beta_{k+1}) log2(e)
@@ -113,6 +126,12 @@ cudaError_t launch_unpack_spins(const uint32_t *src, int8_t *dst, const uint16_t
                                 int R, int G, int N, cudaStream_t st);
 cudaError_t launch_expand_couplings(const void *bond_J, bool gauss, const int32_t *edge_bond, int n_inst,
                                     int N, int Z, int Nb, float *Jd, uint8_t *Jb, cudaStream_t st);
+// Per-instance tables of a diluted batch from the bond couplings: neighbour
+// positions (absent bond -> the site itself), degree and bonds present.
+// nb_inst must be zero on entry (the kernel adds to it).
+cudaError_t launch_expand_dilution(const void *bond_J, bool gauss, const int32_t *edge_bond, const uint16_t *nbr,
+                                   int n_inst, int N, int Z, int Nb, uint16_t *nbr_inst, uint8_t *zdeg_inst,
+                                   int32_t *nb_inst, cudaStream_t st);
 cudaError_t launch_init_energies(const KParams &P, bool gauss, cudaStream_t st);
 cudaError_t launch_energies_to_double(const KParams &P, bool gauss, double *out, cudaStream_t st);
 

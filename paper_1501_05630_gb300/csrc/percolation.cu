@@ -146,17 +146,10 @@ icm_status percolation(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t n_masks
     const uint32_t thr = (uint32_t)tv;
     const int grid = n_masks < 152 * 8 ? n_masks : 152 * 8;
     if (e == cudaSuccess) {
-        if (Z == 4) {
-            e = cudaFuncSetAttribute(largest_cluster_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                largest_cluster_kernel<4><<<grid, 256, smem, st>>>(mk, n_masks, N, d_nbr, d_p2s, thr,
-                                                                   (uint32_t)seed, (uint32_t)(seed >> 32), out);
-        } else {
-            e = cudaFuncSetAttribute(largest_cluster_kernel<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e == cudaSuccess)
-                largest_cluster_kernel<6><<<grid, 256, smem, st>>>(mk, n_masks, N, d_nbr, d_p2s, thr,
-                                                                   (uint32_t)seed, (uint32_t)(seed >> 32), out);
-        }
+        auto kern = Z == 4 ? largest_cluster_kernel<4> : Z == 6 ? largest_cluster_kernel<6> : largest_cluster_kernel<8>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            kern<<<grid, 256, smem, st>>>(mk, n_masks, N, d_nbr, d_p2s, thr, (uint32_t)seed, (uint32_t)(seed >> 32), out);
         if (e == cudaSuccess) e = cudaGetLastError();
     }
     if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(smax, d_out, (size_t)n_masks * 4, cudaMemcpyDeviceToHost, st);

@@ -35,12 +35,29 @@
 #include <cstdio>
 #include <type_traits>
 
+// The file is compiled three times so that the fused-kernel variants build in
+// parallel: ICM_PART 0 = layout kernels and host entry points (the default),
+// 1 = fused kernels for +-J couplings, 2 = fused kernels for Gaussian couplings
+// (fused_pmj.cu and fused_gauss.cu define the macro and include this file).
+#ifndef ICM_PART
+#define ICM_PART 0
+#endif
+
+namespace icm {
+cudaError_t launch_fused_pmj(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st);
+cudaError_t launch_fused_gauss(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st);
+cudaError_t fused_occupancy_pmj(int Z, bool wide, int threads, int smem, int *ctas);
+cudaError_t fused_occupancy_gauss(int Z, bool wide, int threads, int smem, int *ctas);
+int debug_phase_cycles_pmj(unsigned long long *out, int reset);
+int debug_phase_cycles_gauss(unsigned long long *out, int reset);
+}  // namespace icm
+
 // Optional per-phase cycle counters (compile with -DICM_PHASE_TIMERS): thread 0
 // of every CTA adds the clock64() cycles between phase marks to a global
 // table, read back by icm_debug_phase_cycles().  Off by default; no work is
 // skipped either way.
 #ifdef ICM_PHASE_TIMERS
-__device__ unsigned long long g_icm_phase_cycles[16];
+static __device__ unsigned long long g_icm_phase_cycles[16];   // one table per compiled part
 #define PHASE_INIT() long long ph_last_ = clock64(); long long ph_acc_[8] = {0, 0, 0, 0, 0, 0, 0, 0}
 #define PHASE_MARK(i) do { if (threadIdx.x == 0) { const long long n_ = clock64(); ph_acc_[i] += n_ - ph_last_; ph_last_ = n_; } } while (0)
 #define PHASE_FLUSH() do { if (threadIdx.x == 0) for (int i_ = 0; i_ < 7; ++i_) atomicAdd(&g_icm_phase_cycles[i_], (unsigned long long)ph_acc_[i_]); } while (0)
@@ -197,6 +214,8 @@ struct Sm {
     double *accE;
     long long *acc64;
     long long *nmeas;
+    int tie;         // this instance is diluted: a zero-energy proposal is accepted with probability 1/2
+    int nb;          // bonds present in this instance
 };
 
 __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
@@ -228,6 +247,21 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     return S;
 }
 
+// Per bit lane: u >= k, where u's binary digits are the bit-planes c3 c2 c1 c0
+// and k (0..15) is the same for all lanes.
+__device__ __forceinline__ uint32_t ge_bitsliced(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int k)
+{
+    const uint32_t c[4] = {c0, c1, c2, c3};
+    uint32_t gt = 0u, eq = ~0u;
+#pragma unroll
+    for (int i = 3; i >= 0; --i) {
+        const uint32_t kb = 0u - (uint32_t)((k >> i) & 1);
+        gt |= eq & c[i] & ~kb;
+        eq &= ~(c[i] ^ kb);
+    }
+    return gt | eq;
+}
+
 // Neighbour positions of position p (padding entries repeat p), read as
 // 32-bit pairs from the [N][Z] uint16 table (Z even, so rows are 4-byte aligned).
 template <int Z>
@@ -249,7 +283,7 @@ __device__ __forceinline__ void load_nbrs(const uint16_t *nbr, int p, int (&q)[Z
 // are updated at beta = 0 and never read, so the inner loop has no guards.
 // Two Philox4x32-10 blocks are generated together (8 draws) so that their
 // dependency chains interleave.
-template <bool GAUSS, int Z, bool WIDE>
+template <bool GAUSS, int Z, bool WIDE, bool DIL>
 __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g, int COLOR,
                                            int H)
 {
@@ -301,7 +335,14 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                         const float sh = ((sw >> b) & 1u) ? -h : h;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
                         const uint32_t thr = __float2uint_rz(ex2_approx(fmaf(b2l[b], sh, 32.f)));
-                        const bool a = (sh <= 0.f) || (xr < thr);
+                        bool a;
+                        if constexpr (DIL) {
+                            // diluted instance: Delta E = 0 (a site without bonds) is
+                            // accepted with probability 1/2
+                            a = (sh < 0.f) || (sh == 0.f ? (!S.tie || xr < 0x80000000u) : (xr < thr));
+                        } else {
+                            a = (sh <= 0.f) || (xr < thr);
+                        }
                         flip |= (uint32_t)a << b;
                         acc[b] -= sh;                           // e = -s'h: -sh, or +sh after a flip
                         if (a) acc[b] += 2.f * sh;
@@ -309,7 +350,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                 }
             }
         } else {
-            uint32_t c0 = 0, c1 = 0, c2 = 0;
+            uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;   // bit-planes of u = # unsatisfied bonds
             const uint32_t jb = S.Jb[p];
             int q[Z];
             load_nbrs<Z>(S.nbr, p, q);
@@ -320,15 +361,30 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                 c0 ^= u;
                 const uint32_t t1 = c1 & t0;
                 c1 ^= t0;
-                c2 |= t1;
+                if constexpr (Z > 7) {              // u up to 8: a fourth plane
+                    const uint32_t t2 = c2 & t1;
+                    c2 ^= t1;
+                    c3 |= t2;
+                } else {
+                    c2 |= t1;
+                }
             }
             c0 >>= sh0;
             c1 >>= sh0;
             c2 >>= sh0;
-            const int z = P.const_z ? P.const_z : (int)S.zdeg[p];
-            // m = z - 2u <= 0  <=>  u >= ceil(z/2): always accepted
-            flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
-            const uint32_t *thr = S.thr + rbase * 8;
+            c3 >>= sh0;
+            const int z = (!DIL && P.const_z) ? P.const_z : (int)S.zdeg[p];   // degree = bonds present
+            // m = z - 2u <= 0  <=>  u >= ceil(z/2): always accepted; on a diluted
+            // instance only m < 0 (u >= floor(z/2) + 1), m = 0 takes the 1/2 entry
+            if constexpr (DIL) {
+                flip = ge_bitsliced(c0, c1, c2, c3, S.tie ? (z >> 1) + 1 : (z + 1) >> 1) & 0xFFFFu;
+            } else if constexpr (Z > 7) {
+                flip = (c3 | c2) & 0xFFFFu;         // z = 8: u >= 4
+            } else {
+                flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
+            }
+            constexpr int TS = thr_stride(Z);
+            const uint32_t *thr = S.thr + rbase * TS;
 #pragma unroll
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
@@ -337,10 +393,11 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;
-                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2) |
+                                            (((c3 >> b) & 1u) << 3));
                         const int m = z - 2 * u;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
-                        const uint32_t th = thr[b * 8 + (m > 0 ? m : 0)];
+                        const uint32_t th = thr[b * TS + (m > 0 ? m : 0)];
                         flip |= (uint32_t)(xr < th) << b;
                         acc[b] += ((flip >> b) & 1u) ? m : -m;
                     }
@@ -359,14 +416,14 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 // Step 1 for all replicas: colour 0 then colour 1, each as 16-bit passes over
 // the site words.  One call site, so the pass body exists once in the kernel
 // (the instruction cache is shared by all CTAs of the SM).
-template <bool GAUSS, int Z, bool WIDE>
+template <bool GAUSS, int Z, bool WIDE, bool DIL>
 __device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
 {
     const int npass = (P.R + 15) >> 4;          // 16-bit passes per colour
     for (int it = 0; it < 2 * npass; ++it) {
         const int color = it >= npass;
         const int pass = it - color * npass;
-        sweep_pass<GAUSS, Z, WIDE>(P, S, t, inst, pass >> 1, color, pass & 1);
+        sweep_pass<GAUSS, Z, WIDE, DIL>(P, S, t, inst, pass >> 1, color, pass & 1);
         if (pass == npass - 1) __syncthreads();
     }
 }
@@ -417,7 +474,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
                     acc[j] += ((sw >> b) & 1u) ? h : -h;       // e = -s_p h_p
                 }
             } else {
-                uint32_t c0 = 0, c1 = 0, c2 = 0;
+                uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
                 const uint32_t jb = S.Jb[p];
 #pragma unroll
                 for (int d = 0; d < Z; ++d) {
@@ -426,12 +483,19 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
                     c0 ^= u;
                     const uint32_t t1 = c1 & t0;
                     c1 ^= t0;
-                    c2 |= t1;
+                    if constexpr (Z > 7) {
+                        const uint32_t t2 = c2 & t1;
+                        c2 ^= t1;
+                        c3 |= t2;
+                    } else {
+                        c2 |= t1;
+                    }
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int b = 2 * j;
-                    acc[j] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                    acc[j] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2) |
+                                    (((c3 >> b) & 1u) << 3));
                 }
             }
         }
@@ -666,7 +730,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         if (S.icm_seed[k] < 0) continue;
         ET ea = ET(0);
         for (int w = 0; w < nwarps; ++w) ea += ((const ET *)S.Epart)[w * 32 + k];
-        if constexpr (!GAUSS) ea = 2 * ea - P.Nb;            // E = 2 U - N_b
+        if constexpr (!GAUSS) ea = 2 * ea - S.nb;            // E = 2 U - N_b (bonds present)
         E[2 * k] = ea;
         E[2 * k + 1] = esum[k] - ea;
         if (trace) {
@@ -830,7 +894,11 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
 // shared memory): spins and couplings are updated in place in global memory,
 // the neighbour table is read from global memory, and the cluster words and
 // overlap masks use a per-CTA global scratch; the arithmetic is the same.
-template <bool GAUSS, int Z, bool WIDE>
+// DIL = true (some instance of the batch has absent bonds): the neighbour
+// table and degrees are per instance (absent bonds point at the site itself,
+// like padding) and a diluted instance takes the probability-1/2 rule for
+// zero-energy proposals.
+template <bool GAUSS, int Z, bool WIDE, bool DIL>
 __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
@@ -845,15 +913,18 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
         S.zdeg = const_cast<uint8_t *>(P.zdeg);
         S.C = P.scratch + (size_t)blockIdx.x * P.scratch_words;
         S.mask = S.C + 2 * N;
-    } else {
+    } else if constexpr (!DIL) {
         for (int i = tid; i < N * Z; i += nth) S.nbr[i] = P.nbr[i];
         if (!GAUSS && !P.const_z)
             for (int i = tid; i < N; i += nth) S.zdeg[i] = P.zdeg[i];
     }
+    S.tie = 0;
+    S.nb = P.Nb;
     if constexpr (GAUSS) {
         for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
     } else {
-        for (int i = tid; i < 32 * G * 8; i += nth) S.thr[i] = i < R * 8 ? P.thr_metro[i] : 0u;
+        constexpr int TS = thr_stride(Z);
+        for (int i = tid; i < 32 * G * TS; i += nth) S.thr[i] = i < R * TS ? P.thr_metro[i] : 0u;
     }
     if (tid < 32) {
         S.cnt_n[tid] = 0;
@@ -862,6 +933,21 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
 
     for (int slot = blockIdx.x; slot < P.n_inst; slot += gridDim.x) {
         if (P.active && !P.active[slot]) continue;   // free slot of a serving batch
+        if constexpr (DIL) {
+            const uint16_t *nb_src = P.nbr_inst + (size_t)slot * N * Z;
+            const uint8_t *zd_src = P.zdeg_inst + (size_t)slot * N;
+            if constexpr (WIDE) {
+                S.nbr = const_cast<uint16_t *>(nb_src);
+                S.zdeg = const_cast<uint8_t *>(zd_src);
+            } else {
+                const uint32_t *src = (const uint32_t *)nb_src;     // N Z even: whole 32-bit pairs
+                uint32_t *dst = (uint32_t *)S.nbr;
+                for (int i = tid; i < (N * Z) / 2; i += nth) dst[i] = src[i];
+                for (int i = tid; i < N; i += nth) S.zdeg[i] = zd_src[i];
+            }
+            S.nb = P.nb_inst[slot];
+            S.tie = S.nb < P.Nb;
+        }
         if constexpr (WIDE) {
             S.s = P.spins + (size_t)slot * G * N;
             S.Jd = const_cast<float *>(P.Jd) + (size_t)slot * N * Z;
@@ -909,7 +995,7 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
                 __syncthreads();
             }
             if (P.enable_metropolis) {  // step 1
-                metropolis_sweep<GAUSS, Z, WIDE>(P, S, t, inst);
+                metropolis_sweep<GAUSS, Z, WIDE, DIL>(P, S, t, inst);
                 for (int r = tid; r < R; r += nth) {
                     ET e = ET(0);
                     for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + r];
@@ -954,18 +1040,19 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
     PHASE_FLUSH();
 }
 
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 __global__ void __launch_bounds__(kMaxThreads, 7) fused_kernel(const KParams P, uint32_t n_sweeps)
 {
-    fused_body<GAUSS, Z, false>(P, n_sweeps);
+    fused_body<GAUSS, Z, false, DIL>(P, n_sweeps);
 }
 
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 __global__ void __launch_bounds__(kMaxThreadsWide, 1) fused_wide_kernel(const KParams P, uint32_t n_sweeps)
 {
-    fused_body<GAUSS, Z, true>(P, n_sweeps);
+    fused_body<GAUSS, Z, true, DIL>(P, n_sweeps);
 }
 
+#if ICM_PART == 0
 // ---------------------------------------------------------------------------
 // Layout kernels (run at load/read time, not per sweep).
 __global__ void pack_spins_kernel(const int8_t *__restrict__ src, uint32_t *__restrict__ dst,
@@ -1026,6 +1113,36 @@ __global__ void expand_couplings_kernel(const void *__restrict__ bondJ, int gaus
     }
 }
 
+// Per-instance tables of a diluted batch (see launch_expand_dilution).  A
+// bond is absent when its coupling is exactly 0; each bond present is counted
+// once, at the endpoint with the smaller position.
+__global__ void expand_dilution_kernel(const void *__restrict__ bondJ, int gauss, const int32_t *__restrict__ edge_bond,
+                                       const uint16_t *__restrict__ nbr, int n_inst, int N, int Z, int Nb,
+                                       uint16_t *__restrict__ nbr_inst, uint8_t *__restrict__ zdeg_inst,
+                                       int32_t *__restrict__ nb_inst)
+{
+    const size_t total = (size_t)n_inst * N;
+    for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (size_t)gridDim.x * blockDim.x) {
+        const int p = (int)(idx % N);
+        const size_t inst = idx / N;
+        int deg = 0, once = 0;
+        for (int d = 0; d < Z; ++d) {
+            const int b = edge_bond[p * Z + d];
+            bool present = false;
+            if (b >= 0)
+                present = gauss ? ((const float *)bondJ)[inst * Nb + b] != 0.f
+                                : ((const int8_t *)bondJ)[inst * Nb + b] != 0;
+            const int q = nbr[p * Z + d];
+            nbr_inst[idx * Z + d] = (uint16_t)(present ? q : p);
+            deg += present;
+            once += present && p < q;
+        }
+        zdeg_inst[idx] = (uint8_t)deg;
+        if (once) atomicAdd(&nb_inst[inst], once);
+    }
+}
+
 // Energies of every replica from the spins: E = -sum over colour-1 sites of
 // s_i h_i (every bond joins the two colours).  One CTA per instance.
 template <bool GAUSS, int Z>
@@ -1036,6 +1153,7 @@ __global__ void init_energies_kernel(const KParams P)
     const int N = P.N, half = P.half;
     for (int slot = blockIdx.x; slot < P.n_inst; slot += gridDim.x) {
         const uint32_t *s = P.spins + (size_t)slot * P.G * N;
+        const uint16_t *nbr = P.diluted ? P.nbr_inst + (size_t)slot * N * Z : P.nbr;   // absent bonds: self
         for (int r = 0; r < P.R; ++r) {
             const uint32_t *sg = s + (r >> 5) * N;
             const int b = r & 31;
@@ -1043,7 +1161,7 @@ __global__ void init_energies_kernel(const KParams P)
             for (int p = half + threadIdx.x; p < N; p += blockDim.x) {
                 const int si = ((sg[p] >> b) & 1u) ? -1 : 1;
                 for (int d = 0; d < Z; ++d) {
-                    const int q = P.nbr[p * Z + d];
+                    const int q = nbr[p * Z + d];
                     const int sj = ((sg[q] >> b) & 1u) ? -1 : 1;
                     if constexpr (GAUSS) {
                         acc -= P.Jd[((size_t)slot * N + p) * Z + d] * (float)(si * sj);
@@ -1075,6 +1193,8 @@ __global__ void energies_to_double_kernel(const float *Ef, const int32_t *Ei, in
         out[i] = gauss ? (double)Ef[i] : (double)Ei[i];
 }
 
+#endif  // ICM_PART == 0
+
 inline int grid_for(size_t n, int threads)
 {
     size_t g = (n + threads - 1) / threads;
@@ -1082,12 +1202,13 @@ inline int grid_for(size_t n, int threads)
     return g > 0 ? (int)g : 1;
 }
 
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 cudaError_t launch_fused_t(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
 {
     if (P.wide && (threads > kMaxThreadsWide || !P.scratch)) return cudaErrorInvalidValue;
     if (!P.wide && threads > kMaxThreads) return cudaErrorInvalidValue;
-    auto kern = P.wide ? fused_wide_kernel<GAUSS, Z> : fused_kernel<GAUSS, Z>;
+    if (DIL && (!P.nbr_inst || !P.zdeg_inst || !P.nb_inst)) return cudaErrorInvalidValue;
+    auto kern = P.wide ? fused_wide_kernel<GAUSS, Z, DIL> : fused_kernel<GAUSS, Z, DIL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.sm.total);
     if (e != cudaSuccess) return e;
     kern<<<grid, threads, P.sm.total, st>>>(P, n_sweeps);
@@ -1097,7 +1218,8 @@ cudaError_t launch_fused_t(const KParams &P, int threads, int grid, uint32_t n_s
 template <bool GAUSS, int Z>
 cudaError_t occupancy_t(bool wide, int threads, int smem, int *ctas)
 {
-    auto kern = wide ? fused_wide_kernel<GAUSS, Z> : fused_kernel<GAUSS, Z>;
+    // the diluted variants have the same register budget (launch bounds) and layout
+    auto kern = wide ? fused_wide_kernel<GAUSS, Z, false> : fused_kernel<GAUSS, Z, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, kern, threads, smem);
@@ -1105,6 +1227,7 @@ cudaError_t occupancy_t(bool wide, int threads, int smem, int *ctas)
 
 }  // namespace
 
+#if ICM_PART == 0
 // ---------------------------------------------------------------------------
 static int align_up(int v, int a) { return (v + a - 1) / a * a; }
 
@@ -1126,7 +1249,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.zdeg = take(in_smem * N, 16);
     L.E = take(R * 4, 16);
     L.Epart = take(nwarps * (R > 32 ? R : 32) * 4, 16);
-    L.rtab = take(gauss ? G * 32 * 4 : G * 32 * 8 * 4, 16);   // every bit of the G words
+    L.rtab = take(gauss ? G * 32 * 4 : G * 32 * thr_stride(Z) * 4, 16);   // every bit of the G words
     L.icm_mask = take(in_smem * n_icm * NW * 4, 16);
     L.icm_C = take(in_smem * 2 * N * 4, 16);
     L.swap_x = take(2 * 32 * 4, 16);
@@ -1171,18 +1294,12 @@ int wide_scratch_words(int N)
 
 cudaError_t fused_occupancy(bool gauss, int Z, bool wide, int threads, int smem, int *ctas)
 {
-    if (gauss)
-        return Z == 4 ? occupancy_t<true, 4>(wide, threads, smem, ctas) : occupancy_t<true, 6>(wide, threads, smem, ctas);
-    return Z == 4 ? occupancy_t<false, 4>(wide, threads, smem, ctas) : occupancy_t<false, 6>(wide, threads, smem, ctas);
+    return gauss ? fused_occupancy_gauss(Z, wide, threads, smem, ctas) : fused_occupancy_pmj(Z, wide, threads, smem, ctas);
 }
 
 cudaError_t launch_fused(const KParams &P, bool gauss, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
 {
-    if (gauss)
-        return P.Z == 4 ? launch_fused_t<true, 4>(P, threads, grid, n_sweeps, st)
-                        : launch_fused_t<true, 6>(P, threads, grid, n_sweeps, st);
-    return P.Z == 4 ? launch_fused_t<false, 4>(P, threads, grid, n_sweeps, st)
-                    : launch_fused_t<false, 6>(P, threads, grid, n_sweeps, st);
+    return gauss ? launch_fused_gauss(P, threads, grid, n_sweeps, st) : launch_fused_pmj(P, threads, grid, n_sweeps, st);
 }
 
 cudaError_t launch_pack_spins(const int8_t *src, uint32_t *dst, const uint16_t *pos2site, int n_inst, int R, int G,
@@ -1207,15 +1324,34 @@ cudaError_t launch_expand_couplings(const void *bond_J, bool gauss, const int32_
     return cudaGetLastError();
 }
 
+cudaError_t launch_expand_dilution(const void *bond_J, bool gauss, const int32_t *edge_bond, const uint16_t *nbr,
+                                   int n_inst, int N, int Z, int Nb, uint16_t *nbr_inst, uint8_t *zdeg_inst,
+                                   int32_t *nb_inst, cudaStream_t st)
+{
+    expand_dilution_kernel<<<grid_for((size_t)n_inst * N, 256), 256, 0, st>>>(bond_J, gauss ? 1 : 0, edge_bond, nbr,
+                                                                               n_inst, N, Z, Nb, nbr_inst,
+                                                                               zdeg_inst, nb_inst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init_energies(const KParams &P, bool gauss, cudaStream_t st)
 {
     const int grid = P.n_inst < 152 * 8 ? P.n_inst : 152 * 8;
-    if (gauss) {
-        if (P.Z == 4) init_energies_kernel<true, 4><<<grid, kMaxThreads, 0, st>>>(P);
-        else init_energies_kernel<true, 6><<<grid, kMaxThreads, 0, st>>>(P);
-    } else {
-        if (P.Z == 4) init_energies_kernel<false, 4><<<grid, kMaxThreads, 0, st>>>(P);
+    switch (P.Z) {
+    case 4:
+        if (gauss) init_energies_kernel<true, 4><<<grid, kMaxThreads, 0, st>>>(P);
+        else init_energies_kernel<false, 4><<<grid, kMaxThreads, 0, st>>>(P);
+        break;
+    case 6:
+        if (gauss) init_energies_kernel<true, 6><<<grid, kMaxThreads, 0, st>>>(P);
         else init_energies_kernel<false, 6><<<grid, kMaxThreads, 0, st>>>(P);
+        break;
+    case 8:
+        if (gauss) init_energies_kernel<true, 8><<<grid, kMaxThreads, 0, st>>>(P);
+        else init_energies_kernel<false, 8><<<grid, kMaxThreads, 0, st>>>(P);
+        break;
+    default:
+        return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
 }
@@ -1227,18 +1363,91 @@ cudaError_t launch_energies_to_double(const KParams &P, bool gauss, double *out,
     return cudaGetLastError();
 }
 
-}  // namespace icm
+#else  // ICM_PART 1 or 2: the fused kernels of one disorder kind
 
-#ifdef ICM_PHASE_TIMERS
-// Cycles per phase summed over CTAs: 0 sweep + energies, 1 ICM, 2 PT, 3 observables,
-// 4 between the last step and the store, 5 load/store and instance changes.
-extern "C" int icm_debug_phase_cycles(unsigned long long *out, int reset)
+namespace {
+constexpr bool kPartGauss = ICM_PART == 2;
+
+template <bool DIL>
+cudaError_t launch_fused_z(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
 {
+    switch (P.Z) {
+    case 4: return launch_fused_t<kPartGauss, 4, DIL>(P, threads, grid, n_sweeps, st);
+    case 6: return launch_fused_t<kPartGauss, 6, DIL>(P, threads, grid, n_sweeps, st);
+    case 8: return launch_fused_t<kPartGauss, 8, DIL>(P, threads, grid, n_sweeps, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_part(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
+{
+    return P.diluted ? launch_fused_z<true>(P, threads, grid, n_sweeps, st)
+                     : launch_fused_z<false>(P, threads, grid, n_sweeps, st);
+}
+
+cudaError_t occupancy_part(int Z, bool wide, int threads, int smem, int *ctas)
+{
+    switch (Z) {
+    case 4: return occupancy_t<kPartGauss, 4>(wide, threads, smem, ctas);
+    case 6: return occupancy_t<kPartGauss, 6>(wide, threads, smem, ctas);
+    case 8: return occupancy_t<kPartGauss, 8>(wide, threads, smem, ctas);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int phase_cycles_part(unsigned long long *out, int reset)
+{
+#ifdef ICM_PHASE_TIMERS
     if (cudaMemcpyFromSymbol(out, g_icm_phase_cycles, sizeof(unsigned long long) * 16) != cudaSuccess) return -4;
     if (reset) {
         unsigned long long z[16] = {};
         if (cudaMemcpyToSymbol(g_icm_phase_cycles, z, sizeof(z)) != cudaSuccess) return -4;
     }
+    return 0;
+#else
+    (void)out;
+    (void)reset;
+    return -7;
+#endif
+}
+}  // namespace
+
+#if ICM_PART == 1
+cudaError_t launch_fused_pmj(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
+{
+    return launch_part(P, threads, grid, n_sweeps, st);
+}
+cudaError_t fused_occupancy_pmj(int Z, bool wide, int threads, int smem, int *ctas)
+{
+    return occupancy_part(Z, wide, threads, smem, ctas);
+}
+int debug_phase_cycles_pmj(unsigned long long *out, int reset) { return phase_cycles_part(out, reset); }
+#else
+cudaError_t launch_fused_gauss(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
+{
+    return launch_part(P, threads, grid, n_sweeps, st);
+}
+cudaError_t fused_occupancy_gauss(int Z, bool wide, int threads, int smem, int *ctas)
+{
+    return occupancy_part(Z, wide, threads, smem, ctas);
+}
+int debug_phase_cycles_gauss(unsigned long long *out, int reset) { return phase_cycles_part(out, reset); }
+#endif
+
+#endif  // ICM_PART
+}  // namespace icm
+
+#if ICM_PART == 0 && defined(ICM_PHASE_TIMERS)
+// Cycles per phase summed over CTAs and over both fused-kernel parts: 0 sweep +
+// energies, 1 ICM, 2 PT, 3 observables, 4 between the last step and the
+// store, 5 load/store and instance changes.
+extern "C" int icm_debug_phase_cycles(unsigned long long *out, int reset)
+{
+    unsigned long long a[16], b[16];
+    int rc = icm::debug_phase_cycles_pmj(a, reset);
+    if (!rc) rc = icm::debug_phase_cycles_gauss(b, reset);
+    if (rc) return rc;
+    for (int i = 0; i < 16; ++i) out[i] = a[i] + b[i];
     return 0;
 }
 #endif

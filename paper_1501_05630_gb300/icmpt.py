@@ -15,7 +15,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .inputs import CHIMERA, CUBIC3D, GAUSS, PM_J, SQUARE2D  # noqa: F401  (re-exported constants)
+from .inputs import CHIMERA, CUBIC3D, GAUSS, HYPERCUBIC4D, PM_J, SQUARE2D  # noqa: F401  (re-exported constants)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libicmpt.so")
@@ -46,6 +46,7 @@ EXPORTS = [
     "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
+    "icm_read_bond_counts",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
@@ -90,6 +91,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_read_energies.argtypes = [vp, vp, u32]
         L.icm_read_sweeps.argtypes = [vp, vp, u32]
         L.icm_read_observables.argtypes = [vp] + [vp] * 7 + [u32]
+        L.icm_read_bond_counts.argtypes = [vp, vp]
         L.icm_clear_observables.argtypes = [vp]
         L.icm_read_trace.argtypes = [vp] + [vp] * 7 + [u32]
         L.icm_batch_info.argtypes = [vp] + [vp] * 5
@@ -242,6 +244,7 @@ class Observables:
     acc_d: np.ndarray
     hist: np.ndarray
     n_meas: np.ndarray
+    nb: np.ndarray | None = None      # bonds present per instance (the q_l normalisation)
 
 
 class Batch:
@@ -358,7 +361,14 @@ class Batch:
         self.ctx.check(self._lib.icm_read_observables(
             self._h, o.accE.ctypes.data, o.acc_n.ctypes.data, o.acc_q2.ctypes.data, o.acc_pmin.ctypes.data,
             o.acc_d.ctypes.data, o.hist.ctypes.data if hist else None, o.n_meas.ctypes.data, 0))
+        o.nb = self.bond_counts()
         return o
+
+    def bond_counts(self) -> np.ndarray:
+        """Bonds present (coupling != 0) per instance; N_b unless diluted."""
+        out = np.empty(self.n_inst, dtype=np.int32)
+        self.ctx.check(self._lib.icm_read_bond_counts(self._h, out.ctypes.data))
+        return out
 
     def read_trace(self) -> dict:
         n, nT = self.n_inst, self.nT

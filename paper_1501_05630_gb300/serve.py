@@ -80,7 +80,10 @@ class _Class:
         self.stream = torch.cuda.Stream()
         self.ctx = icmpt.Context(ctx_dev, self.stream.cuda_stream)
         self.N, self.Nb = icmpt.lattice_size(req.lattice, req.L)
-        dummy = np.zeros((capacity, self.Nb), dtype=req.couplings.dtype)
+        # placeholder couplings of the free slots: all bonds present (a zero
+        # coupling is an absent bond, which would switch the batch to its
+        # diluted kernels)
+        dummy = np.ones((capacity, self.Nb), dtype=req.couplings.dtype)
         self.batch = icmpt.Batch(self.ctx, req.lattice, req.L, req.disorder, dummy, req.T, req.T_icm, req.seed)
         self.batch.set_active(-1, False)
         self.free = list(range(capacity))[::-1]
@@ -100,7 +103,7 @@ def slot_bytes(r: Request) -> int:
     N, Nb = icmpt.lattice_size(r.lattice, r.L)
     nT = len(r.T)
     R = 2 * nT
-    Z = 4 if r.lattice == icmpt.SQUARE2D else 6
+    Z = {icmpt.SQUARE2D: 4, icmpt.HYPERCUBIC4D: 8}.get(r.lattice, 6)
     G = (R + 31) // 32
     return (N * Z * 4 + G * N * 4 + R * N + Nb * 4 + nT * (N + 1) * 8 + 8 * nT * 8 + R * 16 + 64)
 
@@ -212,8 +215,9 @@ class Server:
         st = c.slots[slot]
         m = int(obs.n_meas[slot])
         e = obs.accE[slot, 0] / (2.0 * c.N * m)
-        ql = 1.0 - 2.0 * obs.acc_d[slot, 0] / (c.Nb * m)
-        done = icmpt.therm_update(st.state, self.crit, e, ql, c.T_min, c.Nb / c.N)
+        nb = int(obs.nb[slot]) if obs.nb is not None else c.Nb     # bonds present (dilution)
+        ql = 1.0 - 2.0 * obs.acc_d[slot, 0] / (max(nb, 1) * m)
+        done = icmpt.therm_update(st.state, self.crit, e, ql, c.T_min, nb / c.N)
         if done or st.t >= self.max_sweeps:
             self.results[st.ticket] = Result(st.ticket, "thermalized" if done else "not_thermalized", st.t,
                                              st.req.arrival, self.clock(), e, ql, st.state.delta,
