@@ -324,6 +324,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
                     philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+                    uint32_t f8 = 0u;                           // this group's accepted bits
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;               // compile-time bit of the pass
@@ -343,10 +344,11 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                         } else {
                             a = (sh <= 0.f) || (xr < thr);
                         }
-                        flip |= (uint32_t)a << b;
+                        f8 |= (uint32_t)a << i;
                         acc[b] -= sh;                           // e = -s'h: -sh, or +sh after a flip
                         if (a) acc[b] += 2.f * sh;
                     }
+                    flip |= f8 << (8 * qq);
                 }
             }
         } else {
@@ -608,9 +610,12 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     uint2 *C2 = (uint2 *)S.C;
     int rounds = 0;
     if (N <= 4 * nth) {
-        // each thread owns sites tid + j nth (j < 4) and keeps their
-        // neighbour positions in registers across rounds
+        // each thread owns sites tid + j nth (j < 4) and keeps, across rounds,
+        // their neighbour positions, their domain words (the q = -1 bits of
+        // the moving pairs, fixed during the growth) and their own cluster
+        // words (written only by this thread) in registers
         uint32_t qn[4][Z / 2];                 // neighbour positions, two per register
+        uint32_t dm0[4], dm1[4], cw0[4], cw1[4];
         uint32_t todo = 0u;                    // bit j: site j not yet absorbed
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -619,6 +624,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             const uint32_t *row = (const uint32_t *)(S.nbr + (ok ? p : 0) * Z);
 #pragma unroll
             for (int i = 0; i < Z / 2; ++i) qn[j][i] = row[i];
+            dm0[j] = dm1[j] = cw0[j] = cw1[j] = 0u;
             if (ok) {
                 const uint32_t w0 = S.s[p] ^ f0;             // step 2a
                 S.s[p] = w0;
@@ -628,7 +634,11 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                     S.s[N + p] = w1;
                 }
                 const uint2 c = C2[p];
-                if (((w0 ^ (w0 >> 1)) & act0) != c.x || ((w1 ^ (w1 >> 1)) & act1) != c.y) todo |= 1u << j;
+                dm0[j] = (w0 ^ (w0 >> 1)) & act0;
+                dm1[j] = (w1 ^ (w1 >> 1)) & act1;
+                cw0[j] = c.x;
+                cw1[j] = c.y;
+                if (dm0[j] != c.x || dm1[j] != c.y) todo |= 1u << j;
             }
         }
         if (act0 | act1) {
@@ -638,9 +648,6 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (!((todo >> j) & 1u)) continue;
-                    const int p = tid + j * nth;
-                    const uint32_t w0 = S.s[p], w1 = G > 1 ? S.s[N + p] : 0u;
-                    const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
                     uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
                     for (int i = 0; i < Z / 2; ++i) {
@@ -648,12 +655,13 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                         nb0 |= a.x | b.x;
                         nb1 |= a.y | b.y;
                     }
-                    const uint2 c = C2[p];                    // written only by this thread
-                    const uint32_t n0 = c.x | (d0 & nb0), n1 = c.y | (d1 & nb1);
-                    if (n0 != c.x || n1 != c.y) {
-                        C2[p] = make_uint2(n0, n1);
+                    const uint32_t n0 = cw0[j] | (dm0[j] & nb0), n1 = cw1[j] | (dm1[j] & nb1);
+                    if (n0 != cw0[j] || n1 != cw1[j]) {
+                        C2[tid + j * nth] = make_uint2(n0, n1);
+                        cw0[j] = n0;
+                        cw1[j] = n1;
                         grew = 1;
-                        if (n0 == d0 && n1 == d1) todo &= ~(1u << j);
+                        if (n0 == dm0[j] && n1 == dm1[j]) todo &= ~(1u << j);
                     }
                 }
                 ++rounds;
@@ -663,9 +671,8 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             for (int j = 0; j < 4; ++j) {
                 const int p = tid + j * nth;
                 if (p < N) {
-                    const uint2 c = C2[p];
-                    if (c.x) S.s[p] ^= c.x | (c.x << 1);
-                    if (c.y) S.s[N + p] ^= c.y | (c.y << 1);
+                    if (cw0[j]) S.s[p] ^= cw0[j] | (cw0[j] << 1);
+                    if (cw1[j]) S.s[N + p] ^= cw1[j] | (cw1[j] << 1);
                 }
             }
         }
