@@ -256,6 +256,77 @@ typedef struct {
 icm_status icm_therm_update(icm_therm_state *st, const icm_therm_criterion *c, double e, double q_l,
                             double T_min, double bonds_per_site, int32_t *thermalized);
 
+/* ---------------------------------------------------------------- request server
+ * Continuous batching of whole runs: each request is one disorder instance
+ * (any lattice, size, disorder kind and ladder) to be run to the test above.
+ * Requests are grouped into shape classes -- (lattice, L, disorder, ladder,
+ * T_icm, seed) -- and each class is one slot-table batch on its own CUDA
+ * stream.  icm_server_step, without waiting on the device:
+ *   1. admits queued requests, first come first served, into free slots of
+ *      idle classes; a new class is created only while the summed size of
+ *      the class batches stays within the device-memory budget (otherwise
+ *      the request waits);
+ *   2. collects every class whose last launch has finished (icm_query),
+ *      advances its slots by `quantum` sweeps and tests each window that
+ *      ended ([Q, 2Q), [2Q, 4Q), ...): a slot that meets the criterion or
+ *      reaches max_sweeps finishes and is freed, the others start their next
+ *      window;
+ *   3. launches the next quantum of every idle class with active slots.
+ * Classes advance independently, so a class of large lattices does not hold
+ * back the small ones.  A request's trajectory depends only on its (seed,
+ * instance id) and its inputs, never on its slot or on the other requests.
+ * One host thread at a time per server.                                    */
+typedef struct icm_server icm_server;
+typedef struct {
+    int32_t slots_per_class;   /* slots of each class batch; default 64 */
+    int32_t quantum;           /* sweeps per launch, a power of two; default 64 */
+    uint32_t max_sweeps;       /* sweep cap of a request; default 65536 */
+    icm_therm_criterion crit;  /* default {0.005, 0.01, 2} */
+    uint64_t hbm_budget;       /* bytes of all class batches together; default 8 GiB */
+} icm_server_config;
+typedef struct {
+    int32_t lattice, L, disorder;
+    int32_t n_T;
+    const double *T;           /* [n_T], strictly ascending, > 0 */
+    double T_icm;
+    uint64_t seed;
+    uint32_t instance_id;      /* < 2^24 */
+    const void *couplings;     /* host [N_b] in bond order, int8 or float32 (copied) */
+    const int8_t *spins;       /* host [2 n_T][N] +-1, or NULL = all +1 (copied) */
+} icm_request;
+typedef struct {
+    int32_t status;            /* ICM_PENDING (queued or running) or ICM_OK (finished) */
+    int32_t thermalized;       /* 1: met the criterion; 0: stopped at max_sweeps */
+    uint32_t sweeps;           /* sweeps run */
+    int32_t slot;              /* slot in its class batch, -1 before admission */
+    double e, q_l, delta;      /* last window at T_min: energy per spin, link overlap, E(q_l) - e */
+    double accE;               /* last window's raw sums at T_min */
+    int64_t acc_d, n_meas;
+    double t_submit, t_admit, t_done;   /* seconds of the host's monotonic clock */
+} icm_result;
+
+/* cfg NULL = the defaults above. */
+icm_status icm_server_create(int32_t device, const icm_server_config *cfg, icm_server **out);
+/* Frees every class batch and stream (waits for running launches). */
+icm_status icm_server_destroy(icm_server *s);
+const char *icm_server_last_error(const icm_server *s);
+/* Queue a request (its arrays are copied).  ICM_ERR_BUDGET: its class alone
+ * exceeds the memory budget; ICM_ERR_ARG: invalid request.                 */
+icm_status icm_server_submit(icm_server *s, const icm_request *r, uint64_t *ticket);
+/* One pass of admit / collect / launch (never blocks on the device).
+ * finished: requests completed in this pass; launched: kernel launches made. */
+icm_status icm_server_step(icm_server *s, int32_t *finished, int32_t *launched);
+/* State of a ticket; ICM_ERR_ARG for an unknown ticket. */
+icm_status icm_server_poll(const icm_server *s, uint64_t ticket, icm_result *out);
+/* Requests queued, requests in slots, classes created. */
+icm_status icm_server_status(const icm_server *s, int32_t *queued, int32_t *active, int32_t *classes);
+/* Class i (creation order): lattice, L, disorder, n_T, CTA width of its
+ * batch, slots in use. */
+icm_status icm_server_class_info(const icm_server *s, int32_t i, int32_t *lattice, int32_t *L, int32_t *disorder,
+                                 int32_t *n_T, int32_t *threads, int32_t *active);
+/* The server's clock (seconds, the host's monotonic clock). */
+double icm_server_clock(void);
+
 /* Eq. 2 over the batch: the mean over measured (active) instances of
  * E(q_l) - e at temperature position k from the current accumulators, with
  * its standard error over instances.                                      */

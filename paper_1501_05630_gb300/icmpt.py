@@ -46,7 +46,9 @@ EXPORTS = [
     "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
-    "icm_read_bond_counts",
+    "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
+    "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
+    "icm_server_clock",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
@@ -61,6 +63,26 @@ class ThermState(ctypes.Structure):
 
 class ThermCriterion(ctypes.Structure):
     _fields_ = [("eps_e", ctypes.c_double), ("eps_ql", ctypes.c_double), ("need", ctypes.c_int32)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("slots_per_class", ctypes.c_int32), ("quantum", ctypes.c_int32), ("max_sweeps", ctypes.c_uint32),
+                ("crit", ThermCriterion), ("hbm_budget", ctypes.c_uint64)]
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_int32), ("L", ctypes.c_int32), ("disorder", ctypes.c_int32),
+                ("n_T", ctypes.c_int32), ("T", ctypes.c_void_p), ("T_icm", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("instance_id", ctypes.c_uint32), ("couplings", ctypes.c_void_p),
+                ("spins", ctypes.c_void_p)]
+
+
+class ServerResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("thermalized", ctypes.c_int32), ("sweeps", ctypes.c_uint32),
+                ("slot", ctypes.c_int32), ("e", ctypes.c_double), ("q_l", ctypes.c_double),
+                ("delta", ctypes.c_double), ("accE", ctypes.c_double), ("acc_d", ctypes.c_int64),
+                ("n_meas", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
 
 
 def load_library(path: str = LIB_PATH):
@@ -92,6 +114,17 @@ def load_library(path: str = LIB_PATH):
         L.icm_read_sweeps.argtypes = [vp, vp, u32]
         L.icm_read_observables.argtypes = [vp] + [vp] * 7 + [u32]
         L.icm_read_bond_counts.argtypes = [vp, vp]
+        L.icm_server_create.argtypes = [i32, ctypes.POINTER(ServerConfig), ctypes.POINTER(vp)]
+        L.icm_server_destroy.argtypes = [vp]
+        L.icm_server_last_error.argtypes = [vp]
+        L.icm_server_last_error.restype = ctypes.c_char_p
+        L.icm_server_submit.argtypes = [vp, ctypes.POINTER(_Request), ctypes.POINTER(u64)]
+        L.icm_server_step.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.icm_server_poll.argtypes = [vp, u64, ctypes.POINTER(ServerResult)]
+        L.icm_server_status.argtypes = [vp] + [ctypes.POINTER(i32)] * 3
+        L.icm_server_class_info.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 6
+        L.icm_server_clock.argtypes = []
+        L.icm_server_clock.restype = ctypes.c_double
         L.icm_clear_observables.argtypes = [vp]
         L.icm_read_trace.argtypes = [vp] + [vp] * 7 + [u32]
         L.icm_batch_info.argtypes = [vp] + [vp] * 5
@@ -114,7 +147,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
         L.icm_load.argtypes = [vp, vp, ctypes.c_size_t]
         for name in EXPORTS:
-            if name != "icm_last_error":
+            if name not in ("icm_last_error", "icm_server_last_error", "icm_server_clock"):
                 getattr(L, name).restype = i32
         _ = i64
         _lib = L

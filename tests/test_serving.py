@@ -36,6 +36,37 @@ def test_therm_update_stability_and_eq1(lib):
         icmpt.therm_update(st, cr, 0, 0, 0.0, 3.0)
 
 
+def test_native_server_host_logic(lib):
+    """Request validation, rejection by the memory budget and the queue, on
+    the host (no class is created before the first step)."""
+    icmpt = lib
+    from paper_1501_05630_gb300.serve import Request, Server
+    N, Nb = icmpt.lattice_size(I.SQUARE2D, 8)
+    T = I.ladder(0.3, 1.5, 8)
+    ok = Request(I.SQUARE2D, 8, I.PM_J, T, 1.0, 1, 7, I.couplings(Nb, I.PM_J, 1, [7])[0])
+    srv = Server(slots_per_class=4, quantum=16, hbm_budget=8 << 20)
+    t = srv.submit(ok)
+    assert srv.poll(t) is None                              # pending
+    assert srv.status() == (1, 0, 0)
+    with pytest.raises(icmpt.IcmError) as e:                 # descending ladder
+        srv.submit(Request(I.SQUARE2D, 8, I.PM_J, T[::-1].copy(), 1.0, 1, 8, ok.couplings))
+    assert e.value.code == -1
+    with pytest.raises(icmpt.IcmError) as e:                 # instance id beyond the RNG key
+        srv.submit(Request(I.SQUARE2D, 8, I.PM_J, T, 1.0, 1, 1 << 24, ok.couplings))
+    assert e.value.code == -1
+    N2, Nb2 = icmpt.lattice_size(I.SQUARE2D, 128)
+    big = Request(I.SQUARE2D, 128, I.PM_J, I.ladder(0.2, 1.5, 32), 1.0, 1, 9, np.ones(Nb2, np.int8))
+    with pytest.raises(icmpt.IcmError) as e:                 # its class alone (21 MiB) exceeds 8 MiB
+        srv.submit(big)
+    assert e.value.code == -3
+    with pytest.raises(icmpt.IcmError):
+        srv.poll(12345)                                      # unknown ticket
+    assert srv.status() == (1, 0, 0)
+    srv.close()
+    with pytest.raises(ValueError):
+        Server(quantum=48)
+
+
 @pytest.fixture(scope="module")
 def gpu(lib):
     import torch
@@ -156,8 +187,9 @@ def test_server_mixes_wide_and_shared_memory_classes(gpu):
     srv.run_until_idle()
     res = [srv.poll(t) for t in tickets]
     assert all(r is not None for r in res)
-    wide = [c for c in srv.classes.values() if c.batch.info()["threads"] > 128]
-    assert len(wide) == 1
+    info = srv.class_info()
+    assert [c.L for c in info if c.threads > 128] == [128]     # the one wide class
+    assert all(c.active == 0 for c in info)
     for r, q in zip(res, reqs):
         a = icmpt.Batch(ctx, q.lattice, q.L, q.disorder, q.couplings[None].copy(), q.T, q.T_icm, q.seed,
                         spins=q.spins[None].copy(), instance_ids=[q.instance_id])
