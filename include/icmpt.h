@@ -60,7 +60,8 @@ typedef int32_t icm_status;
 #define ICM_ERR_TIMEOUT (-5)  /* a bounded device wait expired */
 #define ICM_ERR_STATE (-6)    /* call not valid in the current state */
 #define ICM_ERR_UNSUPPORTED (-7) /* size or feature beyond this build's limits */
-#define ICM_PENDING 1          /* icm_query: work still running (not an error) */
+#define ICM_PENDING 1          /* icm_query / server results: work still running (not an error) */
+#define ICM_CANCELLED 2        /* server results: the request was cancelled (not an error) */
 
 /* Lattice kinds ("Results in two and three space dimensions, as well as on
  * the nonplanar chimera topology").
@@ -295,7 +296,7 @@ typedef struct {
     const int8_t *spins;       /* host [2 n_T][N] +-1, or NULL = all +1 (copied) */
 } icm_request;
 typedef struct {
-    int32_t status;            /* ICM_PENDING (queued or running) or ICM_OK (finished) */
+    int32_t status;            /* ICM_PENDING (queued or running), ICM_OK (finished) or ICM_CANCELLED */
     int32_t thermalized;       /* 1: met the criterion; 0: stopped at max_sweeps */
     uint32_t sweeps;           /* sweeps run */
     int32_t slot;              /* slot in its class batch, -1 before admission */
@@ -318,6 +319,11 @@ icm_status icm_server_submit(icm_server *s, const icm_request *r, uint64_t *tick
 icm_status icm_server_step(icm_server *s, int32_t *finished, int32_t *launched);
 /* State of a ticket; ICM_ERR_ARG for an unknown ticket. */
 icm_status icm_server_poll(const icm_server *s, uint64_t ticket, icm_result *out);
+/* Cancel a request.  A queued request is dropped at once; a running one is
+ * released at its class's next collection (immediately when the class is
+ * idle); its result then has status ICM_CANCELLED and the sweeps it ran.
+ * ICM_ERR_STATE when the request has already finished or was cancelled. */
+icm_status icm_server_cancel(icm_server *s, uint64_t ticket);
 /* Requests queued, requests in slots, classes created. */
 icm_status icm_server_status(const icm_server *s, int32_t *queued, int32_t *active, int32_t *classes);
 /* Class i (creation order): lattice, L, disorder, n_T, CTA width of its

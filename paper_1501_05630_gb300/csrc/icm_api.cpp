@@ -215,6 +215,9 @@ struct icm_batch {
     // degree of the undiluted lattice when uniform (0: chimera)
     std::vector<int32_t> h_nb;
     int uniform_z = 0;
+    // invalid couplings per instance (not finite; +-J outside -1, 0, +1)
+    int32_t *d_bad = nullptr;         // [n_inst]
+    std::vector<int32_t> h_bad;
     // wide (global-resident) layout: per-CTA scratch, grown on demand (in allocs)
     uint32_t *scratch = nullptr;      // [scratch_ctas][wide_scratch_words(N)]
     int scratch_ctas = 0;
@@ -282,20 +285,29 @@ icm_status refresh_dilution(icm_batch *b, int first, int count)
     icm::KParams &P = b->kp;
     const size_t esz = b->gauss ? 4 : 1;
     int32_t *nb = const_cast<int32_t *>(P.nb_inst) + first;
+    int32_t *bad = b->d_bad + first;
     ICM_CUDA(ctx, cudaMemsetAsync(nb, 0, (size_t)count * sizeof(int32_t), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(bad, 0, (size_t)count * sizeof(int32_t), ctx->stream));
     ICM_CUDA(ctx, icm::launch_expand_dilution((const unsigned char *)b->raw_coup + (size_t)first * P.Nb * esz, b->gauss,
                                               b->edge_bond, P.nbr, count, P.N, P.Z, P.Nb,
                                               const_cast<uint16_t *>(P.nbr_inst) + (size_t)first * P.N * P.Z,
-                                              const_cast<uint8_t *>(P.zdeg_inst) + (size_t)first * P.N, nb,
+                                              const_cast<uint8_t *>(P.zdeg_inst) + (size_t)first * P.N, nb, bad,
                                               ctx->stream));
     b->h_nb.resize(b->n_inst, P.Nb);
+    b->h_bad.resize(b->n_inst, 0);
     ICM_CUDA(ctx, cudaMemcpyAsync(b->h_nb.data() + first, nb, (size_t)count * sizeof(int32_t), cudaMemcpyDeviceToHost,
                                   ctx->stream));
+    ICM_CUDA(ctx, cudaMemcpyAsync(b->h_bad.data() + first, bad, (size_t)count * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
     ICM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     bool diluted = false;
     for (int32_t v : b->h_nb) diluted |= v < P.Nb;
     P.diluted = diluted ? 1 : 0;
     P.const_z = diluted ? 0 : b->uniform_z;
+    long long n_bad = 0;
+    for (int i = first; i < first + count; ++i) n_bad += b->h_bad[i];
+    if (n_bad)
+        return fail(ctx, ICM_ERR_ARG, std::to_string(n_bad) + " invalid couplings (not finite, or +-J outside -1, 0, +1)");
     return ICM_OK;
 }
 
@@ -622,6 +634,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         (st = dalloc(b, &d_id, n_inst)) || (st = dalloc(b, &d_thr, (size_t)R * icm::thr_stride(Z))) ||
         (st = dalloc(b, &d_b2l, R)) || (st = dalloc(b, &d_nbr_inst, (size_t)n_inst * N * Z)) ||
         (st = dalloc(b, &d_zdeg_inst, (size_t)n_inst * N)) || (st = dalloc(b, &d_nb_inst, n_inst)) ||
+        (st = dalloc(b, &b->d_bad, n_inst)) ||
         (st = dalloc(b, &d_beta, n_T)) || (st = dalloc(b, &d_dbl, n_T - 1)) || (st = dalloc(b, &d_thrs, thr_swap.size())) ||
         (st = dalloc(b, &d_off, n_T - 1)) || (st = dalloc(b, &d_len, n_T - 1)) || (st = dalloc(b, &d_accE, nk)) ||
         (st = dalloc(b, &d_acc64, 4 * nk)) || (st = dalloc(b, &d_hist, nk * (N + 1))) ||
@@ -640,6 +653,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     P.tr_seed = d_trs; P.tr_csize = d_trc; P.tr_eb = d_treb; P.tr_ea = d_trea; P.tr_swap = d_trsw;
     P.nbr_inst = d_nbr_inst; P.zdeg_inst = d_zdeg_inst; P.nb_inst = d_nb_inst;
     b->h_nb.assign(n_inst, g.Nb);
+    b->h_bad.assign(n_inst, 0);
 
     std::vector<uint32_t> ids(n_inst);
     for (int i = 0; i < n_inst; ++i) {
@@ -723,6 +737,9 @@ icm_status icm_get_schedule(const icm_batch *b, icm_schedule *s)
 icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps)
 {
     if (!b) return ICM_ERR_ARG;
+    for (int i = 0; i < b->n_inst; ++i)
+        if (b->h_bad[i] && (b->h_active.empty() || b->h_active[i]))
+            return fail(b->ctx, ICM_ERR_STATE, "instance " + std::to_string(i) + " holds invalid couplings");
     if (n_sweeps == 0) return ICM_OK;
     icm::KParams &P = b->kp;
     P.icm_every = b->sched.icm_every;
@@ -881,7 +898,13 @@ icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings,
     float *Jd = b->gauss ? const_cast<float *>(P.Jd) + (size_t)slot * P.N * P.Z : nullptr;
     uint8_t *Jb = b->gauss ? nullptr : const_cast<uint8_t *>(P.Jb) + (size_t)slot * P.N;
     ICM_CUDA(ctx, icm::launch_expand_couplings(raw_c, b->gauss, b->edge_bond, 1, P.N, P.Z, P.Nb, Jd, Jb, ctx->stream));
-    if ((st = refresh_dilution(b, slot, 1))) return st;
+    if ((st = refresh_dilution(b, slot, 1))) {
+        if (!b->h_bad[slot]) return st;
+        // invalid couplings: the slot is freed so that the other slots keep running
+        b->h_active[slot] = 0;
+        if (set_slot_flags(b, slot) == ICM_OK) cudaStreamSynchronize(ctx->stream);
+        return st;
+    }
     uint32_t *sp = P.spins + (size_t)slot * P.G * P.N;
     if (spins) {
         int8_t *raw_s = b->raw_spins + (size_t)slot * P.R * P.N;

@@ -127,11 +127,12 @@ cudaError_t launch_unpack_spins(const uint32_t *src, int8_t *dst, const uint16_t
 cudaError_t launch_expand_couplings(const void *bond_J, bool gauss, const int32_t *edge_bond, int n_inst,
                                     int N, int Z, int Nb, float *Jd, uint8_t *Jb, cudaStream_t st);
 // Per-instance tables of a diluted batch from the bond couplings: neighbour
-// positions (absent bond -> the site itself), degree and bonds present.
-// nb_inst must be zero on entry (the kernel adds to it).
+// positions (absent bond -> the site itself), degree and bonds present, and
+// the number of invalid couplings (not finite; +-J outside -1, 0, +1) per
+// instance in bad.  nb_inst and bad must be zero on entry (the kernel adds).
 cudaError_t launch_expand_dilution(const void *bond_J, bool gauss, const int32_t *edge_bond, const uint16_t *nbr,
                                    int n_inst, int N, int Z, int Nb, uint16_t *nbr_inst, uint8_t *zdeg_inst,
-                                   int32_t *nb_inst, cudaStream_t st);
+                                   int32_t *nb_inst, int32_t *bad, cudaStream_t st);
 cudaError_t launch_init_energies(const KParams &P, bool gauss, cudaStream_t st);
 cudaError_t launch_energies_to_double(const KParams &P, bool gauss, double *out, cudaStream_t st);
 

@@ -35,6 +35,7 @@ struct Request {
 
 struct Slot {
     bool used = false;
+    bool cancel = false;     // release at the next collection
     uint64_t ticket = 0;
     uint32_t t = 0;          // sweeps run
     uint32_t boundary = 0;   // end of the current window
@@ -243,6 +244,22 @@ icm_status admit(icm_server *s)
     return st;
 }
 
+// Free a slot whose request was cancelled.
+icm_status release_cancelled(icm_server *s, ShapeClass *c, int slot)
+{
+    Slot &sl = c->slots[slot];
+    icm_result &res = s->results[sl.ticket];
+    res.status = ICM_CANCELLED;
+    res.sweeps = sl.t;
+    res.t_done = now_seconds();
+    const icm_status st = icm_batch_set_active(c->batch, slot, 0);
+    if (st != ICM_OK) return from_ctx(s, c->ctx, st, "slot release");
+    sl = Slot{};
+    c->free.push_back(slot);
+    c->active -= 1;
+    return ICM_OK;
+}
+
 // The window of `slot` ended: thermalization test at T_min, then finish the
 // request or start the next window [t, 2t).
 icm_status close_window(icm_server *s, ShapeClass *c, int slot, int *finished)
@@ -369,9 +386,14 @@ icm_status icm_server_step(icm_server *s, int32_t *finished, int32_t *launched)
             for (int slot : c->in_flight) {
                 Slot &sl = c->slots[slot];
                 sl.t += (uint32_t)s->cfg.quantum;
+                if (sl.cancel) {
+                    if ((st = release_cancelled(s, c, slot)) != ICM_OK) break;
+                    continue;
+                }
                 if (sl.t >= sl.boundary) due.push_back(slot);
             }
             c->in_flight.clear();
+            if (st != ICM_OK) break;
             if (!due.empty()) {
                 icm_status e = icm_read_observables(c->batch, c->accE.data(), nullptr, nullptr, nullptr,
                                                     c->acc_d.data(), nullptr, c->n_meas.data(), 0);
@@ -408,6 +430,30 @@ icm_status icm_server_poll(const icm_server *s, uint64_t ticket, icm_result *out
     if (it == s->results.end()) return ICM_ERR_ARG;
     *out = it->second;
     return ICM_OK;
+}
+
+icm_status icm_server_cancel(icm_server *s, uint64_t ticket)
+{
+    if (!s) return ICM_ERR_ARG;
+    auto it = s->results.find(ticket);
+    if (it == s->results.end()) return fail(s, ICM_ERR_ARG, "unknown ticket");
+    if (it->second.status != ICM_PENDING) return fail(s, ICM_ERR_STATE, "the request is no longer pending");
+    for (auto q = s->queue.begin(); q != s->queue.end(); ++q)
+        if (q->ticket == ticket) {
+            s->queue.erase(q);
+            it->second.status = ICM_CANCELLED;
+            it->second.t_done = now_seconds();
+            return ICM_OK;
+        }
+    for (ShapeClass *c : s->order)
+        for (int i = 0; i < (int)c->slots.size(); ++i) {
+            Slot &sl = c->slots[i];
+            if (!sl.used || sl.ticket != ticket) continue;
+            if (c->in_flight.empty()) return release_cancelled(s, c, i);
+            sl.cancel = true;               // released when the running launch is collected
+            return ICM_OK;
+        }
+    return fail(s, ICM_ERR_STATE, "request not found in the queue or a slot");
 }
 
 icm_status icm_server_status(const icm_server *s, int32_t *queued, int32_t *active, int32_t *classes)

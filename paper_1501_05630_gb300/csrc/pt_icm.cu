@@ -1122,24 +1122,33 @@ __global__ void expand_couplings_kernel(const void *__restrict__ bondJ, int gaus
 
 // Per-instance tables of a diluted batch (see launch_expand_dilution).  A
 // bond is absent when its coupling is exactly 0; each bond present is counted
-// once, at the endpoint with the smaller position.
+// once, at the endpoint with the smaller position.  Invalid couplings (not
+// finite, or +-J values other than -1, 0, +1) are counted per instance into bad.
 __global__ void expand_dilution_kernel(const void *__restrict__ bondJ, int gauss, const int32_t *__restrict__ edge_bond,
                                        const uint16_t *__restrict__ nbr, int n_inst, int N, int Z, int Nb,
                                        uint16_t *__restrict__ nbr_inst, uint8_t *__restrict__ zdeg_inst,
-                                       int32_t *__restrict__ nb_inst)
+                                       int32_t *__restrict__ nb_inst, int32_t *__restrict__ bad)
 {
     const size_t total = (size_t)n_inst * N;
     for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
          idx += (size_t)gridDim.x * blockDim.x) {
         const int p = (int)(idx % N);
         const size_t inst = idx / N;
-        int deg = 0, once = 0;
+        int deg = 0, once = 0, invalid = 0;
         for (int d = 0; d < Z; ++d) {
             const int b = edge_bond[p * Z + d];
             bool present = false;
-            if (b >= 0)
-                present = gauss ? ((const float *)bondJ)[inst * Nb + b] != 0.f
-                                : ((const int8_t *)bondJ)[inst * Nb + b] != 0;
+            if (b >= 0) {
+                if (gauss) {
+                    const float J = ((const float *)bondJ)[inst * Nb + b];
+                    present = J != 0.f;
+                    invalid += !isfinite(J);
+                } else {
+                    const int J = ((const int8_t *)bondJ)[inst * Nb + b];
+                    present = J != 0;
+                    invalid += J < -1 || J > 1;
+                }
+            }
             const int q = nbr[p * Z + d];
             nbr_inst[idx * Z + d] = (uint16_t)(present ? q : p);
             deg += present;
@@ -1147,6 +1156,7 @@ __global__ void expand_dilution_kernel(const void *__restrict__ bondJ, int gauss
         }
         zdeg_inst[idx] = (uint8_t)deg;
         if (once) atomicAdd(&nb_inst[inst], once);
+        if (invalid) atomicAdd(&bad[inst], invalid);
     }
 }
 
@@ -1333,11 +1343,11 @@ cudaError_t launch_expand_couplings(const void *bond_J, bool gauss, const int32_
 
 cudaError_t launch_expand_dilution(const void *bond_J, bool gauss, const int32_t *edge_bond, const uint16_t *nbr,
                                    int n_inst, int N, int Z, int Nb, uint16_t *nbr_inst, uint8_t *zdeg_inst,
-                                   int32_t *nb_inst, cudaStream_t st)
+                                   int32_t *nb_inst, int32_t *bad, cudaStream_t st)
 {
     expand_dilution_kernel<<<grid_for((size_t)n_inst * N, 256), 256, 0, st>>>(bond_J, gauss ? 1 : 0, edge_bond, nbr,
                                                                                n_inst, N, Z, Nb, nbr_inst,
-                                                                               zdeg_inst, nb_inst);
+                                                                               zdeg_inst, nb_inst, bad);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ from .inputs import CHIMERA, CUBIC3D, GAUSS, HYPERCUBIC4D, PM_J, SQUARE2D  # noq
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libicmpt.so")
 DEVICE_PTR = 1
-PENDING = 1          # icm_query: work still running
+PENDING = 1          # icm_query / server results: work still running
+CANCELLED = 2        # server results: the request was cancelled
 
 _lock = threading.Lock()
 _lib = None
@@ -48,7 +49,7 @@ EXPORTS = [
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
     "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
     "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
-    "icm_server_clock",
+    "icm_server_clock", "icm_server_cancel",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
@@ -123,6 +124,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_server_poll.argtypes = [vp, u64, ctypes.POINTER(ServerResult)]
         L.icm_server_status.argtypes = [vp] + [ctypes.POINTER(i32)] * 3
         L.icm_server_class_info.argtypes = [vp, i32] + [ctypes.POINTER(i32)] * 6
+        L.icm_server_cancel.argtypes = [vp, u64]
         L.icm_server_clock.argtypes = []
         L.icm_server_clock.restype = ctypes.c_double
         L.icm_clear_observables.argtypes = [vp]

@@ -51,7 +51,7 @@ class Request:
 @dataclass
 class Result:
     ticket: int
-    status: str                 # "thermalized" or "not_thermalized"
+    status: str                 # "thermalized", "not_thermalized" or "cancelled"
     sweeps: int
     arrival: float
     done: float
@@ -124,9 +124,15 @@ class Server:
         self._check(self._lib.icm_server_poll(self._h, int(ticket), ctypes.byref(out)))
         if out.status == icmpt.PENDING:
             return None
-        return Result(int(ticket), "thermalized" if out.thermalized else "not_thermalized", int(out.sweeps),
+        status = ("cancelled" if out.status == icmpt.CANCELLED else
+                  "thermalized" if out.thermalized else "not_thermalized")
+        return Result(int(ticket), status, int(out.sweeps),
                       self._arrival.get(int(ticket), out.t_submit), out.t_done, out.e, out.q_l, out.delta,
                       out.accE, int(out.acc_d), int(out.n_meas), int(out.slot))
+
+    def cancel(self, ticket: int):
+        """Drop a queued request, or release a running one at its class's next collection."""
+        self._check(self._lib.icm_server_cancel(self._h, int(ticket)))
 
     def status(self) -> tuple[int, int, int]:
         """(requests queued, requests in slots, classes)."""

@@ -62,6 +62,13 @@ def test_native_server_host_logic(lib):
     with pytest.raises(icmpt.IcmError):
         srv.poll(12345)                                      # unknown ticket
     assert srv.status() == (1, 0, 0)
+    t2 = srv.submit(Request(I.SQUARE2D, 8, I.PM_J, T, 1.0, 1, 8, ok.couplings))
+    srv.cancel(t2)                                           # queued: dropped at once
+    assert srv.poll(t2).status == "cancelled" and srv.poll(t2).sweeps == 0
+    with pytest.raises(icmpt.IcmError) as e:
+        srv.cancel(t2)
+    assert e.value.code == -6
+    assert srv.status() == (1, 0, 0) and srv.poll(t) is None
     srv.close()
     with pytest.raises(ValueError):
         Server(quantum=48)
@@ -199,3 +206,55 @@ def test_server_mixes_wide_and_shared_memory_classes(gpu):
         assert oa.accE[0, 0] == r.accE and oa.acc_d[0, 0] == r.acc_d and oa.n_meas[0] == r.n_meas
         a.close()
     srv.close()
+
+
+@pytest.mark.gpu
+def test_server_cancel_running_request(gpu):
+    icmpt, ctx = gpu
+    from paper_1501_05630_gb300.serve import Request, Server
+    T = I.ladder(0.3, 1.5, 8)
+    N, Nb = icmpt.lattice_size(I.SQUARE2D, 8)
+    reqs = [Request(I.SQUARE2D, 8, I.PM_J, T, 1.0, 3, 400 + i, I.couplings(Nb, I.PM_J, 3, [400 + i])[0])
+            for i in range(3)]
+    srv = Server(slots_per_class=4, quantum=16, eps_e=0.0, eps_ql=0.0, need=50, max_sweeps=4096)
+    tk = [srv.submit(r) for r in reqs]
+    for _ in range(20):
+        srv.step()
+    srv.cancel(tk[1])
+    srv.run_until_idle()
+    res = [srv.poll(t) for t in tk]
+    assert res[1].status == "cancelled" and 0 < res[1].sweeps < 4096
+    assert res[0].status == res[2].status == "not_thermalized" and res[0].sweeps == res[2].sweeps == 4096
+    assert srv.status() == (0, 0, 1)
+    srv.close()
+
+
+@pytest.mark.gpu
+def test_invalid_couplings_are_refused(gpu):
+    icmpt, ctx = gpu
+    T = I.ladder(0.3, 2.0, 6)
+    N, Nb = icmpt.lattice_size(I.CUBIC3D, 4)
+    J = I.couplings(Nb, I.PM_J, 1, range(3))
+    bad = J.copy()
+    bad[1, 5] = 2                                            # not a +-J value
+    with pytest.raises(icmpt.IcmError) as e:
+        icmpt.Batch(ctx, I.CUBIC3D, 4, I.PM_J, bad, T, 1.0, 1)
+    assert e.value.code == -1
+    Jg = I.couplings(Nb, I.GAUSS, 1, range(2))
+    Jg[0, 3] = np.nan
+    with pytest.raises(icmpt.IcmError):
+        icmpt.Batch(ctx, I.CUBIC3D, 4, I.GAUSS, Jg, T, 1.0, 1)
+    b = icmpt.Batch(ctx, I.CUBIC3D, 4, I.PM_J, J, T, 1.0, 1)
+    b.run(3)
+    with pytest.raises(icmpt.IcmError):                      # the slot is refused and freed
+        b.set_slot(2, bad[1], None, instance_id=9)
+    b.run(3)                                                 # the other slots keep running
+    assert list(b.read_sweeps()) == [6, 6, 3]
+    with pytest.raises(icmpt.IcmError):
+        b.load(couplings=bad)
+    with pytest.raises(icmpt.IcmError) as e:                 # refused until valid couplings are loaded
+        b.run(1)
+    assert e.value.code == -6
+    b.load(couplings=J)
+    b.run(1)
+    b.close()
