@@ -378,14 +378,21 @@ icm_status icm_percolation_random(icm_ctx *ctx, int32_t lattice, int32_t L, doub
                                   int32_t n_masks, int32_t *smax, uint32_t flags);
 
 /* ---------------------------------------------------------------- launch shape
- * The threads per CTA of a batch's kernel (32, 64, 96 or 128; one CTA runs one
- * instance).  Gaussian results depend on it through the summation order of
- * the fp32 energies; +-J results do not.                                   */
+ * The threads per CTA of a batch's kernel, a multiple of 32 up to 1024; one
+ * CTA runs one instance.  Up to 128 threads the instance lives in shared
+ * memory; wider CTAs use the global-resident layout (the only one for
+ * instances too large for shared memory).  Gaussian results depend on the
+ * width through the summation order of the fp32 energies; +-J results do
+ * not.                                                                      */
 icm_status icm_batch_set_threads(icm_batch *b, int32_t threads);
-/* Time every valid CTA width on `sweeps` sweeps of this batch and keep the
- * fastest.  The batch's state (spins, energies, sweep counters, observables)
- * is restored afterwards, so tuning does not advance the chain.  Allocates a
- * temporary snapshot.                                                      */
+/* Time every valid launch shape on `sweeps` sweeps of this batch and keep
+ * the fastest: CTA widths 32..128 (shared memory) when the instance fits,
+ * and for instances with more than 128 sites per colour also wide CTAs
+ * (256, 512, 1024) and thread-block clusters (K = 4, 8 of 256 or 512
+ * threads).  best_threads is the CTA width; icm_batch_cluster gives K.  The
+ * batch's state (spins, energies, sweep counters, observables) is restored
+ * afterwards, so tuning does not advance the chain.  Allocates a temporary
+ * snapshot.                                                                */
 icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threads, float *best_ms);
 
 /* A group runs several batches (e.g. one per lattice size of a mixed-size
@@ -413,6 +420,19 @@ icm_status icm_load(icm_batch *b, const void *buf, size_t len);
 
 /* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
  * dynamic shared memory bytes per CTA and kernel launches issued so far. */
+/* Thread-block-cluster layout: each instance runs on a cluster of K CTAs
+ * (K = 2, 4 or 8; K SMs), each holding 1/K of the sites of each colour in
+ * its shared memory and reading its neighbours' words through the cluster's
+ * distributed shared memory.  The arithmetic and random keys are those of
+ * the one-CTA layouts (the same chain, bit for bit for +-J); a single large
+ * instance finishes its sweeps up to K times sooner.  Needs degree 4 or 6
+ * lattices (2D, 3D, chimera), an undiluted batch and N/2 divisible into K
+ * blocks of a multiple of 32 sites.  K = 0 returns to one CTA per instance
+ * (CTA width `threads`, as icm_batch_set_threads).  A batch that becomes
+ * diluted returns to one CTA per instance by itself.                      */
+icm_status icm_batch_set_cluster(icm_batch *b, int32_t K, int32_t threads);
+icm_status icm_batch_cluster(const icm_batch *b, int32_t *K);
+
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,
                           int32_t *grid, int32_t *smem_bytes, int64_t *launches);
 

@@ -15,8 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libicmpt.so")
-SOURCES = ["pt_icm.cu", "fused_pmj.cu", "fused_gauss.cu", "icm_api.cpp", "icm_server.cpp", "icm_static.cu",
-           "percolation.cu"]
+SOURCES = ["pt_icm.cu", "fused_pmj.cu", "fused_gauss.cu", "cluster_icm.cu", "icm_api.cpp", "icm_server.cpp",
+           "icm_static.cu", "percolation.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"),
          "-I", CSRC]

@@ -1,0 +1,892 @@
+// cluster_icm.cu -- the simulation step of pt_icm.cu for one instance spread
+// over a thread-block cluster of K CTAs (K SMs), for instances whose single
+// CTA would be slow (2D L=128, 3D L=16 and larger).
+//
+// CTA r of the cluster owns the positions [c half + r hs, c half + (r+1) hs)
+// of each colour c and keeps their spin words, couplings, cluster words and
+// neighbour table in its own shared memory.  A neighbour's word is read
+// through the cluster's distributed shared memory: the neighbour table holds
+// the 32-bit cluster-window address (mapa) of the neighbour's spin word in
+// its owner CTA, read with ld.shared::cluster.  Phases are separated by
+// cluster barriers (barrier.cluster arrive.release / wait.acquire):
+//  * sweep: colour 0, barrier, colour 1; each CTA sums its sites' energies,
+//    barrier, every CTA adds the K shares in rank order (the same E in all);
+//  * ICM: per-CTA overlap counts, barrier, every CTA finds the seed's owner
+//    from the K counts (position order = (colour, rank, local)), the owner
+//    plants it, barrier; growth rounds end with a barrier and the OR of the
+//    K CTAs' round flags; flip, barrier, copy-a energies summed as above;
+//  * PT: every CTA holds the same energies and draws the same numbers, so
+//    all make the same decisions and permute their own words; barrier;
+//  * observables: per-CTA counts, barrier, rank 0 accumulates.
+// Every buffer another CTA reads is rewritten only after a barrier that
+// both have passed since the read.  Random keys are those of the
+// single-CTA kernels, so the chain is the same, bit for bit for +-J.
+#include "icm_internal.h"
+#include "icm_device.cuh"
+
+#include <type_traits>
+
+namespace icm {
+namespace {
+
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cl_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cl_count()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every CTA of the cluster; orders shared-memory accesses
+// across the cluster (release before, acquire after).
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Cluster-window address of the shared-memory byte `local` (a shared-window
+// address of this CTA) in CTA `rank`.
+__device__ __forceinline__ uint32_t cl_map(uint32_t local, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cl_ld(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T cl_ldT(uint32_t addr)
+{
+    const uint32_t v = cl_ld(addr);
+    if constexpr (std::is_same<T, float>::value) return __uint_as_float(v);
+    else return (T)(int)v;
+}
+
+// This CTA's view: pointers into its shared memory and cluster addresses.
+struct CS {
+    uint32_t *s, *C0, *C1, *nb;
+    float *Jd;
+    uint8_t *Jb, *zdeg;
+    void *E, *Epart, *Esw, *Epair, *esum;
+    uint32_t *thr;
+    float *b2l;
+    uint32_t *mask;
+    int *cntloc, *flags, *seed, *csz, *cnt_n, *cnt_d;
+    uint32_t *flipw;
+    uint32_t *swap_x;
+    int *swap_list, *swap_n;
+    uint64_t *swap_mask;
+    double *accE;
+    long long *acc64, *nmeas;
+    uint32_t base;        // shared-window address of this CTA's dynamic shared memory
+    uint32_t rank, K;
+    int hs, nls;
+};
+
+__device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &L)
+{
+    CS S;
+    S.s = (uint32_t *)(smem + L.s);
+    S.C0 = (uint32_t *)(smem + L.C0);
+    S.C1 = (uint32_t *)(smem + L.C1);
+    S.nb = (uint32_t *)(smem + L.nb);
+    S.Jd = (float *)(smem + L.coup);
+    S.Jb = (uint8_t *)(smem + L.coup);
+    S.zdeg = (uint8_t *)(smem + L.zdeg);
+    S.E = smem + L.E;
+    S.Epart = smem + L.Epart;
+    S.Esw = smem + L.Esw;
+    S.Epair = smem + L.Epair;
+    S.esum = smem + L.esum;
+    S.thr = (uint32_t *)(smem + L.rtab);
+    S.b2l = (float *)(smem + L.rtab);
+    S.mask = (uint32_t *)(smem + L.mask);
+    S.cntloc = (int *)(smem + L.cntloc);
+    S.flags = (int *)(smem + L.flags);
+    S.seed = (int *)(smem + L.seed);
+    S.csz = (int *)(smem + L.csz);
+    S.cnt_n = (int *)(smem + L.cnt_n);
+    S.cnt_d = (int *)(smem + L.cnt_d);
+    S.flipw = (uint32_t *)(smem + L.flipw);
+    S.swap_x = (uint32_t *)(smem + L.swap_x);
+    S.swap_list = (int *)(smem + L.swap_list);
+    S.swap_n = (int *)(smem + L.swap_n);
+    S.swap_mask = (uint64_t *)(smem + L.swap_mask);
+    S.accE = (double *)(smem + L.accE);
+    S.acc64 = (long long *)(smem + L.acc64);
+    S.nmeas = (long long *)(smem + L.nmeas);
+    S.base = (uint32_t)__cvta_generic_to_shared(smem);
+    S.rank = cl_rank();
+    S.K = (uint32_t)L.K;
+    S.hs = L.hs;
+    S.nls = L.nls;
+    return S;
+}
+
+// Sum over the cluster, in rank order, of the ET value at byte offset `off`
+// of every CTA's shared memory (the same result in every CTA).
+template <typename ET>
+__device__ __forceinline__ ET cl_sum(const CS &S, int off)
+{
+    ET v = ET(0);
+    for (uint32_t r = 0; r < S.K; ++r) v += cl_ldT<ET>(cl_map(S.base + off, r));
+    return v;
+}
+
+// Global position of local site li of CTA `rank`.
+__device__ __forceinline__ int pos_of(const KParams &P, const CS &S, int li)
+{
+    const int c = li >= S.hs;
+    return c * P.half + (int)S.rank * S.hs + (li - c * S.hs);
+}
+
+// ---------------------------------------------------------------------------
+// Step 1, one 16-bit pass of colour COLOR over word g (see sweep_pass in
+// pt_icm.cu: the same arithmetic, with neighbour words read through the
+// cluster window).
+template <bool GAUSS, int Z>
+__device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uint32_t t, uint32_t inst, int g,
+                                              int COLOR, int H)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nth = blockDim.x;
+    const int rbase = 32 * g + 16 * H;
+    const int sh0 = 16 * H;
+    const int npairs8 = (P.R - rbase + 7) >> 3;
+    const uint32_t goff = (uint32_t)(g * S.nls * 4);
+    uint32_t *sg = S.s + g * S.nls;
+    ET acc[16];
+#pragma unroll
+    for (int b = 0; b < 16; ++b) acc[b] = ET(0);
+    for (int j = threadIdx.x; j < S.hs; j += nth) {
+        const int li = COLOR * S.hs + j;
+        const uint32_t sw0 = sg[li];
+        const uint32_t sw = sw0 >> sh0;
+        const uint32_t site = __ldg(P.pos2site + pos_of(P, S, li));
+        uint32_t nw[Z];
+#pragma unroll
+        for (int d = 0; d < Z; ++d) nw[d] = cl_ld(S.nb[li * Z + d] + goff);
+        uint32_t flip = 0;
+        if constexpr (GAUSS) {
+            float J2[Z];
+            float Jsum = 0.f;
+#pragma unroll
+            for (int d = 0; d < Z; ++d) {
+                nw[d] >>= sh0;
+                const float J = S.Jd[li * Z + d];
+                Jsum += J;
+                J2[d] = 2.f * J;
+            }
+            const float *b2l = S.b2l + rbase;
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq) {
+                if (qq < npairs8) {
+                    uint32_t x[4], y[4];
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+                    uint32_t f8 = 0u;
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int b = 8 * qq + i;
+                        float h = Jsum;
+#pragma unroll
+                        for (int d = 0; d < Z; ++d)
+                            if ((nw[d] >> b) & 1u) h -= J2[d];
+                        const float sh = ((sw >> b) & 1u) ? -h : h;
+                        const uint32_t xr = i < 4 ? x[i] : y[i - 4];
+                        const uint32_t thr = __float2uint_rz(ex2_approx(fmaf(b2l[b], sh, 32.f)));
+                        const bool a = (sh <= 0.f) || (xr < thr);
+                        f8 |= (uint32_t)a << i;
+                        acc[b] -= sh;
+                        if (a) acc[b] += 2.f * sh;
+                    }
+                    flip |= f8 << (8 * qq);
+                }
+            }
+        } else {
+            uint32_t c0 = 0, c1 = 0, c2 = 0;
+            const uint32_t jb = S.Jb[li];
+#pragma unroll
+            for (int d = 0; d < Z; ++d) {
+                const uint32_t u = sw0 ^ nw[d] ^ (0u - ((jb >> d) & 1u));
+                const uint32_t t0 = c0 & u;
+                c0 ^= u;
+                const uint32_t t1 = c1 & t0;
+                c1 ^= t0;
+                c2 |= t1;
+            }
+            c0 >>= sh0;
+            c1 >>= sh0;
+            c2 >>= sh0;
+            const int z = P.const_z ? P.const_z : (int)S.zdeg[li];
+            flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
+            constexpr int TS = thr_stride(Z);
+            const uint32_t *thr = S.thr + rbase * TS;
+#pragma unroll
+            for (int qq = 0; qq < 2; ++qq) {
+                if (qq < npairs8) {
+                    uint32_t x[4], y[4];
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int b = 8 * qq + i;
+                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                        const int m = z - 2 * u;
+                        const uint32_t xr = i < 4 ? x[i] : y[i - 4];
+                        const uint32_t th = thr[b * TS + (m > 0 ? m : 0)];
+                        flip |= (uint32_t)(xr < th) << b;
+                        acc[b] += ((flip >> b) & 1u) ? m : -m;
+                    }
+                }
+            }
+        }
+        sg[li] = sw0 ^ (flip << sh0);
+    }
+    if (COLOR == 1) {
+        const ET v = transpose_reduce16(acc, lane);
+        const int r = rbase + (lane >> 1);
+        if (!(lane & 1) && r < P.R) ((ET *)S.Epart)[warp * P.R + r] = v;
+    }
+}
+
+// Step 1 for all replicas; then every CTA's share of the energies, summed
+// over the cluster in rank order.
+template <bool GAUSS, int Z>
+__device__ __forceinline__ void cl_metropolis(const KParams &P, const ClusterLayout &L, const CS &S, uint32_t t,
+                                              uint32_t inst)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int npass = (P.R + 15) >> 4;
+    const int nwarps = blockDim.x >> 5;
+    for (int it = 0; it < 2 * npass; ++it) {
+        const int color = it >= npass;
+        const int pass = it - color * npass;
+        cl_sweep_pass<GAUSS, Z>(P, S, t, inst, pass >> 1, color, pass & 1);
+        if (pass == npass - 1) {
+            if (color == 0) cl_sync();            // colour 1 reads colour-0 words of other CTAs
+            else __syncthreads();
+        }
+    }
+    for (int r = threadIdx.x; r < P.R; r += blockDim.x) {
+        ET e = ET(0);
+        for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * P.R + r];
+        ((ET *)S.Esw)[r] = e;
+    }
+    cl_sync();
+    for (int r = threadIdx.x; r < P.R; r += blockDim.x) ((ET *)S.E)[r] = cl_sum<ET>(S, L.Esw + 4 * r);
+    __syncthreads();
+}
+
+// Steps 2a and 2b (see cluster_moves in pt_icm.cu).
+template <bool GAUSS, int Z>
+__device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const CS &S, uint32_t t, uint32_t inst,
+                                 int slot, bool trace)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int N = P.N, nicm = P.n_icm, G = P.G, nls = S.nls, hs = S.hs, NWl = L.NWl;
+    ET *E = (ET *)S.E;
+    ET *esum = (ET *)S.esum;
+
+    // (a) overlap masks of the own sites, per-colour-block counts
+    for (int m = warp; m < NWl; m += nwarps) {
+        const int li = 32 * m + lane;
+        const uint32_t w0 = S.s[li];
+        const uint32_t q0 = w0 ^ (w0 >> 1);
+        uint32_t q1 = 0u;
+        if (G > 1) {
+            const uint32_t w1 = S.s[nls + li];
+            q1 = w1 ^ (w1 >> 1);
+        }
+        for (int k = 0; k < nicm; ++k) {
+            const uint32_t word = __ballot_sync(kFull, ((k < 16 ? q0 : q1) >> (2 * (k & 15))) & 1u);
+            if (lane == (k & 31)) S.mask[k * NWl + m] = word;
+        }
+    }
+    for (int i = tid; i < nls; i += nth) {
+        S.C0[i] = 0u;
+        S.C1[i] = 0u;
+    }
+    if (tid < 2) S.flipw[tid] = 0u;
+    if (tid < 32) S.csz[tid] = 0;
+    __syncthreads();
+    for (int k = tid; k < nicm; k += nth)
+        for (int c = 0; c < 2; ++c) {
+            int n = 0;
+            for (int m = c * (hs / 32); m < (c + 1) * (hs / 32); ++m) n += __popc(S.mask[k * NWl + m]);
+            S.cntloc[c * 32 + k] = n;
+        }
+    cl_sync();
+
+    // (b) per pair, in every CTA alike: n, step 2a, the seed's owner by rank;
+    // the owner plants the seed
+    for (int k = tid; k < nicm; k += nth) {
+        int n = 0;
+        for (int c = 0; c < 2; ++c)
+            for (uint32_t r = 0; r < S.K; ++r) n += (int)cl_ld(cl_map(S.base + L.cntloc + 4 * (c * 32 + k), r));
+        const int n_pre = n;
+        const bool flipped = P.enable_2a && 2 * n > N;
+        if (flipped) {
+            n = N - n;
+            atomicOr(&S.flipw[(2 * k + 1) >> 5], 1u << ((2 * k + 1) & 31));
+        }
+        int seed_pos = -1;
+        if (n > 0) {
+            uint32_t x[4];
+            philox10((uint32_t)k, t, 0u, (1u << 24) | inst, P.seed_lo, P.seed_hi, x);
+            uint32_t rank = (uint32_t)(((uint64_t)x[0] * (uint32_t)n) >> 32);
+            for (int c = 0; c < 2 && seed_pos < 0; ++c)
+                for (uint32_t r = 0; r < S.K; ++r) {
+                    int cnt = (int)cl_ld(cl_map(S.base + L.cntloc + 4 * (c * 32 + k), r));
+                    if (flipped) cnt = hs - cnt;
+                    if (rank < (uint32_t)cnt) {
+                        if (r == S.rank) {             // this CTA owns the seed: find the local site
+                            for (int m = c * (hs / 32); m < (c + 1) * (hs / 32); ++m) {
+                                uint32_t w = S.mask[k * NWl + m];
+                                if (flipped) w = ~w;
+                                const uint32_t pc = (uint32_t)__popc(w);
+                                if (rank < pc) {
+                                    for (uint32_t q = 0; q < rank; ++q) w &= w - 1u;
+                                    const int li = 32 * m + __ffs(w) - 1;
+                                    atomicOr((k < 16 ? S.C0 : S.C1) + li, 1u << (2 * (k & 15)));
+                                    if (trace) P.tr_seed[(size_t)slot * P.nT + k] = (int)__ldg(P.pos2site + pos_of(P, S, li));
+                                    break;
+                                }
+                                rank -= pc;
+                            }
+                        }
+                        seed_pos = c * P.half + (int)r * hs;   // block of the seed (the owner records the site)
+                        break;
+                    }
+                    rank -= (uint32_t)cnt;
+                }
+        }
+        S.seed[k] = seed_pos >= 0;
+        esum[k] = E[2 * k] + E[2 * k + 1];
+        if (trace && S.rank == 0) {
+            const size_t o = (size_t)slot * P.nT + k;
+            P.tr_n_pre[o] = n_pre;
+            P.tr_flip2a[o] = flipped;
+            if (seed_pos < 0) P.tr_seed[o] = -1;
+            P.tr_csize[o] = 0;
+            P.tr_eb[o] = (float)(E[2 * k] + E[2 * k + 1]);
+            P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
+        }
+    }
+    cl_sync();
+
+    // (c) step 2a on the own sites, then the clusters of all pairs at once
+    uint32_t act0 = 0u, act1 = 0u;
+    for (int k = 0; k < nicm; ++k)
+        if (S.seed[k]) {
+            if (k < 16) act0 |= 1u << (2 * k);
+            else act1 |= 1u << (2 * (k - 16));
+        }
+    const uint32_t f0 = S.flipw[0], f1 = S.flipw[1];
+    for (int li = tid; li < nls; li += nth) {
+        S.s[li] ^= f0;
+        if (G > 1) S.s[nls + li] ^= f1;
+    }
+    if (!(act0 | act1)) {
+        __syncthreads();
+        return;                                      // the same decision in every CTA
+    }
+    const uint32_t dC0 = (uint32_t)(L.C0 - L.s), dC1 = (uint32_t)(L.C1 - L.s);
+    for (int round = 0;; ++round) {
+        int grew = 0;
+        for (int li = tid; li < nls; li += nth) {
+            const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
+            const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
+            const uint32_t c0 = S.C0[li], c1 = S.C1[li];
+            if (d0 == c0 && d1 == c1) continue;
+            uint32_t nb0 = 0u, nb1 = 0u;
+#pragma unroll
+            for (int d = 0; d < Z; ++d) {
+                const uint32_t e = S.nb[li * Z + d];
+                nb0 |= cl_ld(e + dC0);
+                if (G > 1) nb1 |= cl_ld(e + dC1);
+            }
+            const uint32_t n0 = c0 | (d0 & nb0), n1 = c1 | (d1 & nb1);
+            if (n0 != c0 || n1 != c1) {
+                S.C0[li] = n0;
+                S.C1[li] = n1;
+                grew = 1;
+            }
+        }
+        const int any_here = __syncthreads_or(grew);
+        if (tid == 0) S.flags[round & 1] = any_here;
+        cl_sync();
+        int any = 0;
+        for (uint32_t r = 0; r < S.K; ++r) any |= (int)cl_ld(cl_map(S.base + L.flags + 4 * (round & 1), r));
+        if (!any) break;
+    }
+
+    // (d) flip the own sites; copy-a energies of the moved pairs
+    for (int li = tid; li < nls; li += nth) {
+        const uint32_t c0 = S.C0[li], c1 = S.C1[li];
+        if (c0) S.s[li] ^= c0 | (c0 << 1);
+        if (c1) S.s[nls + li] ^= c1 | (c1 << 1);
+        if (trace)
+            for (int w = 0; w < 2; ++w)
+                for (uint32_t b = w ? c1 : c0; b; b &= b - 1u) atomicAdd(&S.csz[16 * w + ((__ffs(b) - 1) >> 1)], 1);
+    }
+    cl_sync();                                       // flipped words of other CTAs are read below
+    ET *part = (ET *)S.Epart;
+    for (int g = 0; g < G; ++g) {
+        const uint32_t act = g ? act1 : act0;
+        if (!act) continue;
+        const uint32_t goff = (uint32_t)(g * nls * 4);
+        const uint32_t *sg = S.s + g * nls;
+        ET acc[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) acc[j] = ET(0);
+        for (int j = tid; j < hs; j += nth) {
+            const int li = hs + j;                   // colour-1 sites: every bond once
+            const uint32_t sw = sg[li];
+            uint32_t nw[Z];
+#pragma unroll
+            for (int d = 0; d < Z; ++d) nw[d] = cl_ld(S.nb[li * Z + d] + goff);
+            if constexpr (GAUSS) {
+                float J2[Z];
+                float Jsum = 0.f;
+#pragma unroll
+                for (int d = 0; d < Z; ++d) {
+                    const float J = S.Jd[li * Z + d];
+                    Jsum += J;
+                    J2[d] = 2.f * J;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    if (!((act >> (2 * jj)) & 1u)) continue;
+                    const int b = 2 * jj;
+                    float h = Jsum;
+#pragma unroll
+                    for (int d = 0; d < Z; ++d)
+                        if ((nw[d] >> b) & 1u) h -= J2[d];
+                    acc[jj] += ((sw >> b) & 1u) ? h : -h;
+                }
+            } else {
+                uint32_t c0 = 0, c1 = 0, c2 = 0;
+                const uint32_t jb = S.Jb[li];
+#pragma unroll
+                for (int d = 0; d < Z; ++d) {
+                    const uint32_t u = sw ^ nw[d] ^ (0u - ((jb >> d) & 1u));
+                    const uint32_t t0 = c0 & u;
+                    c0 ^= u;
+                    const uint32_t t1 = c1 & t0;
+                    c1 ^= t0;
+                    c2 |= t1;
+                }
+#pragma unroll
+                for (int jj = 0; jj < 16; ++jj) {
+                    const int b = 2 * jj;
+                    acc[jj] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                }
+            }
+        }
+        const ET v = transpose_reduce16(acc, lane);
+        if (!(lane & 1)) part[warp * 32 + 16 * g + (lane >> 1)] = v;
+    }
+    __syncthreads();
+    for (int k = tid; k < nicm; k += nth) {
+        ET e = ET(0);
+        if (S.seed[k])
+            for (int w = 0; w < nwarps; ++w) e += part[w * 32 + k];
+        ((ET *)S.Epair)[k] = e;
+    }
+    cl_sync();
+    for (int k = tid; k < nicm; k += nth) {
+        if (!S.seed[k]) continue;
+        ET ea = cl_sum<ET>(S, L.Epair + 4 * k);
+        if constexpr (!GAUSS) ea = 2 * ea - P.Nb;    // E = 2 U - N_b
+        E[2 * k] = ea;
+        E[2 * k + 1] = esum[k] - ea;
+        if (trace && S.rank == 0) {
+            const size_t o = (size_t)slot * P.nT + k;
+            int cs = 0;
+            for (uint32_t r = 0; r < S.K; ++r) cs += (int)cl_ld(cl_map(S.base + L.csz + 4 * k, r));
+            P.tr_csize[o] = cs;
+            P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
+        }
+    }
+    __syncthreads();
+}
+
+// Step 3 (see pt_pass in pt_icm.cu): the same energies and draws in every
+// CTA give the same decisions; each CTA permutes its own words.
+template <bool GAUSS>
+__device__ void cl_pt_pass(const KParams &P, const CS &S, uint32_t t, uint32_t inst, int slot, bool trace)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int nT = P.nT, np = nT - 1, nls = S.nls;
+    for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
+        const int c = i / np, k = i % np;
+        uint32_t x[4];
+        philox10((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.seed_lo, P.seed_hi, x);
+        S.swap_x[c * 32 + k] = x[0];
+    }
+    __syncthreads();
+    const int second = blockDim.x > 32 ? 32 : 1;
+    if (threadIdx.x == 0 || threadIdx.x == second) {
+        ET *E = (ET *)S.E;
+        const int c = threadIdx.x == 0 ? 0 : 1;
+        uint64_t D = 0;
+        int nrun = 0, run_start = -1;
+        for (int k = 0; k <= np; ++k) {
+            bool acc = false;
+            if (k < np) {
+                const int ra = 2 * k + c, rb = ra + 2;
+                const ET ek = E[ra], ek1 = E[rb];
+                const uint32_t x = S.swap_x[c * 32 + k];
+                if constexpr (GAUSS) {
+                    const float delta = P.dbeta_l2e[k] * (ek - ek1);
+                    acc = (delta >= 0.f) || ((float)(x >> 8) * (1.0f / 16777216.0f) < ex2_approx(delta));
+                } else {
+                    const int dE = ek - ek1;
+                    if (dE >= 0) {
+                        acc = true;
+                    } else {
+                        const int d = (-dE) >> 1;
+                        acc = d >= 1 && d <= P.swap_len[k] && x < P.thr_swap[P.swap_off[k] + d - 1];
+                    }
+                }
+                if (acc) {
+                    E[ra] = ek1;
+                    E[rb] = ek;
+                    D |= 1ull << rb;
+                    if (run_start < 0) run_start = k;
+                }
+                if (trace && S.rank == 0) P.tr_swap[((size_t)slot * 2 + c) * np + k] = (uint8_t)acc;
+            }
+            if (!acc && run_start >= 0) {
+                S.swap_list[c * 32 + nrun++] = ((2 * run_start + c) << 8) | (2 * k + c);
+                run_start = -1;
+            }
+        }
+        S.swap_n[c] = nrun;
+        S.swap_mask[c] = D;
+    }
+    __syncthreads();
+    const int n0 = S.swap_n[0], n1 = S.swap_n[1];
+    if (n0 + n1 > 0) {
+        const uint64_t D = S.swap_mask[0] | S.swap_mask[1];
+        uint64_t U = 0;
+        for (int j = 0; j < n0; ++j) U |= 1ull << (S.swap_list[j] >> 8);
+        for (int j = 0; j < n1; ++j) U |= 1ull << (S.swap_list[32 + j] >> 8);
+        const uint64_t keep = ~(D | U);
+        const bool two = P.G > 1;
+        for (int li = threadIdx.x; li < nls; li += blockDim.x) {
+            const uint64_t x = (uint64_t)S.s[li] | (two ? (uint64_t)S.s[nls + li] << 32 : 0ull);
+            uint64_t y = (x & keep) | ((x & D) >> 2);
+            for (int j = 0; j < n0; ++j) {
+                const int mv = S.swap_list[j];
+                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
+            }
+            for (int j = 0; j < n1; ++j) {
+                const int mv = S.swap_list[32 + j];
+                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
+            }
+            S.s[li] = (uint32_t)y;
+            if (two) S.s[nls + li] = (uint32_t)(y >> 32);
+        }
+    }
+    cl_sync();                                       // the observables read other CTAs' words
+}
+
+// Observables (see measure in pt_icm.cu): per-CTA counts, summed by rank 0.
+template <bool GAUSS, int Z>
+__device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S, int slot)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int lane = threadIdx.x & 31;
+    const int N = P.N, nT = P.nT, nls = S.nls, hs = S.hs;
+    const uint32_t self0 = cl_map(S.base + L.s, S.rank);
+    if (threadIdx.x < 32) {
+        S.cnt_n[threadIdx.x] = 0;
+        S.cnt_d[threadIdx.x] = 0;
+    }
+    __syncthreads();
+    for (int g = 0; g < P.G; ++g) {
+        const int npair = min(16, nT - 16 * g);
+        const uint32_t goff = (uint32_t)(g * nls * 4);
+        const uint32_t *sg = S.s + g * nls;
+        uint32_t pn[kPlanes], pd[kPlanes];
+#pragma unroll
+        for (int i = 0; i < kPlanes; ++i) pn[i] = pd[i] = 0u;
+        for (int li = threadIdx.x; li < nls; li += blockDim.x) {
+            const uint32_t w = sg[li];
+            vadd(pn, (w ^ (w >> 1)) & 0x55555555u);
+        }
+        for (int li = hs + threadIdx.x; li < nls; li += blockDim.x) {
+            const uint32_t w = sg[li];
+            const uint32_t qp = (w ^ (w >> 1)) & 0x55555555u;
+#pragma unroll
+            for (int d = 0; d < Z; ++d) {
+                const uint32_t e = S.nb[li * Z + d];
+                if (e == self0 + 4u * (uint32_t)li) continue;      // padding entry
+                const uint32_t wq = cl_ld(e + goff);
+                vadd(pd, qp ^ ((wq ^ (wq >> 1)) & 0x55555555u));
+            }
+        }
+        for (int j = 0; j < npair; ++j) {
+            const int cn = __reduce_add_sync(kFull, vget(pn, 2 * j));
+            const int cd = __reduce_add_sync(kFull, vget(pd, 2 * j));
+            if (lane == 0) {
+                atomicAdd(&S.cnt_n[16 * g + j], cn);
+                atomicAdd(&S.cnt_d[16 * g + j], cd);
+            }
+        }
+    }
+    cl_sync();
+    if (S.rank == 0) {
+        for (int k = threadIdx.x; k < nT; k += blockDim.x) {
+            long long n = 0, d = 0;
+            for (uint32_t r = 0; r < S.K; ++r) {
+                n += (int)cl_ld(cl_map(S.base + L.cnt_n + 4 * k, r));
+                d += (int)cl_ld(cl_map(S.base + L.cnt_d + 4 * k, r));
+            }
+            const ET *E = (const ET *)S.E;
+            S.accE[k] += (double)E[2 * k] + (double)E[2 * k + 1];
+            S.acc64[0 * nT + k] += n;
+            S.acc64[1 * nT + k] += (N - 2 * n) * (N - 2 * n);
+            S.acc64[2 * nT + k] += n < N - n ? n : N - n;
+            S.acc64[3 * nT + k] += d;
+            atomicAdd(&P.hist[((size_t)slot * nT + k) * (N + 1) + n], 1ull);
+        }
+        if (threadIdx.x == 0) S.nmeas[0] += 1;
+    }
+    __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+template <bool GAUSS, int Z>
+__global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KParams P, const ClusterLayout L,
+                                                                    uint32_t n_sweeps)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const CS S = make_cs(smem, L);
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int N = P.N, R = P.R, nT = P.nT, G = P.G, nls = S.nls, hs = S.hs, half = P.half;
+
+    // neighbour table: cluster-window address of each neighbour's spin word
+    for (int i = tid; i < nls * Z; i += nth) {
+        const int li = i / Z, d = i % Z;
+        const int q = P.nbr[pos_of(P, S, li) * Z + d];
+        const int cq = q >= half;
+        const int hq = q - cq * half;
+        const uint32_t rq = (uint32_t)(hq / hs);
+        const int lq = cq * hs + hq % hs;
+        S.nb[i] = cl_map(S.base + L.s, rq) + 4u * (uint32_t)lq;
+    }
+    if (!GAUSS && !P.const_z)
+        for (int li = tid; li < nls; li += nth) S.zdeg[li] = P.zdeg[pos_of(P, S, li)];
+    if constexpr (GAUSS) {
+        for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
+    } else {
+        constexpr int TS = thr_stride(Z);
+        for (int i = tid; i < 32 * G * TS; i += nth) S.thr[i] = i < R * TS ? P.thr_metro[i] : 0u;
+    }
+
+    for (int slot = (int)cl_id(); slot < P.n_inst; slot += (int)cl_count()) {
+        if (P.active && !P.active[slot]) continue;   // the same for every CTA of the cluster
+        for (int i = tid; i < G * nls; i += nth) {
+            const int g = i / nls, li = i % nls;
+            S.s[i] = P.spins[((size_t)slot * G + g) * N + pos_of(P, S, li)];
+        }
+        if constexpr (GAUSS) {
+            for (int i = tid; i < nls * Z; i += nth)
+                S.Jd[i] = P.Jd[((size_t)slot * N + pos_of(P, S, i / Z)) * Z + i % Z];
+            for (int r = tid; r < R; r += nth) ((float *)S.E)[r] = P.Ef[(size_t)slot * R + r];
+        } else {
+            for (int li = tid; li < nls; li += nth) S.Jb[li] = P.Jb[(size_t)slot * N + pos_of(P, S, li)];
+            for (int r = tid; r < R; r += nth) ((int *)S.E)[r] = P.Ei[(size_t)slot * R + r];
+        }
+        if (S.rank == 0) {
+            for (int k = tid; k < nT; k += nth) {
+                S.accE[k] = P.accE[(size_t)slot * nT + k];
+                for (int a = 0; a < 4; ++a) S.acc64[a * nT + k] = P.acc64[((size_t)a * P.n_inst + slot) * nT + k];
+            }
+            if (tid == 0) S.nmeas[0] = P.n_meas[slot];
+        }
+        const uint32_t inst = P.inst_id[slot];
+        const long long t_meas = P.t_meas_inst ? P.t_meas_inst[slot] : P.t_meas;
+        uint32_t t = P.tsweep[slot];
+        cl_sync();
+
+        for (uint32_t step = 0; step < n_sweeps; ++step, ++t) {
+            const bool trace = P.trace && step + 1 == n_sweeps;
+            if (trace && S.rank == 0) {
+                for (int k = tid; k < nT; k += nth) {
+                    const size_t o = (size_t)slot * nT + k;
+                    P.tr_n_pre[o] = -1;
+                    P.tr_flip2a[o] = 0;
+                    P.tr_seed[o] = -1;
+                    P.tr_csize[o] = 0;
+                    P.tr_eb[o] = 0.f;
+                    P.tr_ea[o] = 0.f;
+                }
+                for (int i = tid; i < 2 * (nT - 1); i += nth) P.tr_swap[(size_t)slot * 2 * (nT - 1) + i] = 0;
+            }
+            cl_sync();                               // buffers read remotely in the last step are free again
+            if (P.enable_metropolis) cl_metropolis<GAUSS, Z>(P, L, S, t, inst);
+            if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)
+                cl_cluster_moves<GAUSS, Z>(P, L, S, t, inst, slot, trace);
+            if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1) cl_pt_pass<GAUSS>(P, S, t, inst, slot, trace);
+            else cl_sync();                          // 2a and cluster flips visible to the observables
+            if ((long long)t >= t_meas) cl_measure<GAUSS, Z>(P, L, S, slot);
+        }
+
+        for (int i = tid; i < G * nls; i += nth) {
+            const int g = i / nls, li = i % nls;
+            P.spins[((size_t)slot * G + g) * N + pos_of(P, S, li)] = S.s[i];
+        }
+        if (S.rank == 0) {
+            for (int r = tid; r < R; r += nth) {
+                if constexpr (GAUSS) P.Ef[(size_t)slot * R + r] = ((float *)S.E)[r];
+                else P.Ei[(size_t)slot * R + r] = ((int *)S.E)[r];
+            }
+            for (int k = tid; k < nT; k += nth) {
+                P.accE[(size_t)slot * nT + k] = S.accE[k];
+                for (int a = 0; a < 4; ++a) P.acc64[((size_t)a * P.n_inst + slot) * nT + k] = S.acc64[a * nT + k];
+            }
+            if (tid == 0) {
+                P.n_meas[slot] = S.nmeas[0];
+                P.tsweep[slot] = t;
+            }
+        }
+        cl_sync();
+    }
+}
+
+template <bool GAUSS, int Z>
+cudaError_t launch_cluster_t(const KParams &P, const ClusterLayout &L, int threads, int n_clusters, uint32_t n_sweeps,
+                             cudaStream_t st)
+{
+    auto kern = cluster_kernel<GAUSS, Z>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(n_clusters * L.K), 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)L.total;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)L.K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, P, L, n_sweeps);
+}
+
+template <bool GAUSS, int Z>
+cudaError_t cluster_occupancy_t(int K, int threads, int smem, int *clusters)
+{
+    auto kern = cluster_kernel<GAUSS, Z>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)K, 1, 1);
+    cfg.blockDim = dim3((unsigned)threads, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)K;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
+}
+
+int align_up16(int v) { return (v + 15) / 16 * 16; }
+
+}  // namespace
+
+ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss)
+{
+    ClusterLayout L{};
+    L.K = K;
+    L.hs = (N / 2) / K;
+    L.nls = 2 * L.hs;
+    L.NWl = L.nls / 32;
+    int o = 0;
+    auto take = [&](int bytes) {
+        o = align_up16(o);
+        const int at = o;
+        o += bytes;
+        return at;
+    };
+    const int nls = L.nls;
+    L.s = take(G * nls * 4);
+    L.C0 = take(nls * 4);
+    L.C1 = take(nls * 4);
+    L.nb = take(nls * Z * 4);
+    L.coup = take(gauss ? nls * Z * 4 : nls);
+    L.zdeg = take(nls);
+    L.E = take(R * 4);
+    L.Epart = take(nwarps * (R > 32 ? R : 32) * 4);
+    L.Esw = take(R * 4);
+    L.Epair = take(32 * 4);
+    L.rtab = take(gauss ? G * 32 * 4 : G * 32 * thr_stride(Z) * 4);
+    L.mask = take(32 * L.NWl * 4);
+    L.cntloc = take(2 * 32 * 4);
+    L.flags = take(2 * 4);
+    L.seed = take(32 * 4);
+    L.esum = take(32 * 4);
+    L.flipw = take(2 * 4);
+    L.csz = take(32 * 4);
+    L.swap_x = take(2 * 32 * 4);
+    L.swap_list = take(2 * 32 * 4);
+    L.swap_n = take(2 * 4);
+    L.swap_mask = take(2 * 8);
+    L.cnt_n = take(32 * 4);
+    L.cnt_d = take(32 * 4);
+    L.accE = take(nT * 8);
+    L.acc64 = take(4 * nT * 8);
+    L.nmeas = take(8);
+    L.total = align_up16(o);
+    return L;
+}
+
+cudaError_t launch_cluster(const KParams &P, const ClusterLayout &L, bool gauss, int threads, int n_clusters,
+                           uint32_t n_sweeps, cudaStream_t st)
+{
+    if (threads > kMaxThreadsWide || L.K < 1 || L.hs % 32 || P.diluted) return cudaErrorInvalidValue;
+    if (gauss) return P.Z == 4 ? launch_cluster_t<true, 4>(P, L, threads, n_clusters, n_sweeps, st)
+                               : launch_cluster_t<true, 6>(P, L, threads, n_clusters, n_sweeps, st);
+    return P.Z == 4 ? launch_cluster_t<false, 4>(P, L, threads, n_clusters, n_sweeps, st)
+                    : launch_cluster_t<false, 6>(P, L, threads, n_clusters, n_sweeps, st);
+}
+
+cudaError_t cluster_occupancy(bool gauss, int Z, int K, int threads, int smem, int *clusters)
+{
+    if (Z != 4 && Z != 6) return cudaErrorInvalidValue;
+    if (gauss) return Z == 4 ? cluster_occupancy_t<true, 4>(K, threads, smem, clusters)
+                             : cluster_occupancy_t<true, 6>(K, threads, smem, clusters);
+    return Z == 4 ? cluster_occupancy_t<false, 4>(K, threads, smem, clusters)
+                  : cluster_occupancy_t<false, 6>(K, threads, smem, clusters);
+}
+
+}  // namespace icm

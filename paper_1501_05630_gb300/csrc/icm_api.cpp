@@ -218,6 +218,10 @@ struct icm_batch {
     // invalid couplings per instance (not finite; +-J outside -1, 0, +1)
     int32_t *d_bad = nullptr;         // [n_inst]
     std::vector<int32_t> h_bad;
+    // cluster layout: one instance per thread-block cluster of cluster_k CTAs
+    int cluster_k = 0;
+    icm::ClusterLayout cl{};
+    int n_clusters = 0;
     // wide (global-resident) layout: per-CTA scratch, grown on demand (in allocs)
     uint32_t *scratch = nullptr;      // [scratch_ctas][wide_scratch_words(N)]
     int scratch_ctas = 0;
@@ -227,6 +231,10 @@ struct icm_batch {
     std::vector<uint8_t> h_active;
     std::vector<long long> h_tmeas;
 };
+
+extern "C" {
+static icm_status apply_threads(icm_batch *b, int threads);   // defined with the ABI functions
+}
 
 namespace {
 
@@ -275,6 +283,13 @@ icm_status copy_out(icm_ctx *ctx, void *dst, const void *src, size_t bytes, uint
     return ICM_OK;
 }
 
+// One launch of n_sweeps simulation steps of the batch, in its layout.
+cudaError_t launch_batch(const icm_batch *b, const icm::KParams &P, uint32_t n_sweeps, cudaStream_t st)
+{
+    if (b->cluster_k) return icm::launch_cluster(P, b->cl, b->gauss, b->threads, b->n_clusters, n_sweeps, st);
+    return icm::launch_fused(P, b->gauss, b->threads, b->grid, n_sweeps, st);
+}
+
 // Per-instance dilution tables of slots [first, first + count) from the bond
 // couplings in raw_coup, then the batch flags: the batch is diluted while any
 // instance has an absent bond (the kernels then read per-instance neighbour
@@ -304,6 +319,11 @@ icm_status refresh_dilution(icm_batch *b, int first, int count)
     for (int32_t v : b->h_nb) diluted |= v < P.Nb;
     P.diluted = diluted ? 1 : 0;
     P.const_z = diluted ? 0 : b->uniform_z;
+    if (diluted && b->cluster_k) {
+        // the cluster layout has no per-instance neighbour tables: back to one CTA per instance
+        icm_status st = apply_threads(b, icm::fused_threads_wide(P.N));
+        if (st) return st;
+    }
     long long n_bad = 0;
     for (int i = first; i < first + count; ++i) n_bad += b->h_bad[i];
     if (n_bad)
@@ -473,8 +493,6 @@ icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_
     *n_bonds = Nb;
     return ICM_OK;
 }
-
-static icm_status apply_threads(icm_batch *b, int threads);
 
 icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
                             const void *couplings, const int8_t *spins, const uint32_t *instance_ids,
@@ -750,7 +768,7 @@ icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps)
     P.t_meas = b->sched.t_meas;
     P.active = b->d_active;
     P.t_meas_inst = b->d_tmeas;
-    ICM_CUDA(b->ctx, icm::launch_fused(P, b->gauss, b->threads, b->grid, n_sweeps, b->ctx->stream));
+    ICM_CUDA(b->ctx, launch_batch(b, P, n_sweeps, b->ctx->stream));
     b->launches += 1;
     return ICM_OK;
 }
@@ -1056,6 +1074,8 @@ static icm_status apply_threads(icm_batch *b, int threads)
         b->scratch = q;
         b->scratch_ctas = grid;
     }
+    b->cluster_k = 0;
+    b->n_clusters = 0;
     P.sm = sm;
     P.wide = wide ? 1 : 0;
     P.scratch = wide ? b->scratch : nullptr;
@@ -1064,6 +1084,52 @@ static icm_status apply_threads(icm_batch *b, int threads)
     b->threads = threads;
     b->ctas_per_sm = ctas;
     b->grid = grid;
+    return ICM_OK;
+}
+
+// One instance per thread-block cluster of K CTAs (K = 2, 4, 8) of `threads`
+// threads each; see cluster_icm.cu.  K = 0 returns to one CTA per instance.
+static icm_status apply_cluster(icm_batch *b, int K, int threads)
+{
+    icm::KParams &P = b->kp;
+    if (K == 0) return apply_threads(b, threads);
+    if (K != 2 && K != 4 && K != 8) return fail(b->ctx, ICM_ERR_ARG, "cluster size must be 2, 4 or 8");
+    if (threads < 32 || threads > icm::kMaxThreadsWide || threads % 32)
+        return fail(b->ctx, ICM_ERR_ARG, "threads per CTA must be a multiple of 32 in 32..1024");
+    if (P.Z != 4 && P.Z != 6) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "the cluster layout takes degrees 4 and 6");
+    if (P.diluted) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "the cluster layout takes undiluted batches");
+    const int half = P.N / 2;
+    if (half % K || (half / K) % 32)
+        return fail(b->ctx, ICM_ERR_UNSUPPORTED, "sites per colour must split into K blocks of a multiple of 32");
+    const int hs = half / K;
+    if (((hs + threads - 1) / threads) * P.Z >= 256 || (2 * hs + threads - 1) / threads >= 256)
+        return fail(b->ctx, ICM_ERR_UNSUPPORTED, "too many sites per thread for the observable counters");
+    const icm::ClusterLayout L = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss);
+    if (L.total > b->ctx->max_smem_optin) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster slice exceeds shared memory");
+    int clusters = 0;
+    cudaError_t e = icm::cluster_occupancy(b->gauss, P.Z, K, threads, L.total, &clusters);
+    if (e != cudaSuccess) return cuda_fail(b->ctx, e, "cluster occupancy");
+    if (clusters < 1) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster does not fit");
+    b->cluster_k = K;
+    b->cl = L;
+    b->threads = threads;
+    b->n_clusters = b->n_inst < clusters ? b->n_inst : clusters;
+    b->grid = b->n_clusters * K;
+    b->ctas_per_sm = 1;
+    P.small_counts = 0;
+    return ICM_OK;
+}
+
+icm_status icm_batch_set_cluster(icm_batch *b, int32_t K, int32_t threads)
+{
+    if (!b) return ICM_ERR_ARG;
+    return apply_cluster(b, K, threads);
+}
+
+icm_status icm_batch_cluster(const icm_batch *b, int32_t *K)
+{
+    if (!b || !K) return ICM_ERR_ARG;
+    *K = b->cluster_k;
     return ICM_OK;
 }
 
@@ -1112,14 +1178,22 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
     // does not, or when a colour has more sites than 128 threads
     const bool fits = icm::smem_layout(P.N, P.Z, P.R, P.G, P.nT, b->n_icm, icm::kMaxThreads / 32, b->gauss,
                                        false).total <= ctx->max_smem_optin;
-    std::vector<int> cand;
+    // (cluster size, CTA width) candidates: one CTA per instance in shared
+    // memory when it fits, wide CTAs when a colour has more than 128 sites,
+    // and thread-block clusters for those large instances too
+    std::vector<std::pair<int, int>> cand;
     if (fits)
-        for (int th : {32, 64, 96, 128}) cand.push_back(th);
-    if (!fits || P.N / 2 > icm::kMaxThreads)
-        for (int th : {256, 512, 1024}) cand.push_back(th);
+        for (int th : {32, 64, 96, 128}) cand.push_back({0, th});
+    if (!fits || P.N / 2 > icm::kMaxThreads) {
+        for (int th : {256, 512, 1024}) cand.push_back({0, th});
+        for (int K : {4, 8})
+            for (int th : {256, 512}) cand.push_back({K, th});
+    }
+    const int original_k = b->cluster_k;
+    int best_k = original_k;
     for (size_t ci = 0; !st && ci < cand.size(); ++ci) {
-        const int th = cand[ci];
-        if (apply_threads(b, th) != ICM_OK) continue;
+        const int K = cand[ci].first, th = cand[ci].second;
+        if (apply_cluster(b, K, th) != ICM_OK) continue;
         if ((st = icm_run_sweeps(b, sweeps))) break;               // warm-up
         cudaEventRecord(e0, ctx->stream);
         if ((st = icm_run_sweeps(b, sweeps))) break;
@@ -1130,6 +1204,7 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
         if (ms < best_t) {
             best_t = ms;
             best = th;
+            best_k = K;
         }
         b->launches -= 2;
     }
@@ -1142,7 +1217,7 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
     cudaStreamSynchronize(ctx->stream);
     for (auto &pc : pieces)
         if (pc.save) cudaFree(pc.save);
-    icm_status st2 = apply_threads(b, st ? original : best);
+    icm_status st2 = st ? apply_cluster(b, original_k, original) : apply_cluster(b, best_k, best);
     if (st) return st;
     if (st2) return st2;
     if (best_threads) *best_threads = best;
@@ -1217,7 +1292,7 @@ icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, 
         P.t_meas = b->sched.t_meas;
         P.active = b->d_active;
         P.t_meas_inst = b->d_tmeas;
-        e = icm::launch_fused(P, b->gauss, b->threads, b->grid, sweeps_per_launch, g->streams[i]);
+        e = launch_batch(b, P, sweeps_per_launch, g->streams[i]);
         if (e == cudaSuccess) e = cudaEventRecord(g->events[i], g->streams[i]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(origin, g->events[i], 0);
     }

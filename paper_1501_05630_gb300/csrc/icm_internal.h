@@ -110,6 +110,41 @@ struct HostTables {
 bool host_tables(int lattice, int L, HostTables &t);
 
 SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps, bool gauss, bool wide);
+
+// Thread-block-cluster layout (cluster_icm.cu): one instance per cluster of
+// K CTAs.  CTA r owns the positions [c half + r hs, c half + (r+1) hs) of
+// each colour c (hs = half / K), stored as local index li = c hs + i; every
+// per-site array has stride 4 bytes per local site, so the cluster-window
+// address of a neighbour's spin word also locates its other words.  Byte
+// offsets into each CTA's dynamic shared memory:
+struct ClusterLayout {
+    int K, hs, nls, NWl;   // CTAs, own sites per colour, own sites (2 hs), mask words (nls / 32)
+    int s;          // uint32 [G][nls]   spin words
+    int C0, C1;     // uint32 [nls]      cluster bits of word 0 / word 1 pairs
+    int nb;         // uint32 [nls][Z]   cluster-window address of the neighbour's s[0] word
+    int coup;       // float [nls][Z] (Gaussian) or uint8 [nls] sign bits (+-J)
+    int zdeg;       // uint8 [nls]
+    int E;          // float or int32 [R]       energies (the same in every CTA)
+    int Epart;      // float or int32 [nwarps][max(R, 32)]
+    int Esw;        // float or int32 [R]       this CTA's share of the sweep energies (read remotely)
+    int Epair;      // float or int32 [32]      this CTA's share of the copy-a energies (read remotely)
+    int rtab;       // thresholds (+-J) or -2 beta log2(e) (Gaussian), as in SmemLayout
+    int mask;       // uint32 [32][NWl]         overlap masks of the ICM pairs
+    int cntloc;     // int32 [2][32]            q = -1 sites per colour block and pair (read remotely)
+    int flags;      // int32 [2]                growth-round flags, by round parity (read remotely)
+    int seed;       // int32 [32]               1 = the pair moves
+    int esum;       // float or int32 [32]
+    int flipw;      // uint32 [2]
+    int csz;        // int32 [32]               this CTA's cluster sites per pair (read remotely)
+    int swap_x, swap_list, swap_n, swap_mask;   // as in SmemLayout
+    int cnt_n, cnt_d;   // int32 [32]           this CTA's observable counts (read remotely)
+    int accE, acc64, nmeas;                     // observables (rank 0)
+    int total;
+};
+ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss);
+cudaError_t launch_cluster(const KParams &P, const ClusterLayout &CL, bool gauss, int threads, int n_clusters,
+                           uint32_t n_sweeps, cudaStream_t st);
+cudaError_t cluster_occupancy(bool gauss, int Z, int K, int threads, int smem, int *clusters);
 int fused_threads(int N);
 int fused_threads_wide(int N);
 // uint32 words of per-CTA scratch of the wide layout (2 N cluster words, 32

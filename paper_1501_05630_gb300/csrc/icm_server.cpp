@@ -168,6 +168,16 @@ icm_status create_class(icm_server *s, const Request &r, ShapeClass **out)
     icm_status st = icm_batch_create(c->ctx, r.lattice, r.L, r.disorder, n, J.data(), nullptr, nullptr, r.T.data(),
                                      n_T, r.T_icm, r.seed, 0, &c->batch);
     if (st == ICM_OK) st = icm_batch_set_active(c->batch, -1, 0);
+    if (st == ICM_OK) {
+        // a class of large instances (one wide CTA each) runs each instance on
+        // a thread-block cluster instead: lower latency per request
+        int32_t th = 0, cps = 0, grid = 0, smem = 0;
+        int64_t launches = 0;
+        st = icm_batch_info(c->batch, &th, &cps, &grid, &smem, &launches);
+        if (st == ICM_OK && th > 128 && icm_batch_set_cluster(c->batch, 8, 512) != ICM_OK &&
+            icm_batch_set_cluster(c->batch, 4, 512) != ICM_OK)
+            st = icm_batch_set_cluster(c->batch, 0, th);          // keep the one-CTA layout
+    }
     if (st != ICM_OK) {
         icm_status e = from_ctx(s, c->ctx, st, "class batch");
         destroy_class(c.get());

@@ -31,6 +31,7 @@
 //  * Observables: vertical (bit-sliced) counters of q_i = -1 sites and of
 //    bonds with q_i q_j = -1 for every pair at once.
 #include "icm_internal.h"
+#include "icm_device.cuh"
 
 #include <cstdio>
 #include <type_traits>
@@ -74,121 +75,6 @@ static __device__ unsigned long long g_icm_phase_cycles[16];   // one table per 
 namespace icm {
 
 namespace {
-
-constexpr uint32_t kFull = 0xffffffffu;
-
-// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, multipliers
-// 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
-__device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                         uint32_t k1, uint32_t (&o)[4])
-{
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        const uint64_t m0 = (uint64_t)c0 * 0xD2511F53ull;
-        const uint64_t m1 = (uint64_t)c2 * 0xCD9E8D57ull;
-        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1;
-        c1 = (uint32_t)m1;
-        c3 = (uint32_t)m0;
-        c0 = n0;
-        c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
-}
-
-// Two Philox4x32-10 blocks with counters {c0, c1, c2, c3} and {c0, c1, c2+1, c3},
-// written as two independent chains so that the scheduler can interleave them.
-__device__ __forceinline__ void philox10x2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                           uint32_t k1, uint32_t (&o)[4], uint32_t (&p)[4])
-{
-    uint32_t a0 = c0, a1 = c1, a2 = c2, a3 = c3;
-    uint32_t b0 = c0, b1 = c1, b2 = c2 + 1u, b3 = c3;
-#pragma unroll
-    for (int i = 0; i < 10; ++i) {
-        const uint64_t ma0 = (uint64_t)a0 * 0xD2511F53ull, ma1 = (uint64_t)a2 * 0xCD9E8D57ull;
-        const uint64_t mb0 = (uint64_t)b0 * 0xD2511F53ull, mb1 = (uint64_t)b2 * 0xCD9E8D57ull;
-        const uint32_t na0 = (uint32_t)(ma1 >> 32) ^ a1 ^ k0, na2 = (uint32_t)(ma0 >> 32) ^ a3 ^ k1;
-        const uint32_t nb0 = (uint32_t)(mb1 >> 32) ^ b1 ^ k0, nb2 = (uint32_t)(mb0 >> 32) ^ b3 ^ k1;
-        a1 = (uint32_t)ma1; a3 = (uint32_t)ma0; a0 = na0; a2 = na2;
-        b1 = (uint32_t)mb1; b3 = (uint32_t)mb0; b0 = nb0; b2 = nb2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
-    }
-    o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3;
-    p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3;
-}
-
-__device__ __forceinline__ float ex2_approx(float x)
-{
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Sum of a[j] over the 32 lanes, delivered to lane j (31 shuffles).
-template <typename T>
-__device__ __forceinline__ T transpose_reduce(T (&a)[32], int lane)
-{
-#pragma unroll
-    for (int s = 16; s >= 1; s >>= 1) {
-        const bool upper = (lane & s) != 0;
-#pragma unroll
-        for (int j = 0; j < s; ++j) {
-            const T send = upper ? a[j] : a[j + s];
-            const T keep = upper ? a[j + s] : a[j];
-            a[j] = keep + __shfl_xor_sync(kFull, send, s);
-        }
-    }
-    return a[0];
-}
-
-// Sum of a[j] over the 32 lanes, delivered to lanes 2j and 2j+1 (16 shuffles).
-template <typename T>
-__device__ __forceinline__ T transpose_reduce16(T (&a)[16], int lane)
-{
-#pragma unroll
-    for (int s = 8; s >= 1; s >>= 1) {
-        const bool upper = (lane & (2 * s)) != 0;
-#pragma unroll
-        for (int j = 0; j < s; ++j) {
-            const T send = upper ? a[j] : a[j + s];
-            const T keep = upper ? a[j + s] : a[j];
-            a[j] = keep + __shfl_xor_sync(kFull, send, 2 * s);
-        }
-    }
-    return a[0] + __shfl_xor_sync(kFull, a[0], 1);
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_sum_lane0(T v)
-{
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) v += __shfl_down_sync(kFull, v, o);
-    return v;
-}
-
-// Add one word to NPL bit-planes of per-bit counters (vertical counters).
-template <int NPL>
-__device__ __forceinline__ void vadd(uint32_t (&pl)[NPL], uint32_t w)
-{
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) {
-        const uint32_t c = pl[i] & w;
-        pl[i] ^= w;
-        w = c;
-    }
-}
-
-template <int NPL>
-__device__ __forceinline__ int vget(const uint32_t (&pl)[NPL], int bit)
-{
-    int v = 0;
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) v |= (int)((pl[i] >> bit) & 1u) << i;
-    return v;
-}
 
 struct Sm {
     uint32_t *s;
@@ -245,21 +131,6 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.acc64 = (long long *)(base + L.acc64);
     S.nmeas = (long long *)(base + L.nmeas);
     return S;
-}
-
-// Per bit lane: u >= k, where u's binary digits are the bit-planes c3 c2 c1 c0
-// and k (0..15) is the same for all lanes.
-__device__ __forceinline__ uint32_t ge_bitsliced(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int k)
-{
-    const uint32_t c[4] = {c0, c1, c2, c3};
-    uint32_t gt = 0u, eq = ~0u;
-#pragma unroll
-    for (int i = 3; i >= 0; --i) {
-        const uint32_t kb = 0u - (uint32_t)((k >> i) & 1);
-        gt |= eq & c[i] & ~kb;
-        eq &= ~(c[i] ^ kb);
-    }
-    return gt | eq;
 }
 
 // Neighbour positions of position p (padding entries repeat p), read as

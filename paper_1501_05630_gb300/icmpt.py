@@ -49,7 +49,7 @@ EXPORTS = [
     "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
     "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
     "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
-    "icm_server_clock", "icm_server_cancel",
+    "icm_server_clock", "icm_server_cancel", "icm_batch_set_cluster", "icm_batch_cluster",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
@@ -417,6 +417,15 @@ class Batch:
 
     def set_threads(self, threads: int):
         self.ctx.check(self._lib.icm_batch_set_threads(self._h, int(threads)))
+
+    def set_cluster(self, K: int, threads: int):
+        """One instance per thread-block cluster of K CTAs (K = 0: one CTA per instance)."""
+        self.ctx.check(self._lib.icm_batch_set_cluster(self._h, int(K), int(threads)))
+
+    def cluster(self) -> int:
+        k = ctypes.c_int32()
+        self.ctx.check(self._lib.icm_batch_cluster(self._h, ctypes.byref(k)))
+        return k.value
 
     def autotune(self, sweeps: int = 16):
         """Pick the fastest CTA width; the batch's state is left unchanged."""

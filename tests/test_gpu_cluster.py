@@ -1,0 +1,140 @@
+"""The thread-block-cluster layout: one instance per cluster of K CTAs that
+share its sites through distributed shared memory.
+
++-J: the same chain as the oracle, bit for bit, sweep by sweep (spins,
+integer energies, step-2a decisions, seeds, cluster sizes, PT decisions,
+observables), for K = 2, 4, 8 and several CTA widths, up to 2D L=128.
+Gaussian: energy conservation of every cluster move, energies consistent
+with the spins, and the same equilibrium as the one-CTA layout.  A captured
+group with a cluster batch equals its separate launches; a batch that
+becomes diluted leaves the cluster layout by itself.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1501_05630_gb300 import inputs as I
+from test_gpu_parity import _compare_sweeps, _setup, icm  # noqa: F401  (fixture)
+
+pytestmark = pytest.mark.gpu
+
+
+def _cluster(K, threads):
+    def setup(b):
+        b.set_cluster(K, threads)
+        assert b.cluster() == K and b.info()["threads"] == threads
+    return setup
+
+
+@pytest.mark.parametrize("kind,L,nT,T_hi,T_icm,n_inst,K,threads", [
+    (O.CUBIC3D, 8, 24, 2.0, 1.0, 3, 2, 128),      # two spin words, slabs of 4 planes
+    (O.CUBIC3D, 8, 12, 2.0, 1.0, 2, 8, 32),       # one plane per CTA: every z-neighbour remote
+    (O.SQUARE2D, 16, 16, 1.5, 1.0, 3, 4, 64),
+    (O.CHIMERA, 4, 30, 3.0, 1.5, 2, 2, 32),       # per-site degrees, padded neighbour lists
+    (O.SQUARE2D, 32, 32, 1.5, 1.0, 1, 8, 256),    # 64 replicas
+])
+def test_cluster_pmj_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, n_inst, K, threads):
+    _compare_sweeps(icm, kind, L, nT, 0.2, T_hi, T_icm, n_inst, 30, 0xC1 + L + K, setup=_cluster(K, threads))
+
+
+def test_cluster_2d_L128_64_replicas(icm):
+    _compare_sweeps(icm, O.SQUARE2D, 128, 32, 0.2, 1.5, 1.0, 1, 6, 0x1502, check_every=3,
+                    setup=_cluster(8, 1024))
+
+
+def test_cluster_schedule_and_multi_sweep_launches(icm):
+    _compare_sweeps(icm, O.CUBIC3D, 8, 10, 0.2, 2.0, 1.0, 2, 40, 77, check_every=7, setup=_cluster(4, 64),
+                    icm_every=3, swap_every=2, t_meas=11)
+
+
+def test_cluster_gauss_conservation_and_consistency(icm):
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 24)
+    seed = 0x15010563000000C1
+    n = 6
+    g, J, s0, ids = _setup(O.CUBIC3D, 16, I.GAUSS, n, T, seed)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 16, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_cluster(8, 256)
+    b.set_schedule(trace=1)
+    scale = np.abs(J).astype(np.float64).sum(1)
+    moves = 0
+    for rep in range(4):
+        b.run(5)
+        tr = b.read_trace()
+        k = tr["n_pre"] >= 0
+        moves += int((tr["csize"] > 0).sum())
+        err = np.abs(tr["esum_after"] - tr["esum_before"])[k]
+        assert np.all(err <= 1e-5 * np.repeat(scale[:, None], 24, 1)[k])
+        spins, E = b.read_spins(), b.read_energies()
+        for a in range(n):
+            e_ref = -np.einsum("b,rb->r", J[a].astype(np.float64),
+                               (spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64))
+            assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a])
+    assert moves > 50
+
+
+def test_cluster_gauss_equilibrium_equals_one_cta_layout(icm):
+    """3D L=8 Gaussian, 96 instances: per-temperature energy and link overlap
+    of the cluster layout agree with the one-CTA layout's (paired by instance)."""
+    icmpt, ctx = icm
+    T = I.ladder(0.4, 2.0, 8)
+    seed = 515
+    n = 96
+    g, J, s0, ids = _setup(O.CUBIC3D, 8, I.GAUSS, n, T, seed)
+    out = []
+    for K in (0, 4):
+        b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.GAUSS, J, T, 1.0, seed, spins=s0)
+        if K:
+            b.set_cluster(K, 64)
+        b.set_schedule(t_meas=1000)
+        b.run(4000)
+        o = b.read_observables()
+        m = o.n_meas[:, None].astype(np.float64)
+        out.append((o.accE / (2 * g.N * m), 1 - 2 * o.acc_d / (g.Nb * m)))
+        b.close()
+    for i in range(2):
+        d = out[1][i] - out[0][i]
+        mu, se = d.mean(0), d.std(0, ddof=1) / math.sqrt(n)
+        assert np.all(np.abs(mu) <= 3.5 * se + 1e-9), (i, mu, se)
+
+
+def test_group_with_cluster_batch_equals_separate_launches(icm):
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 12)
+    batches = []
+    for rep in range(2):
+        row = []
+        for L, n, K in ((8, 5, 4), (4, 7, 0)):
+            g, J, s0, ids = _setup(O.CUBIC3D, L, I.PM_J, n, T, 31 + L)
+            b = icmpt.Batch(ctx, O.CUBIC3D, L, I.PM_J, J, T, 1.0, 31 + L, spins=s0)
+            if K:
+                b.set_cluster(K, 64)
+            row.append(b)
+        batches.append(row)
+    grp = icmpt.Group(ctx, batches[0], sweeps_per_launch=5)
+    grp.run(3)
+    ctx.sync()
+    for b in batches[1]:
+        b.run(15)
+    for a, b in zip(*batches):
+        assert np.array_equal(a.read_spins(), b.read_spins())
+        assert np.array_equal(a.read_energies(), b.read_energies())
+    grp.close()
+
+
+def test_dilution_leaves_cluster_layout(icm):
+    icmpt, ctx = icm
+    T = I.ladder(0.3, 2.0, 8)
+    g, J, s0, ids = _setup(O.CUBIC3D, 8, I.PM_J, 2, T, 5)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.PM_J, J, T, 1.0, 5, spins=s0)
+    b.set_cluster(4, 64)
+    b.run(2)
+    Jd = I.dilute(J, 0.2, 5, ids)
+    b.load(couplings=Jd)
+    assert b.cluster() == 0
+    b.run(2)
+    with pytest.raises(icmpt.IcmError):
+        b.set_cluster(4, 64)
+    b.close()

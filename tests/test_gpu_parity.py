@@ -47,7 +47,7 @@ TRACE_KEYS = ("n_pre", "flip2a", "seed_site", "csize", "esum_before", "esum_afte
 
 
 def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, check_every=1, threads=None,
-                    **sched):
+                    setup=None, **sched):
     icmpt, ctx = icm
     T = I.ladder(T_lo, T_hi, nT)
     g, J, s0, ids = _setup(kind, L, I.PM_J, n_inst, T, seed)
@@ -55,6 +55,8 @@ def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, c
     if threads is not None:
         b.set_threads(threads)
         assert b.info()["threads"] == threads
+    if setup is not None:
+        setup(b)
     b.set_schedule(trace=1, **sched)
     refs = [_oracle(g, J[a], s0[a], T, T_icm, seed, ids[a], I.PM_J, **sched) for a in range(n_inst)]
     done = 0
