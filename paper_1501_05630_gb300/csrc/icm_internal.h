@@ -37,6 +37,7 @@ struct SmemLayout {
     int swap_list;  // int32 [2][32]   per run: (source bit << 8) | destination bit
     int swap_n;     // int32 [2]       runs per copy
     int swap_mask;  // uint64 [2]      bits moving down one slot, per copy
+    int swap_tab;   // [3][32]         per neighbouring pair k: dbeta log2(e) (float), +-J table offset and length
     int flipw;      // uint32 [2]      step-2a reversal masks of the two words
     int icm_seed;   // int32 [32]      seed position per ICM pair (-1: none)
     int icm_esum;   // float or int32 [32]  E_a + E_b of each ICM pair before the move

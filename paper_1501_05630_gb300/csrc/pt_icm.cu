@@ -92,6 +92,8 @@ struct Sm {
     int *swap_list;
     int *swap_n;
     uint64_t *swap_mask;
+    float *sw_dbl;       // [32] (beta_k - beta_{k+1}) log2(e)
+    int *sw_off, *sw_len;  // [32] +-J swap threshold table of pair k
     uint32_t *flipw;
     int *icm_seed;
     void *icm_esum_raw;
@@ -122,6 +124,9 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.swap_list = (int *)(base + L.swap_list);
     S.swap_n = (int *)(base + L.swap_n);
     S.swap_mask = (uint64_t *)(base + L.swap_mask);
+    S.sw_dbl = (float *)(base + L.swap_tab);
+    S.sw_off = (int *)(base + L.swap_tab + 128);
+    S.sw_len = (int *)(base + L.swap_tab + 256);
     S.flipw = (uint32_t *)(base + L.flipw);
     S.icm_seed = (int *)(base + L.icm_seed);
     S.icm_esum_raw = base + L.icm_esum;
@@ -644,18 +649,22 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
         // Accepted swaps (k,k+1), (k+1,k+2), ..., (m,m+1) in a row form a run:
         // the configuration at k bubbles up to m+1 and those at k+1..m+1 move
         // down one slot.  Record, per copy, the bits that move down (D) and one
-        // (source, destination) bit pair per run.
+        // (source, destination) bit pair per run.  The energy of the
+        // configuration now at k is carried in a register (the one that came
+        // up, or the one that was there); position k+1 has not been written
+        // yet in this pass, so its energy is read as it was.
         uint64_t D = 0;
         int nrun = 0, run_start = -1;
+        ET ek = E[c];
         for (int k = 0; k <= np; ++k) {
             bool acc = false;
             if (k < np) {
                 const int ra = 2 * k + c, rb = ra + 2;
-                const ET ek = E[ra], ek1 = E[rb];
+                const ET ek1 = E[rb];
                 const uint32_t x = S.swap_x[c * 32 + k];
                 if constexpr (GAUSS) {
                     // log2(e) (beta_k - beta_{k+1}) (E_k - E_{k+1}); accept iff >= 0 or u < 2^delta
-                    const float delta = P.dbeta_l2e[k] * (ek - ek1);
+                    const float delta = S.sw_dbl[k] * (ek - ek1);
                     acc = (delta >= 0.f) || ((float)(x >> 8) * (1.0f / 16777216.0f) < ex2_approx(delta));
                 } else {
                     const int dE = ek - ek1;
@@ -663,14 +672,16 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
                         acc = true;
                     } else {
                         const int d = (-dE) >> 1;
-                        acc = d >= 1 && d <= P.swap_len[k] && x < P.thr_swap[P.swap_off[k] + d - 1];
+                        acc = d >= 1 && d <= S.sw_len[k] && x < P.thr_swap[S.sw_off[k] + d - 1];
                     }
                 }
                 if (acc) {
                     E[ra] = ek1;
-                    E[rb] = ek;
+                    E[rb] = ek;                      // ek moves up and stays the carried energy
                     D |= 1ull << (rb);
                     if (run_start < 0) run_start = k;
+                } else {
+                    ek = ek1;
                 }
                 if (trace) P.tr_swap[((size_t)slot * 2 + c) * np + k] = (uint8_t)acc;
             }
@@ -798,6 +809,14 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
     }
     S.tie = 0;
     S.nb = P.Nb;
+    for (int k = tid; k < nT - 1; k += nth) {
+        if constexpr (GAUSS) {
+            S.sw_dbl[k] = P.dbeta_l2e[k];
+        } else {
+            S.sw_off[k] = P.swap_off[k];
+            S.sw_len[k] = P.swap_len[k];
+        }
+    }
     if constexpr (GAUSS) {
         for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
     } else {
@@ -1144,6 +1163,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.swap_list = take(2 * 32 * 4, 16);
     L.swap_n = take(2 * 4, 16);
     L.swap_mask = take(2 * 8, 16);
+    L.swap_tab = take(3 * 32 * 4, 16);
     L.flipw = take(2 * 4, 16);
     L.icm_seed = take(32 * 4, 16);
     L.icm_esum = take(32 * 4, 16);
