@@ -406,6 +406,55 @@ def run_thermalization(args):
     print(json.dumps(out))
 
 
+# Fig. 1 systems: Table I ladders and sizes (N_c cluster temperatures), Gaussian
+# disorder; p_c = site-percolation thresholds the paper quotes
+FIG1 = [
+    dict(name="2D", lattice=I.SQUARE2D, Ls=(16, 24, 32), T=(0.212, 1.6325, 30), n_c=30, p_c=0.592),
+    dict(name="chimera", lattice=I.CHIMERA, Ls=(4, 6, 8, 10, 12), T=(0.212, 1.6325, 30), n_c=19, p_c=0.3866),
+    dict(name="3D", lattice=I.CUBIC3D, Ls=(4, 6, 8, 10, 12), T=(0.42, 1.8, 26), n_c=13, p_c=0.311),
+]
+
+
+def run_fig1(args):
+    """Fraction p(T) of potential cluster sites for the Table I systems (Fig. 1
+    at reduced instance counts) and the temperature where it reaches the
+    lattice's site-percolation threshold."""
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    from paper_1501_05630_gb300.experiments import cluster_fraction, crossing_temperature
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = icmpt.Context(0)
+    sweeps = 1 << args.log2_max_fig1
+    out = {"metric": "fig1_crossing_temperature", "unit": "T at p(T) = p_c (largest N)", "higher_is_better": None,
+           "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "fig1", "instances": args.instances, "sweeps": sweeps, "t_meas": sweeps // 2,
+                      "disorder": "Gaussian", "method": "PT + ICM at the lowest N_c temperatures (Table I)"},
+           "systems": {}}
+    t0 = time.perf_counter()
+    updates = 0
+    for sysd in FIG1:
+        T = I.ladder(*sysd["T"])
+        T_icm = float(T[sysd["n_c"] - 1]) + 1e-9
+        res = {"p_c": sysd["p_c"], "sizes": {}}
+        for L in sysd["Ls"]:
+            N, Nb = icmpt.lattice_size(sysd["lattice"], L)
+            seed = 0x1501056300000010 + L
+            J = I.couplings(Nb, I.GAUSS, seed, range(args.instances))
+            s0 = I.initial_spins(N, 2 * len(T), seed, range(args.instances))
+            c = cluster_fraction(ctx, sysd["lattice"], L, I.GAUSS, J, s0, T, T_icm, seed, sweeps, sweeps // 2)
+            updates += args.instances * N * 2 * len(T) * sweeps
+            res["sizes"][N] = {"p": [round(float(x), 4) for x in c.p], "se": [round(float(x), 4) for x in c.se],
+                               "T_cross": crossing_temperature(c, sysd["p_c"]), "p_max": round(float(c.p.max()), 4)}
+        res["T"] = [round(float(x), 4) for x in T]
+        out["systems"][sysd["name"]] = res
+    largest = {k: v["sizes"][max(v["sizes"])]["T_cross"] for k, v in out["systems"].items()}
+    out["value"] = largest
+    out["wall_s"] = time.perf_counter() - t0
+    out["updates_per_ns"] = updates / out["wall_s"] / 1e9
+    print(json.dumps(out))
+
+
 def run_annealing(args):
     """Simulated annealing with and without isoenergetic cluster moves at
     equal sweeps (the ground-state use the paper proposes): mean final energy
@@ -487,7 +536,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation", "thermalization",
-                                                                   "annealing"])
+                                                                   "annealing", "fig1"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -498,6 +547,7 @@ def main():
     ap.add_argument("--masks", type=int, default=40000)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--log2-max", type=int, default=17)
+    ap.add_argument("--log2-max-fig1", type=int, default=14, help="fig1: sweeps = 2^this, measured over the second half")
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--ref-sweeps", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
@@ -511,6 +561,10 @@ def main():
     if args.workload == "thermalization":
         if int(os.environ.get("RANK", "0")) == 0:
             run_thermalization(args)
+        return
+    if args.workload == "fig1":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_fig1(args)
         return
     if args.workload == "annealing":
         if int(os.environ.get("RANK", "0")) == 0:

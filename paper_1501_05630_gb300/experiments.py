@@ -1,4 +1,14 @@
-"""Thermalization experiments of the paper at reduced scale (Fig. 2, Fig. 3).
+"""Experiments of the paper at reduced scale: the fraction of potential
+cluster sites (Fig. 1), thermalization (Fig. 2, Fig. 3) and simulated
+annealing with cluster moves.
+
+Fig. 1: p(T) is the fraction of sites with negative overlap q_i = -1 between
+the two replicas at temperature T, after step 2a (so p <= 1/2), averaged over
+the measured sweeps and then over disorder instances.  Clusters of the
+isoenergetic move percolate once p exceeds the site-percolation threshold
+p_c of the lattice; `crossing_temperature` locates where p(T) reaches p_c.
+
+Thermalization:
 
 For one method -- plain parallel tempering (no cluster moves), PT with the
 isoenergetic cluster moves (ICM at T_k <= T_icm, with step 2a), or the
@@ -94,3 +104,40 @@ def anneal(ctx, lattice: int, L: int, disorder: int, couplings, spins, T_hi: flo
         b.set_temperatures([T], min(T_icm, 1e300))
         b.run(sweeps_per_step)
     return b
+
+
+# ----------------------------------------------------------------------------- Fig. 1
+@dataclass
+class FractionCurve:
+    T: np.ndarray          # temperatures, ascending
+    p: np.ndarray          # disorder average of <min(n, N - n)> / N
+    se: np.ndarray         # standard error over instances
+
+
+def cluster_fraction(ctx, lattice: int, L: int, disorder: int, couplings, spins, T, T_icm: float, seed: int,
+                     sweeps: int, t_meas: int, instance_ids=None) -> FractionCurve:
+    """p(T) of a batch of instances run with PT and cluster moves (steps 1-3)
+    for `sweeps` sweeps, measured from sweep t_meas on."""
+    b = icmpt.Batch(ctx, lattice, L, disorder, couplings, T, T_icm, seed, spins=spins, instance_ids=instance_ids)
+    b.set_schedule(t_meas=t_meas)
+    b.run(sweeps)
+    o = b.read_observables(hist=False)
+    b.close()
+    per = o.acc_pmin / (b.N * np.maximum(o.n_meas, 1)[:, None].astype(np.float64))
+    n = per.shape[0]
+    se = per.std(0, ddof=1) / np.sqrt(n) if n > 1 else np.zeros(per.shape[1])
+    return FractionCurve(np.asarray(T, dtype=np.float64), per.mean(0), se)
+
+
+def crossing_temperature(curve: FractionCurve, p_c: float):
+    """The temperature at which p(T) first reaches p_c, going up in T (linear
+    interpolation between ladder points), or None if p stays below p_c."""
+    T, p = curve.T, curve.p
+    for k in range(len(T)):
+        if p[k] >= p_c:
+            if k == 0:
+                return float(T[0])
+            f = (p_c - p[k - 1]) / (p[k] - p[k - 1])
+            return float(T[k - 1] + f * (T[k] - T[k - 1]))
+    return None
+

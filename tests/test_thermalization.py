@@ -102,3 +102,40 @@ def test_annealing_equals_oracle(env, icm):
         assert np.array_equal(spins[a], r.s)
         assert np.array_equal(E[a], r.E)
     b.close()
+
+
+# ----------------------------------------------------------------------------- Fig. 1
+def test_crossing_temperature_interpolates():
+    from paper_1501_05630_gb300.experiments import FractionCurve, crossing_temperature
+    c = FractionCurve(np.array([0.5, 1.0, 1.5, 2.0]), np.array([0.1, 0.2, 0.4, 0.45]), np.zeros(4))
+    assert crossing_temperature(c, 0.3) == pytest.approx(1.25)
+    assert crossing_temperature(c, 0.05) == 0.5
+    assert crossing_temperature(c, 0.5) is None
+
+
+@pytest.mark.gpu
+def test_cluster_fraction_equals_oracle_and_stays_below_2d_threshold():
+    """p(T) of a +-J batch equals the oracle's per-instance averages (bit-exact
+    sums); for 2D the fraction never reaches p_c = 0.592 (Fig. 1, top panel)
+    and approaches 1/2 at high T."""
+    import torch
+    from oracle import oracle as O
+    from paper_1501_05630_gb300 import build, icmpt
+    from paper_1501_05630_gb300.experiments import cluster_fraction
+    build.build()
+    torch.cuda.set_device(0)
+    ctx = icmpt.Context(0)
+    T = I.ladder(0.3, 4.0, 8)
+    g = O.Geometry(O.SQUARE2D, 8)
+    n, sweeps, t_meas = 6, 600, 200
+    J = I.couplings(g.Nb, I.PM_J, 12, range(n))
+    s0 = I.initial_spins(g.N, 16, 12, range(n))
+    c = cluster_fraction(ctx, O.SQUARE2D, 8, I.PM_J, J, s0, T, 1.0, 12, sweeps, t_meas)
+    per = []
+    for a in range(n):
+        r = O.Instance(g, J[a].astype(np.float64), T, s0[a], pm=True, T_icm=1.0, seed=12, inst=a, t_meas=t_meas)
+        r.run(sweeps)
+        per.append(r.observables()["p"])
+    assert np.allclose(c.p, np.mean(per, axis=0), rtol=0, atol=1e-12)
+    assert np.all(c.p < 0.592) and c.p[-1] > 0.4
+    ctx.close()
