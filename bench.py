@@ -70,21 +70,27 @@ def kernel_source_digest() -> str:
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per fused-kernel launch from the committed ncu summary of this
-    workload, or None when the kernel sources changed since that capture."""
+def recorded_counter(workload: str, key: str):
+    """A counter of the committed ncu summary of this workload's fused kernel
+    (traffic_bytes_per_launch, instructions_per_update), or None when the
+    kernel sources changed since that capture."""
     path = os.path.join(ROOT, "profiles", f"fused_kernel_{workload}.md")
     try:
         vals = {}
         for line in open(path):
-            if ":" in line and line.strip().startswith(("traffic_bytes_per_launch", "kernel_source_digest")):
+            if ":" in line and line.strip().startswith((key, "kernel_source_digest")):
                 k, v = line.strip().strip("`").split(":", 1)
                 vals[k.strip()] = v.strip().strip("`")
         if vals.get("kernel_source_digest") != kernel_source_digest():
             return None
-        return float(vals["traffic_bytes_per_launch"])
+        return float(vals[key])
     except Exception:
         return None
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per fused-kernel launch (see recorded_counter)."""
+    return recorded_counter(workload, "traffic_bytes_per_launch")
 
 
 def _peaks():
@@ -683,10 +689,16 @@ def main():
     per_launch_ms = ms / max(args.steps, 1) / (world if False else 1)
     achieved = updates_per_step * ops_per_update / (per_launch_ms * 1e-3) / 1e12     # Tops/s
     peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12                   # issue limit
+    # executed thread-instructions per update (ncu) give the issue utilisation
+    # beside the algorithmic fraction
+    ipu = recorded_counter(args.workload, "instructions_per_update")
+    issue_frac = (updates_per_step * ipu / (per_launch_ms * 1e-3) / 1e12) / peak if ipu else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(args.workload), "kernel": "fused_kernel",
-                "ops_per_update": ops_per_update,
-                "peak_note": f"issue limit: 152 SMs x 128 thread-instr/clk x sm_max_mhz ({peak_src}); traffic = DRAM bytes per launch"}
+                "ops_per_update": ops_per_update, "instructions_per_update": ipu, "issue_frac": issue_frac,
+                "peak_note": f"issue limit: 152 SMs x 128 thread-instr/clk x sm_max_mhz ({peak_src}); "
+                             "frac = algorithmic ops, issue_frac = executed instructions (ncu); "
+                             "traffic = DRAM bytes per launch"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
