@@ -27,26 +27,35 @@ def _nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+# Checked build: every guarded index of the fused kernel is tested against its
+# bound and an out-of-range index is recorded (icm_debug_check) and replaced by
+# 0, so that the access stays in bounds.  Built apart, never on the product path.
+CHECKED_BUILD = os.path.join(PKG, "_build_checked")
+CHECKED_LIB = os.path.join(CHECKED_BUILD, "libicmpt.so")
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "icmpt.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, checked: bool = False) -> str:
+    out_dir, lib = (CHECKED_BUILD, CHECKED_LIB) if checked else (BUILD, LIB)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     objs = []
     cmds = []
+    defs = ["-DICM_CHECKED"] if checked else []
     for src in SOURCES:
-        obj = os.path.join(BUILD, src + ".o")
+        obj = os.path.join(out_dir, src + ".o")
         objs.append(obj)
         extra = ["-x", "cu"] if src.endswith(".cu") else []
-        cmds.append([nvcc, *ARCH, *FLAGS, *extra, "-c", os.path.join(CSRC, src), "-o", obj])
+        cmds.append([nvcc, *ARCH, *FLAGS, *defs, *extra, "-c", os.path.join(CSRC, src), "-o", obj])
     if verbose:
         cmds[0].insert(1, "-Xptxas=-v")
     with cf.ThreadPoolExecutor(len(cmds)) as ex:
@@ -55,12 +64,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 raise RuntimeError("nvcc failed:\n" + r.stdout + r.stderr)
             if verbose and r.stderr:
                 print(r.stderr)
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     r = subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -10,6 +10,29 @@ namespace {
 
 constexpr uint32_t kFull = 0xffffffffu;
 
+// Checked builds (-DICM_CHECKED): ICM_IDX(i, n, site) tests a data-dependent
+// index against its bound.  An index out of range is counted in g_icm_check
+// (count, then the site code, index and bound of the first one) and replaced
+// by 0, so the access stays inside the array and the kernel runs on; the
+// host reads the word with icm_debug_check.  In normal builds ICM_IDX is the
+// index itself.  (The substitute for a memory checker on this pool.)
+#ifdef ICM_CHECKED
+static __device__ unsigned int g_icm_check[4];
+__device__ __forceinline__ int icm_guard(int idx, int bound, int site)
+{
+    if ((unsigned)idx < (unsigned)bound) return idx;
+    if (atomicAdd(&g_icm_check[0], 1u) == 0u) {
+        g_icm_check[1] = (unsigned)site;
+        g_icm_check[2] = (unsigned)idx;
+        g_icm_check[3] = (unsigned)bound;
+    }
+    return 0;
+}
+#define ICM_IDX(i, n, site) icm_guard((int)(i), (int)(n), (site))
+#else
+#define ICM_IDX(i, n, site) (i)
+#endif
+
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, multipliers
 // 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
 __device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,

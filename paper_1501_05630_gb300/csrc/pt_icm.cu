@@ -51,6 +51,8 @@ cudaError_t fused_occupancy_pmj(int Z, bool wide, int threads, int smem, int *ct
 cudaError_t fused_occupancy_gauss(int Z, bool wide, int threads, int smem, int *ctas);
 int debug_phase_cycles_pmj(unsigned long long *out, int reset);
 int debug_phase_cycles_gauss(unsigned long long *out, int reset);
+int debug_check_pmj(unsigned int *out, int reset);
+int debug_check_gauss(unsigned int *out, int reset);
 }  // namespace icm
 
 // Optional per-phase cycle counters (compile with -DICM_PHASE_TIMERS): thread 0
@@ -189,8 +191,8 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             float Jsum = 0.f;
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                nw[d] = sg[q[d]] >> sh0;
-                const float J = S.Jd[p * Z + d];
+                nw[d] = sg[ICM_IDX(q[d], N, 1)] >> sh0;
+                const float J = S.Jd[ICM_IDX(p * Z + d, N * Z, 2)];
                 Jsum += J;
                 J2[d] = 2.f * J;
             }
@@ -229,12 +231,12 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             }
         } else {
             uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;   // bit-planes of u = # unsatisfied bonds
-            const uint32_t jb = S.Jb[p];
+            const uint32_t jb = S.Jb[ICM_IDX(p, N, 3)];
             int q[Z];
             load_nbrs<Z>(S.nbr, p, q);
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                const uint32_t u = sw0 ^ sg[q[d]] ^ (0u - ((jb >> d) & 1u));
+                const uint32_t u = sw0 ^ sg[ICM_IDX(q[d], N, 1)] ^ (0u - ((jb >> d) & 1u));
                 const uint32_t t0 = c0 & u;
                 c0 ^= u;
                 const uint32_t t1 = c1 & t0;
@@ -251,7 +253,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             c1 >>= sh0;
             c2 >>= sh0;
             c3 >>= sh0;
-            const int z = (!DIL && P.const_z) ? P.const_z : (int)S.zdeg[p];   // degree = bonds present
+            const int z = (!DIL && P.const_z) ? P.const_z : (int)S.zdeg[ICM_IDX(p, N, 3)];   // degree = bonds present
             // m = z - 2u <= 0  <=>  u >= ceil(z/2): always accepted; on a diluted
             // instance only m < 0 (u >= floor(z/2) + 1), m = 0 takes the 1/2 entry
             if constexpr (DIL) {
@@ -275,7 +277,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                                             (((c3 >> b) & 1u) << 3));
                         const int m = z - 2 * u;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
-                        const uint32_t th = thr[b * TS + (m > 0 ? m : 0)];
+                        const uint32_t th = thr[b * TS + ICM_IDX(m > 0 ? m : 0, TS, 4)];
                         flip |= (uint32_t)(xr < th) << b;
                         acc[b] += ((flip >> b) & 1u) ? m : -m;
                     }
@@ -287,7 +289,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
     if (COLOR == 1) {   // energies: every bond touches exactly one colour-1 site
         const ET v = transpose_reduce16(acc, lane);
         const int r = rbase + (lane >> 1);
-        if (!(lane & 1) && r < P.R) ((ET *)S.Epart)[warp * P.R + r] = v;
+        if (!(lane & 1) && r < P.R) ((ET *)S.Epart)[ICM_IDX(warp * P.R + r, (nth >> 5) * (P.R > 32 ? P.R : 32), 5)] = v;
     }
 }
 
@@ -336,8 +338,8 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
                 float Jsum = 0.f;
 #pragma unroll
                 for (int d = 0; d < Z; ++d) {
-                    nw[d] = sg[q[d]];
-                    const float J = S.Jd[p * Z + d];
+                    nw[d] = sg[ICM_IDX(q[d], N, 6)];
+                    const float J = S.Jd[ICM_IDX(p * Z + d, N * Z, 2)];
                     Jsum += J;
                     J2[d] = 2.f * J;
                 }
@@ -353,10 +355,10 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
                 }
             } else {
                 uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-                const uint32_t jb = S.Jb[p];
+                const uint32_t jb = S.Jb[ICM_IDX(p, N, 3)];
 #pragma unroll
                 for (int d = 0; d < Z; ++d) {
-                    const uint32_t u = sw ^ sg[q[d]] ^ (0u - ((jb >> d) & 1u));
+                    const uint32_t u = sw ^ sg[ICM_IDX(q[d], N, 6)] ^ (0u - ((jb >> d) & 1u));
                     const uint32_t t0 = c0 & u;
                     c0 ^= u;
                     const uint32_t t1 = c1 & t0;
@@ -378,7 +380,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
             }
         }
         const ET v = transpose_reduce16(acc, lane);
-        if (!(lane & 1)) part[warp * 32 + 16 * g + (lane >> 1)] = v;
+        if (!(lane & 1)) part[ICM_IDX(warp * 32 + 16 * g + (lane >> 1), (nth >> 5) * 32, 7)] = v;
     }
 }
 
@@ -418,7 +420,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         }
         for (int k = 0; k < nicm; ++k) {
             const uint32_t word = __ballot_sync(kFull, ((k < 16 ? q0 : q1) >> (2 * (k & 15))) & 1u);
-            if (lane == (k & 31)) S.mask[k * NW + m] = word;
+            if (lane == (k & 31)) S.mask[ICM_IDX(k * NW + m, nicm * NW, 8)] = word;
         }
     }
     for (int i = tid; i < 2 * N; i += nth) S.C[i] = 0u;
@@ -456,7 +458,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                 }
                 rank -= c;
             }
-            atomicOr(&S.C[2 * seed + (k >> 4)], 1u << (2 * (k & 15)));
+            atomicOr(&S.C[ICM_IDX(2 * seed + (k >> 4), 2 * N, 9)], 1u << (2 * (k & 15)));
         }
         S.icm_seed[k] = seed;
         esum[k] = E[2 * k] + E[2 * k + 1];
@@ -527,7 +529,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                     uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
                     for (int i = 0; i < Z / 2; ++i) {
-                        const uint2 a = C2[qn[j][i] & 0xffffu], b = C2[qn[j][i] >> 16];
+                        const uint2 a = C2[ICM_IDX(qn[j][i] & 0xffffu, N, 10)], b = C2[ICM_IDX(qn[j][i] >> 16, N, 10)];
                         nb0 |= a.x | b.x;
                         nb1 |= a.y | b.y;
                     }
@@ -572,7 +574,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                     uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
                     for (int d = 0; d < Z; ++d) {
-                        const uint2 a = C2[q[d]];
+                        const uint2 a = C2[ICM_IDX(q[d], N, 10)];
                         nb0 |= a.x;
                         nb1 |= a.y;
                     }
@@ -660,7 +662,7 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
             bool acc = false;
             if (k < np) {
                 const int ra = 2 * k + c, rb = ra + 2;
-                const ET ek1 = E[rb];
+                const ET ek1 = E[ICM_IDX(rb, P.R, 11)];
                 const uint32_t x = S.swap_x[c * 32 + k];
                 if constexpr (GAUSS) {
                     // log2(e) (beta_k - beta_{k+1}) (E_k - E_{k+1}); accept iff >= 0 or u < 2^delta
@@ -676,7 +678,7 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
                     }
                 }
                 if (acc) {
-                    E[ra] = ek1;
+                    E[ICM_IDX(ra, P.R, 11)] = ek1;
                     E[rb] = ek;                      // ek moves up and stays the carried energy
                     D |= 1ull << (rb);
                     if (run_start < 0) run_start = k;
@@ -686,7 +688,7 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
                 if (trace) P.tr_swap[((size_t)slot * 2 + c) * np + k] = (uint8_t)acc;
             }
             if (!acc && run_start >= 0) {   // run [run_start, k-1] ends
-                S.swap_list[c * 32 + nrun++] = ((2 * run_start + c) << 8) | (2 * k + c);
+                S.swap_list[c * 32 + ICM_IDX(nrun++, 32, 12)] = ((2 * run_start + c) << 8) | (2 * k + c);
                 run_start = -1;
             }
         }
@@ -747,7 +749,7 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
             for (int d = 0; d < Z; ++d) {
                 const int q = qn[d];
                 if (q == p) continue;
-                const uint32_t wq = sg[q];
+                const uint32_t wq = sg[ICM_IDX(q, N, 13)];
                 vadd(pd, qp ^ ((wq ^ (wq >> 1)) & 0x55555555u));
             }
         }
@@ -771,7 +773,7 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
         S.acc64[1 * nT + k] += (N - 2 * n) * (N - 2 * n);
         S.acc64[2 * nT + k] += n < N - n ? n : N - n;
         S.acc64[3 * nT + k] += d;
-        atomicAdd(&P.hist[((size_t)slot * nT + k) * (N + 1) + n], 1ull);
+        atomicAdd(&P.hist[((size_t)slot * nT + k) * (N + 1) + ICM_IDX(n, N + 1, 14)], 1ull);
     }
     if (threadIdx.x == 0) S.nmeas[0] += 1;
     __syncthreads();
@@ -1303,6 +1305,22 @@ cudaError_t occupancy_part(int Z, bool wide, int threads, int smem, int *ctas)
     }
 }
 
+int check_part(unsigned int *out, int reset)
+{
+#ifdef ICM_CHECKED
+    if (cudaMemcpyFromSymbol(out, g_icm_check, sizeof(unsigned int) * 4) != cudaSuccess) return -4;
+    if (reset) {
+        unsigned int z[4] = {};
+        if (cudaMemcpyToSymbol(g_icm_check, z, sizeof(z)) != cudaSuccess) return -4;
+    }
+    return 0;
+#else
+    (void)out;
+    (void)reset;
+    return -7;
+#endif
+}
+
 int phase_cycles_part(unsigned long long *out, int reset)
 {
 #ifdef ICM_PHASE_TIMERS
@@ -1330,6 +1348,7 @@ cudaError_t fused_occupancy_pmj(int Z, bool wide, int threads, int smem, int *ct
     return occupancy_part(Z, wide, threads, smem, ctas);
 }
 int debug_phase_cycles_pmj(unsigned long long *out, int reset) { return phase_cycles_part(out, reset); }
+int debug_check_pmj(unsigned int *out, int reset) { return check_part(out, reset); }
 #else
 cudaError_t launch_fused_gauss(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st)
 {
@@ -1340,10 +1359,27 @@ cudaError_t fused_occupancy_gauss(int Z, bool wide, int threads, int smem, int *
     return occupancy_part(Z, wide, threads, smem, ctas);
 }
 int debug_phase_cycles_gauss(unsigned long long *out, int reset) { return phase_cycles_part(out, reset); }
+int debug_check_gauss(unsigned int *out, int reset) { return check_part(out, reset); }
 #endif
 
 #endif  // ICM_PART
 }  // namespace icm
+
+#if ICM_PART == 0 && defined(ICM_CHECKED)
+// Checked builds: out[0] = guarded indices found out of range in the fused
+// kernels (both disorder kinds), out[1..3] = site code, index and bound of the
+// first one of the ±J part, or of the Gaussian part when the ±J part has none.
+extern "C" int icm_debug_check(unsigned int *out, int reset)
+{
+    unsigned int a[4], b[4];
+    int rc = icm::debug_check_pmj(a, reset);
+    if (!rc) rc = icm::debug_check_gauss(b, reset);
+    if (rc) return rc;
+    out[0] = a[0] + b[0];
+    for (int i = 1; i < 4; ++i) out[i] = a[0] ? a[i] : b[i];
+    return 0;
+}
+#endif
 
 #if ICM_PART == 0 && defined(ICM_PHASE_TIMERS)
 // Cycles per phase summed over CTAs and over both fused-kernel parts: 0 sweep +
