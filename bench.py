@@ -44,6 +44,11 @@ WORKLOADS = {
     "2d_pmj_L8": dict(lattice=I.SQUARE2D, L=8, disorder=I.PM_J, n_inst=1, T=(0.2, 1.5, 16), T_icm=1.0,
                       seed=0x1501056300000001,
                       desc="2D EA L=8 periodic (64 spins), +-J, 1 instance, 16 T geometric [0.2,1.5], ICM T<=1.0"),
+    # the largest 2D size of the serving menu, a few instances at a time (with --cluster: 8 SMs each)
+    "2d_pmj_L128": dict(lattice=I.SQUARE2D, L=128, disorder=I.PM_J, n_inst=20, T=(0.2, 1.5, 32), T_icm=1.0,
+                        seed=0x1501056300000008,
+                        desc="2D EA L=128 periodic (16384 spins), +-J, 20 instances, 32 T geometric [0.2,1.5], "
+                             "ICM T<=1.0"),
 }
 
 # Algorithmic integer/fp operations per spin update (the per-unit figure of the
@@ -555,6 +560,8 @@ def main():
     ap.add_argument("--log2-max", type=int, default=17)
     ap.add_argument("--log2-max-fig1", type=int, default=14, help="fig1: sweeps = 2^this, measured over the second half")
     ap.add_argument("--sweeps-per-step", type=int, default=256)
+    ap.add_argument("--cluster", type=int, default=0, help="run each instance on a thread-block cluster of K CTAs")
+    ap.add_argument("--cluster-threads", type=int, default=512)
     ap.add_argument("--ref-sweeps", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -617,6 +624,8 @@ def main():
     J_dev, s_dev = J_pin.cuda(), s_pin.cuda()
     b = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], J_dev, T, wl["T_icm"], wl["seed"],
                     spins=s_dev, instance_ids=ids)
+    if args.cluster:
+        b.set_cluster(args.cluster, args.cluster_threads)     # one instance per thread-block cluster
     info = b.info()
     S = args.sweeps_per_step
     n_icm = int(np.sum(T <= wl["T_icm"]))
@@ -661,6 +670,8 @@ def main():
     if not args.no_e2e:
         hb = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], J_pin.numpy(), T, wl["T_icm"], wl["seed"],
                          spins=s_pin.numpy(), instance_ids=ids)
+        if args.cluster:
+            hb.set_cluster(args.cluster, args.cluster_threads)
         for _ in range(2):
             hb.load(J_pin.numpy(), s_pin.numpy())
             hb.run(S)
@@ -691,10 +702,11 @@ def main():
     peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12                   # issue limit
     # executed thread-instructions per update (ncu) give the issue utilisation
     # beside the algorithmic fraction
-    ipu = recorded_counter(args.workload, "instructions_per_update")
+    ipu = None if args.cluster else recorded_counter(args.workload, "instructions_per_update")
     issue_frac = (updates_per_step * ipu / (per_launch_ms * 1e-3) / 1e12) / peak if ipu else None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak, "traffic": recorded_traffic(args.workload), "kernel": "fused_kernel",
+                "frac": achieved / peak, "traffic": None if args.cluster else recorded_traffic(args.workload),
+                "kernel": "cluster_kernel" if args.cluster else "fused_kernel",
                 "ops_per_update": ops_per_update, "instructions_per_update": ipu, "issue_frac": issue_frac,
                 "peak_note": f"issue limit: 152 SMs x 128 thread-instr/clk x sm_max_mhz ({peak_src}); "
                              "frac = algorithmic ops, issue_frac = executed instructions (ncu); "
