@@ -558,49 +558,15 @@ __device__ void cl_pt_pass(const KParams &P, const CS &S, uint32_t t, uint32_t i
         const int c = i / np, k = i % np;
         uint32_t x[4];
         philox10((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.seed_lo, P.seed_hi, x);
-        S.swap_x[c * 32 + k] = x[0];
+        if constexpr (GAUSS) S.swap_x[c * 32 + k] = pt_word_gauss(x[0]);
+        else S.swap_x[c * 32 + k] = pt_word_pmj(x[0], P.thr_swap + P.swap_off[k], P.swap_len[k], P.dbeta_l2e[k]);
     }
     __syncthreads();
-    const int second = blockDim.x > 32 ? 32 : 1;
-    if (threadIdx.x == 0 || threadIdx.x == second) {
-        ET *E = (ET *)S.E;
-        const int c = threadIdx.x == 0 ? 0 : 1;
-        uint64_t D = 0;
-        int nrun = 0, run_start = -1;
-        for (int k = 0; k <= np; ++k) {
-            bool acc = false;
-            if (k < np) {
-                const int ra = 2 * k + c, rb = ra + 2;
-                const ET ek = E[ra], ek1 = E[rb];
-                const uint32_t x = S.swap_x[c * 32 + k];
-                if constexpr (GAUSS) {
-                    const float delta = P.dbeta_l2e[k] * (ek - ek1);
-                    acc = (delta >= 0.f) || ((float)(x >> 8) * (1.0f / 16777216.0f) < ex2_approx(delta));
-                } else {
-                    const int dE = ek - ek1;
-                    if (dE >= 0) {
-                        acc = true;
-                    } else {
-                        const int d = (-dE) >> 1;
-                        acc = d >= 1 && d <= P.swap_len[k] && x < P.thr_swap[P.swap_off[k] + d - 1];
-                    }
-                }
-                if (acc) {
-                    E[ra] = ek1;
-                    E[rb] = ek;
-                    D |= 1ull << rb;
-                    if (run_start < 0) run_start = k;
-                }
-                if (trace && S.rank == 0) P.tr_swap[((size_t)slot * 2 + c) * np + k] = (uint8_t)acc;
-            }
-            if (!acc && run_start >= 0) {
-                S.swap_list[c * 32 + nrun++] = ((2 * run_start + c) << 8) | (2 * k + c);
-                run_start = -1;
-            }
-        }
-        S.swap_n[c] = nrun;
-        S.swap_mask[c] = D;
-    }
+    // every CTA decides alike (the same energies and draws); rank 0 traces
+    for (int c = threadIdx.x >> 5; c < 2; c += blockDim.x >> 5)
+        pt_copy_warp<GAUSS, ET>((ET *)S.E, P.R, c, np, S.swap_x + c * 32, P.dbeta_l2e, S.swap_list + c * 32,
+                                S.swap_n + c, S.swap_mask + c,
+                                trace && S.rank == 0 ? P.tr_swap + ((size_t)slot * 2 + c) * np : nullptr);
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {

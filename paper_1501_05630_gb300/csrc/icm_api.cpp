@@ -142,15 +142,20 @@ uint32_t acceptance_threshold(double a)
 //    m = 0 (the zero-energy proposal of a diluted instance; the other
 //    instances accept every m <= 0 before the table); stride thr_stride(Z);
 //  b2l[r] = -2 beta_k log2(e) for the Gaussian test;
-//  dbeta_l2e[k] = (beta_k - beta_{k+1}) log2(e) for Gaussian PT decisions;
+//  dbeta_l2e[k] = (beta_k - beta_{k+1}) log2(e) for PT decisions (the Gaussian
+//    test; the +-J count of thresholds above a draw starts from it);
 //  thr_swap (per pair k, d = 1..len_k) = floor(exp((-2d)(beta_k - beta_{k+1})) 2^32)
-//    for +-J PT decisions, cut where it reaches 0.
+//    for +-J PT decisions, cut where it reaches 0.  The kernels count the
+//    leading thresholds above a draw (stepping from the closed form), which
+//    needs each pair's run to be non-increasing in d (exp is monotone);
+//    swap_monotone records that it is.
 struct TempTables {
     std::vector<double> beta;
     std::vector<uint32_t> thr_metro;
     std::vector<float> b2l, dbeta_l2e;
     std::vector<uint32_t> thr_swap;
     std::vector<int32_t> swap_off, swap_len;
+    bool swap_monotone = true;
 };
 
 void temperature_tables(const double *T, int n_T, int Nb, int Z, TempTables &t)
@@ -178,6 +183,7 @@ void temperature_tables(const double *T, int n_T, int Nb, int Z, TempTables &t)
         for (int d = 1; d <= Nb; ++d) {
             const uint32_t v = acceptance_threshold((double)(-2 * d) * db);
             if (v == 0u) break;
+            if (len > 0 && v > t.thr_swap.back()) t.swap_monotone = false;
             t.thr_swap.push_back(v);
             ++len;
         }
@@ -607,6 +613,10 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     // temperature tables
     TempTables tt;
     temperature_tables(T, n_T, g.Nb, Z, tt);
+    if (!tt.swap_monotone) {
+        destroy_batch(b);
+        return fail(ctx, ICM_ERR_STATE, "swap thresholds not monotone in the energy difference");
+    }
     std::vector<double> &beta = tt.beta;
     std::vector<uint32_t> &thr_metro = tt.thr_metro;
     std::vector<float> &b2l = tt.b2l, &dbeta_l2e = tt.dbeta_l2e;
@@ -1340,6 +1350,7 @@ icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, doub
     }
     TempTables tt;
     temperature_tables(T, n_T, P.Nb, P.Z, tt);
+    if (!tt.swap_monotone) return fail(b->ctx, ICM_ERR_STATE, "swap thresholds not monotone in the energy difference");
     icm_status st;
     if (tt.thr_swap.size() > b->thr_swap_cap) {
         uint32_t *d = nullptr;

@@ -83,6 +83,96 @@ __device__ __forceinline__ float ex2_approx(float x)
     return y;
 }
 
+// ---------------------------------------------------------------------------
+// Step 3 (the PT pass).  For each copy c the swaps (k, k+1), k = 0 .. np-1, are
+// decided in ascending k; an accepted swap moves the configuration at k up to
+// k+1, so the energy compared at step k+1 is the one carried up (or, after a
+// rejection, the original energy at k+1).  The draw x of (c, k) is first
+// turned into the form its test takes inside that sequential loop:
+//  * Gaussian: accept iff Delta >= 0 or u < 2^Delta, with Delta = (beta_k -
+//    beta_{k+1}) log2(e) (E_k - E_{k+1}) and u = (x >> 8) 2^-24, that is iff
+//    Delta >= 0 or log2(u) < Delta: the word is log2(u) (fp32 bits);
+//  * +-J: accept iff E_k >= E_{k+1} or x < thr[d - 1], d = (E_{k+1} - E_k) / 2
+//    in 1..len (thr = floor(exp(-2 d (beta_k - beta_{k+1})) 2^32), non-
+//    increasing in d), that is iff d <= d_lim, the number of leading
+//    thresholds above x: the word is d_lim, found from the closed form of
+//    thr and checked against the table.
+__device__ __forceinline__ uint32_t pt_word_gauss(uint32_t x)
+{
+    return __float_as_uint(__log2f((float)(x >> 8) * (1.0f / 16777216.0f)));
+}
+
+__device__ __forceinline__ uint32_t pt_word_pmj(uint32_t x, const uint32_t *thr, int len, float dbl)
+{
+    // thr[d-1] > x iff exp(-2 d dbeta) 2^32 >= x + 1 iff d <= (32 - log2(x + 1)) / (2 dbl),
+    // dbl = dbeta log2(e): start there, then step to the exact count against
+    // the table (from any start: up while thr[d] > x, down while thr[d-1] <= x)
+    const float est = (32.f - __log2f((float)x + 1.f)) / (2.f * dbl);
+    int d = est >= (float)len ? len : (est > 0.f ? (int)est : 0);
+    while (d < len && __ldg(thr + d) > x) ++d;
+    while (d > 0 && __ldg(thr + d - 1) <= x) --d;
+    return (uint32_t)d;
+}
+
+// The pass of copy c, run by one whole warp.  Every lane runs the sequential
+// decisions (loads and compares only: the energies at positions k+1 are read
+// as they were before the pass); then lane k writes the energy of position k
+// after the pass, the run of accepted swaps that starts at k as a (source,
+// destination) pair of replica slots, and its trace byte; lane 0 writes the run count and the
+// mask of replica slots whose configuration moves down one position.
+//   E [R] energies, slot 2k + c; w [np] words of pt_word_*; dbl [np]
+//   (beta_k - beta_{k+1}) log2(e) (Gaussian); list [32]; trace [np] or null.
+template <bool GAUSS, typename ET>
+__device__ __forceinline__ void pt_copy_warp(ET *E, int R, int c, int np, const uint32_t *w, const float *dbl,
+                                             int *list, int *nlist, uint64_t *down, uint8_t *trace)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t acc = 0u;
+    ET ek = E[c];
+#pragma unroll
+    for (int k = 0; k < 31; ++k) {
+        if (k < np) {
+            const ET ek1 = E[ICM_IDX(2 * k + 2 + c, R, 11)];
+            bool a;
+            if constexpr (GAUSS) {
+                const float delta = dbl[k] * (ek - ek1);
+                a = (delta >= 0.f) || (__uint_as_float(w[k]) < delta);
+            } else {
+                const int dE = ek - ek1;                   // even: +-J energies differ by 2 d
+                a = (dE >= 0) || (((-dE) >> 1) <= (int)w[k]);
+            }
+            acc |= (uint32_t)a << k;
+            if (!a) ek = ek1;
+        }
+    }
+    // position k after the pass: the configuration from k+1 if swap k was
+    // accepted; else, if swap k-1 was, the one that started the run at rs;
+    // else its own
+    const int k = lane;
+    ET en = ET(0);
+    if (k <= np) {
+        if ((acc >> k) & 1u) en = E[2 * k + 2 + c];
+        else if (k > 0 && ((acc >> (k - 1)) & 1u)) en = E[2 * (32 - __clz(~acc & ((1u << k) - 1u))) + c];
+        else en = E[2 * k + c];
+    }
+    __syncwarp();
+    if (k <= np) E[2 * k + c] = en;
+    const uint32_t starts = acc & ~(acc << 1);
+    if (k < np) {
+        if ((starts >> k) & 1u) {
+            const int end = k + __ffs(~(acc >> k)) - 1;    // the first rejected swap above k (or np)
+            list[ICM_IDX(__popc(starts & ((1u << k) - 1u)), 32, 12)] = ((2 * k + c) << 8) | (2 * end + c);
+        }
+        if (trace) trace[k] = (uint8_t)((acc >> k) & 1u);
+    }
+    if (lane == 0) {
+        *nlist = __popc(starts);
+        uint64_t D = 0;
+        for (uint32_t b = acc; b; b &= b - 1u) D |= 1ull << (2 * (__ffs(b) - 1) + 2 + c);
+        *down = D;
+    }
+}
+
 // Sum of a[j] over the 32 lanes, delivered to lane j (31 shuffles).
 template <typename T>
 __device__ __forceinline__ T transpose_reduce(T (&a)[32], int lane)

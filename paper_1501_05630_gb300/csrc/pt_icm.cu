@@ -637,64 +637,23 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int nT = P.nT, np = nT - 1, N = P.N;
+    // draws of all (copy, pair) in parallel, in the form of their test
     for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
         const int c = i / np, k = i % np;
         uint32_t x[4];
         philox10((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.seed_lo, P.seed_hi, x);
-        S.swap_x[c * 32 + k] = x[0];
+        if constexpr (GAUSS) S.swap_x[c * 32 + k] = pt_word_gauss(x[0]);
+        else S.swap_x[c * 32 + k] = pt_word_pmj(x[0], P.thr_swap + S.sw_off[k], S.sw_len[k], P.dbeta_l2e[k]);
     }
     __syncthreads();
-    const int second = blockDim.x > 32 ? 32 : 1;   // copy 1 runs on another warp when there is one
-    if (threadIdx.x == 0 || threadIdx.x == second) {
-        ET *E = (ET *)S.E;
-        const int c = threadIdx.x == 0 ? 0 : 1;
-        // Accepted swaps (k,k+1), (k+1,k+2), ..., (m,m+1) in a row form a run:
-        // the configuration at k bubbles up to m+1 and those at k+1..m+1 move
-        // down one slot.  Record, per copy, the bits that move down (D) and one
-        // (source, destination) bit pair per run.  The energy of the
-        // configuration now at k is carried in a register (the one that came
-        // up, or the one that was there); position k+1 has not been written
-        // yet in this pass, so its energy is read as it was.
-        uint64_t D = 0;
-        int nrun = 0, run_start = -1;
-        ET ek = E[c];
-        for (int k = 0; k <= np; ++k) {
-            bool acc = false;
-            if (k < np) {
-                const int ra = 2 * k + c, rb = ra + 2;
-                const ET ek1 = E[ICM_IDX(rb, P.R, 11)];
-                const uint32_t x = S.swap_x[c * 32 + k];
-                if constexpr (GAUSS) {
-                    // log2(e) (beta_k - beta_{k+1}) (E_k - E_{k+1}); accept iff >= 0 or u < 2^delta
-                    const float delta = S.sw_dbl[k] * (ek - ek1);
-                    acc = (delta >= 0.f) || ((float)(x >> 8) * (1.0f / 16777216.0f) < ex2_approx(delta));
-                } else {
-                    const int dE = ek - ek1;
-                    if (dE >= 0) {
-                        acc = true;
-                    } else {
-                        const int d = (-dE) >> 1;
-                        acc = d >= 1 && d <= S.sw_len[k] && x < P.thr_swap[S.sw_off[k] + d - 1];
-                    }
-                }
-                if (acc) {
-                    E[ICM_IDX(ra, P.R, 11)] = ek1;
-                    E[rb] = ek;                      // ek moves up and stays the carried energy
-                    D |= 1ull << (rb);
-                    if (run_start < 0) run_start = k;
-                } else {
-                    ek = ek1;
-                }
-                if (trace) P.tr_swap[((size_t)slot * 2 + c) * np + k] = (uint8_t)acc;
-            }
-            if (!acc && run_start >= 0) {   // run [run_start, k-1] ends
-                S.swap_list[c * 32 + ICM_IDX(nrun++, 32, 12)] = ((2 * run_start + c) << 8) | (2 * k + c);
-                run_start = -1;
-            }
-        }
-        S.swap_n[c] = nrun;
-        S.swap_mask[c] = D;
-    }
+    // warp c runs copy c (a one-warp CTA runs both in turn).  Accepted swaps
+    // (k,k+1), ..., (m,m+1) in a row form a run: the configuration at k
+    // bubbles up to m+1 and those at k+1..m+1 move down one slot; the words
+    // are permuted below from the runs and the mask of bits that move down.
+    for (int c = threadIdx.x >> 5; c < 2; c += blockDim.x >> 5)
+        pt_copy_warp<GAUSS, ET>((ET *)S.E, P.R, c, np, S.swap_x + c * 32, S.sw_dbl, S.swap_list + c * 32,
+                                S.swap_n + c, S.swap_mask + c,
+                                trace ? P.tr_swap + ((size_t)slot * 2 + c) * np : nullptr);
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {
