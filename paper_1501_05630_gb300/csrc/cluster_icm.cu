@@ -13,10 +13,8 @@
 //    barrier, every CTA adds the K shares in rank order (the same E in all);
 //  * ICM: per-CTA overlap counts, barrier, every CTA finds the seed's owner
 //    from the K counts (position order = (colour, rank, local)), the owner
-//    plants it, barrier; growth in rounds: each CTA scans its own sites until
-//    they stop growing, then a cluster barrier and the OR of the K CTAs'
-//    flags (did a site with a neighbour in another CTA grow?); flip,
-//    barrier, copy-a energies summed as above;
+//    plants it, barrier; growth rounds end with a barrier and the OR of the
+//    K CTAs' round flags; flip, barrier, copy-a energies summed as above;
 //  * PT: every CTA holds the same energies and draws the same numbers, so
 //    all make the same decisions and permute their own words; barrier;
 //  * observables: per-CTA counts, barrier, rank 0 accumulates.
@@ -412,43 +410,29 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         __syncthreads();
         return;                                      // the same decision in every CTA
     }
-    // Growth in outer rounds, each ending with a cluster barrier.  Inside a
-    // round this CTA scans its sites until a scan adds nothing (CTA barriers
-    // only), so the growth crosses its whole slice; another round follows
-    // only if some CTA grew a site with a neighbour in another CTA.  The
-    // updates are in place, so a scan can carry the growth several sites
-    // along.  The fixed point is each seed's component of q = -1.
     const uint32_t dC0 = (uint32_t)(L.C0 - L.s), dC1 = (uint32_t)(L.C1 - L.s);
-    const uint32_t own_s = cl_map(S.base + L.s, S.rank);   // this CTA's s[0] in the cluster window
     for (int round = 0;; ++round) {
-        int sent = 0;
-        for (;;) {
-            int grew = 0;
-            for (int li = tid; li < nls; li += nth) {
-                const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
-                const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
-                const uint32_t c0 = S.C0[li], c1 = S.C1[li];
-                if (d0 == c0 && d1 == c1) continue;
-                uint32_t e[Z];
-                uint32_t nb0 = 0u, nb1 = 0u;
+        int grew = 0;
+        for (int li = tid; li < nls; li += nth) {
+            const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
+            const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
+            const uint32_t c0 = S.C0[li], c1 = S.C1[li];
+            if (d0 == c0 && d1 == c1) continue;
+            uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    e[d] = S.nb[li * Z + d];
-                    nb0 |= cl_ld(e[d] + dC0);
-                    if (G > 1) nb1 |= cl_ld(e[d] + dC1);
-                }
-                const uint32_t n0 = c0 | (d0 & nb0), n1 = c1 | (d1 & nb1);
-                if (n0 != c0 || n1 != c1) {
-                    S.C0[li] = n0;
-                    S.C1[li] = n1;
-                    grew = 1;
-#pragma unroll
-                    for (int d = 0; d < Z; ++d) sent |= (e[d] - own_s) >= 4u * (uint32_t)nls;
-                }
+            for (int d = 0; d < Z; ++d) {
+                const uint32_t e = S.nb[li * Z + d];
+                nb0 |= cl_ld(e + dC0);
+                if (G > 1) nb1 |= cl_ld(e + dC1);
             }
-            if (!__syncthreads_or(grew)) break;
+            const uint32_t n0 = c0 | (d0 & nb0), n1 = c1 | (d1 & nb1);
+            if (n0 != c0 || n1 != c1) {
+                S.C0[li] = n0;
+                S.C1[li] = n1;
+                grew = 1;
+            }
         }
-        const int any_here = __syncthreads_or(sent);
+        const int any_here = __syncthreads_or(grew);
         if (tid == 0) S.flags[round & 1] = any_here;
         cl_sync();
         int any = 0;

@@ -103,6 +103,15 @@ def test_diluted_pmj_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, dilution, row
              threads=threads)
 
 
+def test_fully_diluted_every_swap_accepted(icm):
+    """Every bond absent: all energies are 0, so every PT swap is accepted and
+    each copy's pass is one run over all 32 temperatures (the longest run the
+    decision warp can form); sweep by sweep equal to the oracle."""
+    icmpt, ctx = icm
+    _compare(icm, O.CUBIC3D, 4, 32, 2.0, 1.0, 2, 6, 0xF0, dilution=1.0)
+    _compare(icm, O.SQUARE2D, 4, 2, 1.5, 1.0, 1, 6, 0xF1, dilution=1.0)   # one pair: a run of one swap
+
+
 def test_diluted_instance_admitted_into_undiluted_batch(icm):
     """A slot replaced by a diluted instance switches the batch to its diluted
     kernels; every slot still evolves like its instance alone."""
