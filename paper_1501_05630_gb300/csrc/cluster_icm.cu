@@ -547,10 +547,9 @@ __device__ void cl_pt_pass(const KParams &P, const CS &S, uint32_t t, uint32_t i
     }
     __syncthreads();
     // every CTA decides alike (the same energies and draws); rank 0 traces
-    for (int c = threadIdx.x >> 5; c < 2; c += blockDim.x >> 5)
-        pt_copy_warp<GAUSS, ET>((ET *)S.E, P.R, c, np, S.swap_x + c * 32, P.dbeta_l2e, S.swap_list + c * 32,
-                                S.swap_n + c, S.swap_mask + c,
-                                trace && S.rank == 0 ? P.tr_swap + ((size_t)slot * 2 + c) * np : nullptr);
+    if (threadIdx.x < 32)
+        pt_warp<GAUSS, ET>((ET *)S.E, P.R, np, S.swap_x, P.dbeta_l2e, S.swap_list, S.swap_n, S.swap_mask,
+                           trace && S.rank == 0 ? P.tr_swap + (size_t)slot * 2 * np : nullptr);
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {

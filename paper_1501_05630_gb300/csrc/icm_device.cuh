@@ -114,19 +114,23 @@ __device__ __forceinline__ uint32_t pt_word_pmj(uint32_t x, const uint32_t *thr,
     return (uint32_t)d;
 }
 
-// The pass of copy c, run by one whole warp.  Every lane runs the sequential
-// decisions (loads and compares only: the energies at positions k+1 are read
-// as they were before the pass); then lane k writes the energy of position k
-// after the pass, the run of accepted swaps that starts at k as a (source,
-// destination) pair of replica slots, and its trace byte; lane 0 writes the run count and the
-// mask of replica slots whose configuration moves down one position.
-//   E [R] energies, slot 2k + c; w [np] words of pt_word_*; dbl [np]
-//   (beta_k - beta_{k+1}) log2(e) (Gaussian); list [32]; trace [np] or null.
+// The passes of both copies, run by one warp: lanes 16c .. 16c+15 run copy c.
+// Each lane runs its copy's sequential decisions (loads and compares only:
+// the energies at positions k+1 are read as they were before the pass); then
+// lane h of copy c, for the positions k = h and h + 16, writes the energy of
+// position k after the pass, the run of accepted swaps that starts at k as a
+// (source, destination) pair of replica slots, and its trace byte; lane 0 of
+// each half writes its copy's run count and the mask of replica slots whose
+// configuration moves down one position.
+//   E [R] energies, slot 2k + c; w [2][32] words of pt_word_* (copy c at 32 c);
+//   dbl [np] (beta_k - beta_{k+1}) log2(e) (Gaussian); list [2][32];
+//   nlist [2]; down [2]; trace [2][np] or null.
 template <bool GAUSS, typename ET>
-__device__ __forceinline__ void pt_copy_warp(ET *E, int R, int c, int np, const uint32_t *w, const float *dbl,
-                                             int *list, int *nlist, uint64_t *down, uint8_t *trace)
+__device__ __forceinline__ void pt_warp(ET *E, int R, int np, const uint32_t *w, const float *dbl, int *list,
+                                        int *nlist, uint64_t *down, uint8_t *trace)
 {
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, c = lane >> 4, h = lane & 15;
+    const uint32_t *wc = w + 32 * c;
     uint32_t acc = 0u;
     ET ek = E[c];
 #pragma unroll
@@ -136,10 +140,10 @@ __device__ __forceinline__ void pt_copy_warp(ET *E, int R, int c, int np, const 
             bool a;
             if constexpr (GAUSS) {
                 const float delta = dbl[k] * (ek - ek1);
-                a = (delta >= 0.f) || (__uint_as_float(w[k]) < delta);
+                a = (delta >= 0.f) || (__uint_as_float(wc[k]) < delta);
             } else {
                 const int dE = ek - ek1;                   // even: +-J energies differ by 2 d
-                a = (dE >= 0) || (((-dE) >> 1) <= (int)w[k]);
+                a = (dE >= 0) || (((-dE) >> 1) <= (int)wc[k]);
             }
             acc |= (uint32_t)a << k;
             if (!a) ek = ek1;
@@ -148,28 +152,36 @@ __device__ __forceinline__ void pt_copy_warp(ET *E, int R, int c, int np, const 
     // position k after the pass: the configuration from k+1 if swap k was
     // accepted; else, if swap k-1 was, the one that started the run at rs;
     // else its own
-    const int k = lane;
-    ET en = ET(0);
-    if (k <= np) {
-        if ((acc >> k) & 1u) en = E[2 * k + 2 + c];
-        else if (k > 0 && ((acc >> (k - 1)) & 1u)) en = E[2 * (32 - __clz(~acc & ((1u << k) - 1u))) + c];
-        else en = E[2 * k + c];
+    ET en[2];
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int k = h + 16 * it;
+        en[it] = ET(0);
+        if (k <= np) {
+            if ((acc >> k) & 1u) en[it] = E[2 * k + 2 + c];
+            else if (k > 0 && ((acc >> (k - 1)) & 1u)) en[it] = E[2 * (32 - __clz(~acc & ((1u << k) - 1u))) + c];
+            else en[it] = E[2 * k + c];
+        }
     }
     __syncwarp();
-    if (k <= np) E[2 * k + c] = en;
     const uint32_t starts = acc & ~(acc << 1);
-    if (k < np) {
-        if ((starts >> k) & 1u) {
-            const int end = k + __ffs(~(acc >> k)) - 1;    // the first rejected swap above k (or np)
-            list[ICM_IDX(__popc(starts & ((1u << k) - 1u)), 32, 12)] = ((2 * k + c) << 8) | (2 * end + c);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const int k = h + 16 * it;
+        if (k <= np) E[2 * k + c] = en[it];
+        if (k < np) {
+            if ((starts >> k) & 1u) {
+                const int end = k + __ffs(~(acc >> k)) - 1;    // the first rejected swap above k (or np)
+                list[32 * c + ICM_IDX(__popc(starts & ((1u << k) - 1u)), 32, 12)] = ((2 * k + c) << 8) | (2 * end + c);
+            }
+            if (trace) trace[c * np + k] = (uint8_t)((acc >> k) & 1u);
         }
-        if (trace) trace[k] = (uint8_t)((acc >> k) & 1u);
     }
-    if (lane == 0) {
-        *nlist = __popc(starts);
+    if (h == 0) {
+        nlist[c] = __popc(starts);
         uint64_t D = 0;
         for (uint32_t b = acc; b; b &= b - 1u) D |= 1ull << (2 * (__ffs(b) - 1) + 2 + c);
-        *down = D;
+        down[c] = D;
     }
 }
 

@@ -646,14 +646,13 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
         else S.swap_x[c * 32 + k] = pt_word_pmj(x[0], P.thr_swap + S.sw_off[k], S.sw_len[k], P.dbeta_l2e[k]);
     }
     __syncthreads();
-    // warp c runs copy c (a one-warp CTA runs both in turn).  Accepted swaps
-    // (k,k+1), ..., (m,m+1) in a row form a run: the configuration at k
-    // bubbles up to m+1 and those at k+1..m+1 move down one slot; the words
-    // are permuted below from the runs and the mask of bits that move down.
-    for (int c = threadIdx.x >> 5; c < 2; c += blockDim.x >> 5)
-        pt_copy_warp<GAUSS, ET>((ET *)S.E, P.R, c, np, S.swap_x + c * 32, S.sw_dbl, S.swap_list + c * 32,
-                                S.swap_n + c, S.swap_mask + c,
-                                trace ? P.tr_swap + ((size_t)slot * 2 + c) * np : nullptr);
+    // warp 0 runs both copies (a half-warp each).  Accepted swaps (k,k+1), ...,
+    // (m,m+1) in a row form a run: the configuration at k bubbles up to m+1
+    // and those at k+1..m+1 move down one slot; the words are permuted below
+    // from the runs and the mask of bits that move down.
+    if (threadIdx.x < 32)
+        pt_warp<GAUSS, ET>((ET *)S.E, P.R, np, S.swap_x, S.sw_dbl, S.swap_list, S.swap_n, S.swap_mask,
+                           trace ? P.tr_swap + (size_t)slot * 2 * np : nullptr);
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {
