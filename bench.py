@@ -66,12 +66,19 @@ FUSED_SOURCES = ("pt_icm.cu", "fused_pmj.cu", "fused_gauss.cu", "icm_device.cuh"
 
 
 def kernel_source_digest() -> str:
+    """Digest of the fused kernel's code: its sources with comments removed and
+    whitespace collapsed, so that a comment edit keeps the recorded counters."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1501_05630_gb300", "csrc")
     for f in FUSED_SOURCES:
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(csrc, f)) as fh:
+            code = fh.read()
+        code = re.sub(r"/\*.*?\*/", " ", code, flags=re.S)
+        code = re.sub(r"//[^\n]*", " ", code)
+        code = " ".join(code.split())
+        h.update(f.encode() + code.encode())
     return h.hexdigest()[:16]
 
 

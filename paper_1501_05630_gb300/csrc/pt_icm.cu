@@ -26,8 +26,10 @@
 //    the clusters of all pairs grow at once, bit-parallel (bit 2k of a site's
 //    cluster word = member of pair k's cluster), until a round adds nothing;
 //    both copies flip by XOR, E_a is recomputed and E_b = (E_a+E_b) - E_a.
-//  * Step 3: one thread runs each copy's sequential PT pass on the energies;
-//    accepted swaps are then applied to every site word as bit transpositions.
+//  * Step 3: the draws of all swaps are turned into the form of their test in
+//    parallel; one warp runs both copies' sequential passes (a half-warp
+//    each) as chains of loads and compares; accepted swaps are then applied
+//    to every site word as bit transpositions.
 //  * Observables: vertical (bit-sliced) counters of q_i = -1 sites and of
 //    bonds with q_i q_j = -1 for every pair at once.
 #include "icm_internal.h"
@@ -631,7 +633,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
 }
 
 // ---------------------------------------------------------------------------
-// Step 3: sequential PT pass per copy, then the configuration swaps.
+// Step 3: the PT pass of each copy (see pt_warp), then the configuration swaps.
 template <bool GAUSS, bool WIDE>
 __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
 {
