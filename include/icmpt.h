@@ -139,7 +139,17 @@ icm_status icm_lattice_size(int32_t lattice, int32_t L, int32_t *n_sites, int32_
 /* Create a batch of n_inst disorder instances of one lattice and disorder
  * kind that share one temperature ladder.
  *   couplings : [n_inst][N_b] in bond order; int8 (+-1, or 0 = absent) for
- *               ICM_PM_J, float32 (0 = absent) for ICM_GAUSS.  Required.
+ *               ICM_PM_J, float32 (0 = absent) for ICM_GAUSS.  NULL = drawn
+ *               from `seed` and each instance id (the paper's disorder,
+ *               "Benchmark model and observables": J = +-1 with probability
+ *               1/2, or Gaussian with mean 0 and variance 1), Philox
+ *               domain 3 keyed by instance id and bond index only:
+ *                 +-J bond b: the top bit of word b & 3 of counter
+ *                   {b >> 2, 0, 0, 3<<24 | id}, 0 -> +1, 1 -> -1;
+ *                 Gaussian bond b: words o0, o1 of counter {b, 1, 0, 3<<24 | id},
+ *                   J = sqrt(-2 ln u1) cos(2 pi u2) in double, u1 = (o0 + 1) 2^-32,
+ *                   u2 = o1 2^-32, rounded to fp32.
+ *               icm_read_couplings returns them.
  *   spins     : [n_inst][2 n_T][N] int8 (+1/-1), replica r = 2k + c is copy
  *               c at temperature position k.  NULL = all spins +1.
  *   instance_ids : [n_inst] uint32 < 2^24, the instance's RNG key.
@@ -186,6 +196,9 @@ icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps);
  * N_b for an undiluted instance.  The link overlap of instance i is
  * q_l = 1 - 2 acc_d / (bonds_i * n_meas).  No device work.               */
 icm_status icm_read_bond_counts(const icm_batch *b, int32_t *out);
+/* Couplings [n_inst][N_b] in bond order, as loaded or drawn: int8 for
+ * ICM_PM_J, float32 for ICM_GAUSS (host or device buffer, ICM_DEVICE_PTR). */
+icm_status icm_read_couplings(icm_batch *b, void *out, uint32_t flags);
 /* Spins [n_inst][2 n_T][N] int8 +-1, site order, replica r = 2k + c. */
 icm_status icm_read_spins(icm_batch *b, int8_t *out, uint32_t flags);
 /* Energies [n_inst][2 n_T] (double; exact integers for ICM_PM_J). */
@@ -226,8 +239,9 @@ icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t
  * replaced while the others keep their state; free slots are skipped by the
  * kernel; each slot has its own measurement window.                       */
 
-/* Load one instance into `slot`: couplings [N_b], spins [2 n_T][N] (NULL =
- * all +1), its RNG instance id; the slot's sweep counter restarts at 0, its
+/* Load one instance into `slot`: couplings [N_b] (NULL = drawn from the
+ * batch seed and instance_id as in icm_batch_create), spins [2 n_T][N]
+ * (NULL = all +1), its RNG instance id; the slot's sweep counter restarts at 0, its
  * observables are cleared, its window starts at t = 0 and it becomes active.
  * The other slots are untouched.                                          */
 icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings, const int8_t *spins,

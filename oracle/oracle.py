@@ -93,6 +93,34 @@ def philox(ctr, key) -> np.ndarray:
     return out
 
 
+def philox_couplings(n_bonds: int, pm: bool, seed: int, instance_ids) -> np.ndarray:
+    """Disorder drawn from the seed (the paper's "Benchmark model and
+    observables": J = +-1 with probability 1/2, or Gaussian with mean 0 and
+    variance 1), Philox domain 3 keyed by instance id and bond index:
+      +-J bond b: the top bit of word b & 3 of counter {b >> 2, 0, 0, 3<<24 | id},
+        0 -> +1, 1 -> -1 (int8);
+      Gaussian bond b: words o0, o1 of counter {b, 1, 0, 3<<24 | id}, Box-Muller
+        in double, J = sqrt(-2 ln u1) cos(2 pi u2), u1 = (o0 + 1) 2^-32,
+        u2 = o1 2^-32, rounded to fp32.
+    Returns [len(instance_ids)][n_bonds]."""
+    import math
+    key = [int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF]
+    ids = list(instance_ids)
+    out = np.empty((len(ids), n_bonds), dtype=np.int8 if pm else np.float32)
+    for a, inst in enumerate(ids):
+        c3 = (3 << 24) | int(inst)
+        for b in range(n_bonds):
+            if pm:
+                o = philox([b >> 2, 0, 0, c3], key)
+                out[a, b] = -1 if (int(o[b & 3]) >> 31) else 1
+            else:
+                o = philox([b, 1, 0, c3], key)
+                u1 = (int(o[0]) + 1) / 4294967296.0
+                u2 = int(o[1]) / 4294967296.0
+                out[a, b] = np.float32(math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2))
+    return out
+
+
 class Geometry:
     """Sites, bonds (in bond order) and the two-colouring of one lattice."""
 

@@ -127,6 +127,62 @@ bool build_geometry(int lattice, int L, Geometry &g)
     return true;
 }
 
+// Philox4x32-10 on the host (Salmon, Moraes, Dror, Shaw, SC'11: multipliers
+// 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85), for
+// disorder drawn from the seed when a caller passes no couplings.
+void host_philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint64_t seed, uint32_t o[4])
+{
+    uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {
+        const uint64_t m0 = (uint64_t)c0 * 0xD2511F53ull;
+        const uint64_t m1 = (uint64_t)c2 * 0xCD9E8D57ull;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0;
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1;
+        c1 = (uint32_t)m1;
+        c3 = (uint32_t)m0;
+        c0 = n0;
+        c2 = n2;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
+}
+
+// Couplings [n][Nb] of instances ids[0..n) drawn from the seed (Philox domain
+// 3, counters by instance id and bond index only):
+//   +-J      bond b: the top bit of word b & 3 of ctr {b >> 2, 0, 0, 3<<24 | id}
+//            (0 -> +1, 1 -> -1), the paper's bimodal distribution;
+//   Gaussian bond b: words o0, o1 of ctr {b, 1, 0, 3<<24 | id}, u1 = (o0 + 1) 2^-32,
+//            u2 = o1 2^-32, J = sqrt(-2 ln u1) cos(2 pi u2) (Box-Muller, in
+//            double, rounded to fp32), the paper's N(0, 1).
+void generate_couplings(bool gauss, int n, int Nb, const uint32_t *ids, uint64_t seed,
+                        std::vector<unsigned char> &out)
+{
+    out.assign((size_t)n * Nb * (gauss ? 4 : 1), 0);
+    for (int a = 0; a < n; ++a) {
+        const uint32_t c3 = (3u << 24) | ids[a];
+        if (gauss) {
+            float *J = (float *)out.data() + (size_t)a * Nb;
+            for (int b = 0; b < Nb; ++b) {
+                uint32_t o[4];
+                host_philox((uint32_t)b, 1u, 0u, c3, seed, o);
+                const double u1 = ((double)o[0] + 1.0) * (1.0 / 4294967296.0);
+                const double u2 = (double)o[1] * (1.0 / 4294967296.0);
+                const double r = std::sqrt(-2.0 * std::log(u1));
+                const double w = std::cos(6.283185307179586 * u2);
+                J[b] = (float)(r * w);
+            }
+        } else {
+            int8_t *J = (int8_t *)out.data() + (size_t)a * Nb;
+            for (int b = 0; b < Nb; ++b) {
+                uint32_t o[4];
+                host_philox((uint32_t)b >> 2, 0u, 0u, c3, seed, o);
+                J[b] = (o[b & 3] >> 31) ? (int8_t)-1 : (int8_t)1;
+            }
+        }
+    }
+}
+
 // floor(exp(a) * 2^32), saturated at 2^32 - 1 (a <= 0).
 uint32_t acceptance_threshold(double a)
 {
@@ -513,7 +569,6 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     if (lattice != ICM_CHIMERA && (L < 2 || (L & 1))) return fail(ctx, ICM_ERR_ARG, "lattices need an even L >= 2");
     if (lattice == ICM_CHIMERA && L < 1) return fail(ctx, ICM_ERR_ARG, "chimera needs M >= 1");
     if (n_inst < 1) return fail(ctx, ICM_ERR_ARG, "n_inst must be >= 1");
-    if (!couplings) return fail(ctx, ICM_ERR_ARG, "couplings are required");
     if (!T || n_T < 1 || n_T > 32) return fail(ctx, ICM_ERR_ARG, "need 1 <= n_T <= 32 temperatures");
     for (int k = 0; k < n_T; ++k) {
         if (!(T[k] > 0.0) || !std::isfinite(T[k])) return fail(ctx, ICM_ERR_ARG, "temperatures must be finite and > 0");
@@ -713,7 +768,12 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         destroy_batch(b);
         return cuda_fail(ctx, e, "batch upload");
     }
-    if ((st = clear_observables(b)) || (st = upload_state(b, couplings, spins, flags))) {
+    std::vector<unsigned char> drawn;
+    if (!couplings) generate_couplings(b->gauss, n_inst, g.Nb, ids.data(), seed, drawn);
+    if ((st = clear_observables(b)) ||
+        (st = couplings ? upload_state(b, couplings, spins, flags)
+                        : upload_state(b, drawn.data(), nullptr, flags & ~ICM_DEVICE_PTR)) ||
+        (!couplings && spins && (st = upload_state(b, nullptr, spins, flags)))) {
         destroy_batch(b);
         return st;
     }
@@ -787,6 +847,16 @@ icm_status icm_read_bond_counts(const icm_batch *b, int32_t *out)
 {
     if (!b || !out) return ICM_ERR_ARG;
     for (int i = 0; i < b->n_inst; ++i) out[i] = b->h_nb[i];
+    return ICM_OK;
+}
+
+icm_status icm_read_couplings(icm_batch *b, void *out, uint32_t flags)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    const size_t bytes = (size_t)b->n_inst * b->kp.Nb * (b->gauss ? 4 : 1);
+    icm_status st = copy_out(b->ctx, out, b->raw_coup, bytes, flags);
+    if (st) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
     return ICM_OK;
 }
 
@@ -914,7 +984,6 @@ icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings,
 {
     if (!b) return ICM_ERR_ARG;
     if (slot < 0 || slot >= b->n_inst) return fail(b->ctx, ICM_ERR_ARG, "slot out of range");
-    if (!couplings) return fail(b->ctx, ICM_ERR_ARG, "couplings are required");
     if (instance_id >= (1u << 24)) return fail(b->ctx, ICM_ERR_ARG, "instance ids must be < 2^24");
     icm_status st;
     if ((st = ensure_slot_arrays(b))) return st;
@@ -922,7 +991,11 @@ icm_status icm_batch_set_slot(icm_batch *b, int32_t slot, const void *couplings,
     icm::KParams &P = b->kp;
     const size_t esz = b->gauss ? 4 : 1;
     unsigned char *raw_c = (unsigned char *)b->raw_coup + (size_t)slot * P.Nb * esz;
-    if ((st = copy_in(ctx, raw_c, couplings, (size_t)P.Nb * esz, flags))) return st;
+    std::vector<unsigned char> drawn;
+    if (!couplings) generate_couplings(b->gauss, 1, P.Nb, &instance_id, b->seed, drawn);
+    if ((st = couplings ? copy_in(ctx, raw_c, couplings, (size_t)P.Nb * esz, flags)
+                        : copy_in(ctx, raw_c, drawn.data(), (size_t)P.Nb * esz, flags & ~ICM_DEVICE_PTR)))
+        return st;
     float *Jd = b->gauss ? const_cast<float *>(P.Jd) + (size_t)slot * P.N * P.Z : nullptr;
     uint8_t *Jb = b->gauss ? nullptr : const_cast<uint8_t *>(P.Jb) + (size_t)slot * P.N;
     ICM_CUDA(ctx, icm::launch_expand_couplings(raw_c, b->gauss, b->edge_bond, 1, P.N, P.Z, P.Nb, Jd, Jb, ctx->stream));

@@ -46,7 +46,8 @@ EXPORTS = [
     "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_query", "icm_lattice_size",
     "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
-    "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables", "icm_clear_observables",
+    "icm_read_couplings", "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables",
+    "icm_clear_observables",
     "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
     "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
     "icm_server_clock", "icm_server_cancel", "icm_batch_set_cluster", "icm_batch_cluster",
@@ -111,6 +112,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_get_schedule.argtypes = [vp, ctypes.POINTER(Schedule)]
         L.icm_run_sweeps.argtypes = [vp, u32]
         L.icm_read_spins.argtypes = [vp, vp, u32]
+        L.icm_read_couplings.argtypes = [vp, vp, u32]
         L.icm_read_energies.argtypes = [vp, vp, u32]
         L.icm_read_sweeps.argtypes = [vp, vp, u32]
         L.icm_read_observables.argtypes = [vp] + [vp] * 7 + [u32]
@@ -283,10 +285,14 @@ class Observables:
 
 
 class Batch:
-    """n_inst disorder instances sharing one lattice, disorder kind and ladder."""
+    """n_inst disorder instances sharing one lattice, disorder kind and ladder.
+
+    couplings [n_inst][N_b] (host array or device tensor), or None: the
+    library draws them from the seed and the instance ids (then give n_inst
+    or instance_ids)."""
 
     def __init__(self, ctx: Context, lattice: int, L: int, disorder: int, couplings, T, T_icm: float,
-                 seed: int, spins=None, instance_ids=None):
+                 seed: int, spins=None, instance_ids=None, n_inst=None):
         self.ctx = ctx
         self._lib = ctx._lib
         self.lattice, self.L, self.disorder = int(lattice), int(L), int(disorder)
@@ -294,18 +300,23 @@ class Batch:
         self.T = np.ascontiguousarray(T, dtype=np.float64)
         self.nT = len(self.T)
         self.R = 2 * self.nT
-        n_inst = couplings.shape[0]
+        if couplings is not None:
+            n_inst = couplings.shape[0]
+        elif n_inst is None:
+            if instance_ids is None:
+                raise ValueError("without couplings, give n_inst or instance_ids")
+            n_inst = len(instance_ids)
         self.n_inst = int(n_inst)
         cp, cflags = _ptr(couplings)
         sp, sflags = _ptr(spins)
-        if spins is not None and cflags != sflags:
+        if spins is not None and couplings is not None and cflags != sflags:
             raise ValueError("couplings and spins must both be host or both be device buffers")
         ids = None if instance_ids is None else np.ascontiguousarray(instance_ids, dtype=np.uint32)
         h = ctypes.c_void_p()
         ctx.check(self._lib.icm_batch_create(
             ctx._h, self.lattice, self.L, self.disorder, self.n_inst, cp, sp,
             None if ids is None else ids.ctypes.data, self.T.ctypes.data, self.nT, float(T_icm),
-            int(seed) & 0xFFFFFFFFFFFFFFFF, cflags, ctypes.byref(h)))
+            int(seed) & 0xFFFFFFFFFFFFFFFF, cflags | sflags, ctypes.byref(h)))
         self._h = h
         ctx._batches.add(self)
 
@@ -370,6 +381,14 @@ class Batch:
         return m.value, se.value, n.value
 
     # -- reads
+    def read_couplings(self, out=None):
+        """Couplings [n_inst][N_b] as loaded or drawn (int8 +-J, float32 Gaussian)."""
+        if out is None:
+            out = np.empty((self.n_inst, self.Nb), dtype=np.float32 if self.disorder == GAUSS else np.int8)
+        p, f = _ptr(out)
+        self.ctx.check(self._lib.icm_read_couplings(self._h, p, f))
+        return out
+
     def read_spins(self, out=None):
         if out is None:
             out = np.empty((self.n_inst, self.R, self.N), dtype=np.int8)
