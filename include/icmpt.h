@@ -220,6 +220,16 @@ icm_status icm_read_sweeps(icm_batch *b, uint32_t *out, uint32_t flags);
 icm_status icm_read_observables(icm_batch *b, double *accE, int64_t *acc_n, int64_t *acc_q2,
                                 int64_t *acc_pmin, int64_t *acc_d, int64_t *hist,
                                 int64_t *n_meas, uint32_t flags);
+/* Overlaps per instance and temperature position k over the measured sweeps,
+ * from the accumulators above ("Benchmark model and observables"):
+ *   q_mean  [n_inst][n_T] : <q>,   q = 1 - 2n/N = (1/N) sum_i q_i
+ *   q2_mean [n_inst][n_T] : <q^2>
+ *   ql_mean [n_inst][n_T] : <q_l>, q_l = (1/N_b) sum over the bonds present of q_i q_j
+ *   q_hist  [n_inst][n_T][N+1] : counts of n (P(q) at q = 1 - 2n/N)
+ * NaN where no sweep was measured.  Host buffers; any may be NULL.  Step 2a
+ * flips copy 1 at ICM temperatures, so the sign of q there is folded:
+ * compare P(q) symmetrised.                                                */
+icm_status icm_read_overlaps(icm_batch *b, double *q_mean, double *q2_mean, double *ql_mean, int64_t *q_hist);
 icm_status icm_clear_observables(icm_batch *b);
 
 /* Decisions of the last sweep of the last icm_run_sweeps (schedule.trace = 1):

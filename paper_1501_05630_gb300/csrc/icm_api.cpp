@@ -909,6 +909,27 @@ icm_status icm_read_observables(icm_batch *b, double *accE, int64_t *acc_n, int6
     return ICM_OK;
 }
 
+icm_status icm_read_overlaps(icm_batch *b, double *q_mean, double *q2_mean, double *ql_mean, int64_t *q_hist)
+{
+    if (!b) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    const size_t nk = (size_t)b->n_inst * P.nT;
+    std::vector<int64_t> acc(4 * nk), nm(b->n_inst);
+    icm_status st = icm_read_observables(b, nullptr, acc.data(), acc.data() + nk, nullptr, acc.data() + 3 * nk,
+                                         q_hist, nm.data(), 0u);
+    if (st) return st;
+    const double N = (double)P.N, nan = std::nan("");
+    for (int i = 0; i < b->n_inst; ++i)
+        for (int k = 0; k < P.nT; ++k) {
+            const size_t o = (size_t)i * P.nT + k;
+            const double m = (double)nm[i], nb = (double)b->h_nb[i];
+            if (q_mean) q_mean[o] = m > 0 ? 1.0 - 2.0 * (double)acc[o] / (N * m) : nan;
+            if (q2_mean) q2_mean[o] = m > 0 ? (double)acc[nk + o] / (N * N * m) : nan;
+            if (ql_mean) ql_mean[o] = m > 0 && nb > 0 ? 1.0 - 2.0 * (double)acc[3 * nk + o] / (nb * m) : nan;
+        }
+    return ICM_OK;
+}
+
 icm_status icm_clear_observables(icm_batch *b)
 {
     if (!b) return ICM_ERR_ARG;

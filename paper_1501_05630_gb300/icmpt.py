@@ -46,7 +46,7 @@ EXPORTS = [
     "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_query", "icm_lattice_size",
     "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
-    "icm_read_couplings", "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables",
+    "icm_read_couplings", "icm_read_overlaps", "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables",
     "icm_clear_observables",
     "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
     "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
@@ -113,6 +113,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_run_sweeps.argtypes = [vp, u32]
         L.icm_read_spins.argtypes = [vp, vp, u32]
         L.icm_read_couplings.argtypes = [vp, vp, u32]
+        L.icm_read_overlaps.argtypes = [vp, vp, vp, vp, vp]
         L.icm_read_energies.argtypes = [vp, vp, u32]
         L.icm_read_sweeps.argtypes = [vp, vp, u32]
         L.icm_read_observables.argtypes = [vp] + [vp] * 7 + [u32]
@@ -388,6 +389,15 @@ class Batch:
         p, f = _ptr(out)
         self.ctx.check(self._lib.icm_read_couplings(self._h, p, f))
         return out
+
+    def read_overlaps(self, hist: bool = True):
+        """(q_mean, q2_mean, ql_mean, q_hist) per instance and temperature (see icm_read_overlaps)."""
+        shape = (self.n_inst, self.nT)
+        q, q2, ql = (np.empty(shape, dtype=np.float64) for _ in range(3))
+        h = np.empty(shape + (self.N + 1,), dtype=np.int64) if hist else None
+        self.ctx.check(self._lib.icm_read_overlaps(self._h, q.ctypes.data, q2.ctypes.data, ql.ctypes.data,
+                                                   None if h is None else h.ctypes.data))
+        return q, q2, ql, h
 
     def read_spins(self, out=None):
         if out is None:

@@ -420,3 +420,27 @@ def test_invalid_arguments(icm):
     with pytest.raises(icmpt.IcmError):
         icmpt.Batch(ctx, O.SQUARE2D, 256, I.PM_J, I.couplings(2 * 256 * 256, I.PM_J, 0, [0]), T, 1.0, 0)
     del J
+
+
+def test_read_overlaps_equals_oracle_averages(icm):
+    """icm_read_overlaps normalises the accumulators into <q>, <q^2>, <q_l> and
+    the counts of n; for +-J they equal the oracle's averages (same chain)."""
+    icmpt, ctx = icm
+    T = I.ladder(0.3, 2.0, 8)
+    g, J, s0, ids = _setup(O.CUBIC3D, 4, I.PM_J, 2, T, 0x0E)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 4, I.PM_J, J, T, 1.2, 0x0E, spins=s0)
+    b.set_schedule(t_meas=30)
+    b.run(90)
+    q, q2, ql, h = b.read_overlaps()
+    for a in range(2):
+        r = _oracle(g, J[a], s0[a], T, 1.2, 0x0E, a, I.PM_J, t_meas=30)
+        r.run(90)
+        ob = r.observables()
+        assert np.allclose(q[a], 1.0 - 2.0 * ob["n_frac"], rtol=0, atol=1e-12)
+        assert np.allclose(q2[a], ob["q2"], rtol=0, atol=1e-12)
+        assert np.allclose(ql[a], ob["q_l"], rtol=0, atol=1e-12)
+        assert np.array_equal(h[a], r.hist)
+    b.clear_observables()
+    q, q2, ql, _ = b.read_overlaps(hist=False)
+    assert np.all(np.isnan(q)) and np.all(np.isnan(ql))      # nothing measured yet
+    b.close()
