@@ -119,6 +119,29 @@ typedef struct {
 /* Create a context on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * (NULL = the legacy default stream) on which all work is enqueued.       */
 icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream);
+
+/* Device-memory hooks for a context (no counterpart in the paper: a host
+ * facility, so that a framework's caching allocator, e.g. PyTorch's, can own
+ * the library's device memory).  alloc returns `bytes` of device memory
+ * usable on `stream` (NULL on failure); free releases a block that alloc
+ * returned, with the same size.  Calls come from the thread that calls the
+ * library, never from device work.                                         */
+typedef struct {
+    void *(*alloc)(size_t bytes, int32_t device, void *stream, void *user);
+    void (*free)(void *ptr, size_t bytes, int32_t device, void *stream, void *user);
+    void *user;
+} icm_allocator;
+/* As icm_ctx_create, plus a device-memory budget and allocator.
+ *   hbm_budget : bytes of device memory the context's batches may hold at
+ *                once (0 = no limit); an allocation past it fails with
+ *                ICM_ERR_BUDGET and the call that needed it fails cleanly.
+ *   alloc      : NULL = cudaMalloc / cudaFree; else copied into the context
+ *                and used for every batch allocation (state, staging,
+ *                scratch, tuning snapshots).                               */
+icm_status icm_ctx_create_ex(icm_ctx **out, int32_t device, void *cuda_stream, size_t hbm_budget,
+                             const icm_allocator *alloc);
+/* Device bytes the context's batches hold now, and its budget (0 = none). */
+icm_status icm_ctx_memory(const icm_ctx *ctx, size_t *in_use, size_t *budget);
 /* Destroys the context and every batch still alive on it (their handles
  * become invalid). */
 icm_status icm_ctx_destroy(icm_ctx *ctx);

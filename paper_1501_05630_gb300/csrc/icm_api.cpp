@@ -24,6 +24,10 @@ struct icm_ctx {
     int max_smem_optin = 0;
     std::string err = "no error";
     std::set<icm_batch *> batches;   // live batches, freed with the context
+    size_t budget = 0;               // device bytes the batches may hold (0 = no limit)
+    size_t in_use = 0;               // device bytes they hold now
+    bool hooked = false;             // allocations go through `alloc`
+    icm_allocator alloc{};
 };
 
 namespace {
@@ -267,7 +271,7 @@ struct icm_batch {
     int threads = 0, grid = 0, ctas_per_sm = 0, n_icm = 0;
     size_t thr_swap_cap = 0;      // entries allocated for the +-J swap thresholds
     int64_t launches = 0;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;   // device blocks and their sizes
     // staging buffers for loads and reads
     void *raw_coup = nullptr;     // [n_inst][Nb] int8 or float
     int8_t *raw_spins = nullptr;  // [n_inst][R][N]
@@ -317,16 +321,47 @@ icm_status cuda_fail(icm_ctx *ctx, cudaError_t e, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
     } while (0)
 
+// Device memory of a context: through its allocator hooks or cudaMalloc,
+// counted against its budget.
+icm_status ctx_alloc(icm_ctx *ctx, void **p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    if (ctx->budget && ctx->in_use + bytes > ctx->budget)
+        return fail(ctx, ICM_ERR_BUDGET, "device memory budget exceeded (" + std::to_string(ctx->in_use + bytes) +
+                                             " > " + std::to_string(ctx->budget) + " bytes)");
+    if (ctx->hooked) {
+        *p = ctx->alloc.alloc(bytes, ctx->device, (void *)ctx->stream, ctx->alloc.user);
+        if (!*p) return fail(ctx, ICM_ERR_OOM, "allocator hook returned NULL");
+    } else {
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            *p = nullptr;
+            return fail(ctx, ICM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+    }
+    ctx->in_use += bytes;
+    return ICM_OK;
+}
+
+void ctx_free(icm_ctx *ctx, void *p, size_t bytes)
+{
+    if (!p) return;
+    if (bytes == 0) bytes = 16;
+    if (ctx->hooked) ctx->alloc.free(p, bytes, ctx->device, (void *)ctx->stream, ctx->alloc.user);
+    else cudaFree(p);
+    ctx->in_use -= bytes;
+}
+
 template <typename T>
 icm_status dalloc(icm_batch *b, T **p, size_t count)
 {
     void *q = nullptr;
-    cudaError_t e = cudaMalloc(&q, count * sizeof(T) > 0 ? count * sizeof(T) : 16);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return fail(b->ctx, ICM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-    }
-    b->allocs.push_back(q);
+    const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    icm_status st = ctx_alloc(b->ctx, &q, bytes);
+    if (st) return st;
+    b->allocs.push_back({q, bytes});
     *p = (T *)q;
     return ICM_OK;
 }
@@ -436,7 +471,7 @@ void destroy_batch(icm_batch *b)
         cudaStreamSynchronize(b->ctx->stream);
         b->ctx->batches.erase(b);
     }
-    for (void *p : b->allocs) cudaFree(p);
+    for (auto &a : b->allocs) ctx_free(b->ctx, a.first, a.second);
     delete b;
 }
 
@@ -450,6 +485,10 @@ void set_ctx_error(icm_ctx *ctx, const std::string &msg)
 }
 cudaStream_t ctx_stream(const icm_ctx *ctx) { return ctx->stream; }
 int ctx_device(const icm_ctx *ctx) { return ctx->device; }
+// device memory of the context (its allocator and budget) for the other
+// translation units; the status is ICM_OK, ICM_ERR_BUDGET or ICM_ERR_OOM
+icm_status ctx_device_alloc(icm_ctx *ctx, void **p, size_t bytes) { return ctx_alloc(ctx, p, bytes); }
+void ctx_device_free(icm_ctx *ctx, void *p, size_t bytes) { ctx_free(ctx, p, bytes); }
 
 }  // namespace icm
 
@@ -500,7 +539,14 @@ extern "C" {
 
 icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream)
 {
+    return icm_ctx_create_ex(out, device, cuda_stream, 0, nullptr);
+}
+
+icm_status icm_ctx_create_ex(icm_ctx **out, int32_t device, void *cuda_stream, size_t hbm_budget,
+                             const icm_allocator *alloc)
+{
     if (!out) return ICM_ERR_ARG;
+    if (alloc && (!alloc->alloc || !alloc->free)) return ICM_ERR_ARG;
     *out = nullptr;
     icm_ctx *ctx = new (std::nothrow) icm_ctx();
     if (!ctx) return ICM_ERR_OOM;
@@ -514,7 +560,20 @@ icm_status icm_ctx_create(icm_ctx **out, int32_t device, void *cuda_stream)
         delete ctx;
         return ICM_ERR_CUDA;
     }
+    ctx->budget = hbm_budget;
+    if (alloc) {
+        ctx->hooked = true;
+        ctx->alloc = *alloc;
+    }
     *out = ctx;
+    return ICM_OK;
+}
+
+icm_status icm_ctx_memory(const icm_ctx *ctx, size_t *in_use, size_t *budget)
+{
+    if (!ctx) return ICM_ERR_ARG;
+    if (in_use) *in_use = ctx->in_use;
+    if (budget) *budget = ctx->budget;
     return ICM_OK;
 }
 
@@ -1262,11 +1321,7 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
     };
     icm_status st = ICM_OK;
     for (auto &pc : pieces) {
-        if (cudaMalloc(&pc.save, pc.bytes) != cudaSuccess) {
-            (void)cudaGetLastError();
-            st = fail(ctx, ICM_ERR_OOM, "autotune snapshot");
-            break;
-        }
+        if ((st = ctx_alloc(ctx, &pc.save, pc.bytes))) break;
         if (cudaMemcpyAsync(pc.save, pc.dst, pc.bytes, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
             st = fail(ctx, ICM_ERR_CUDA, "autotune snapshot copy");
             break;
@@ -1320,7 +1375,7 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
         }
     cudaStreamSynchronize(ctx->stream);
     for (auto &pc : pieces)
-        if (pc.save) cudaFree(pc.save);
+        if (pc.save) ctx_free(ctx, pc.save, pc.bytes);
     icm_status st2 = st ? apply_cluster(b, original_k, original) : apply_cluster(b, best_k, best);
     if (st) return st;
     if (st2) return st2;

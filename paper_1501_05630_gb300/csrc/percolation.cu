@@ -11,6 +11,8 @@
 
 namespace icm {
 void set_ctx_error(icm_ctx *ctx, const std::string &msg);
+icm_status ctx_device_alloc(icm_ctx *ctx, void **p, size_t bytes);
+void ctx_device_free(icm_ctx *ctx, void *p, size_t bytes);
 cudaStream_t ctx_stream(const icm_ctx *ctx);
 }  // namespace icm
 
@@ -132,10 +134,23 @@ icm_status percolation(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t n_masks
     uint16_t *d_nbr = nullptr, *d_p2s = nullptr;
     uint8_t *d_masks = nullptr;
     int32_t *d_out = nullptr;
-    cudaError_t e = cudaMalloc(&d_nbr, tab.nbr.size() * 2);
-    if (e == cudaSuccess) e = cudaMalloc(&d_p2s, tab.pos2site.size() * 2);
-    if (e == cudaSuccess && masks && !dev) e = cudaMalloc(&d_masks, (size_t)n_masks * N);
-    if (e == cudaSuccess && !dev) e = cudaMalloc(&d_out, (size_t)n_masks * 4);
+    const size_t b_nbr = tab.nbr.size() * 2, b_p2s = tab.pos2site.size() * 2;
+    const size_t b_masks = (size_t)n_masks * N, b_out = (size_t)n_masks * 4;
+    icm_status ast = icm::ctx_device_alloc(ctx, (void **)&d_nbr, b_nbr);
+    if (!ast) ast = icm::ctx_device_alloc(ctx, (void **)&d_p2s, b_p2s);
+    if (!ast && masks && !dev) ast = icm::ctx_device_alloc(ctx, (void **)&d_masks, b_masks);
+    if (!ast && !dev) ast = icm::ctx_device_alloc(ctx, (void **)&d_out, b_out);
+    auto release = [&]() {
+        icm::ctx_device_free(ctx, d_nbr, b_nbr);
+        icm::ctx_device_free(ctx, d_p2s, b_p2s);
+        icm::ctx_device_free(ctx, d_masks, b_masks);
+        icm::ctx_device_free(ctx, d_out, b_out);
+    };
+    if (ast) {
+        release();
+        return ast;
+    }
+    cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_nbr, tab.nbr.data(), tab.nbr.size() * 2, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_p2s, tab.pos2site.data(), tab.pos2site.size() * 2, cudaMemcpyHostToDevice, st);
@@ -154,10 +169,8 @@ icm_status percolation(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t n_masks
     }
     if (e == cudaSuccess && !dev) e = cudaMemcpyAsync(smax, d_out, (size_t)n_masks * 4, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(d_nbr);
-    cudaFree(d_p2s);
-    if (d_masks) cudaFree(d_masks);
-    if (d_out) cudaFree(d_out);
+    else cudaStreamSynchronize(st);            // nothing may still use the blocks freed below
+    release();
     if (e != cudaSuccess) {
         icm::set_ctx_error(ctx, std::string("icm_percolation: ") + cudaGetErrorString(e));
         return ICM_ERR_CUDA;

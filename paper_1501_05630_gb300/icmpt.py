@@ -43,7 +43,7 @@ class Schedule(ctypes.Structure):
 
 
 EXPORTS = [
-    "icm_ctx_create", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_query", "icm_lattice_size",
+    "icm_ctx_create", "icm_ctx_create_ex", "icm_ctx_memory", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_query", "icm_lattice_size",
     "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
     "icm_read_couplings", "icm_read_overlaps", "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables",
@@ -98,6 +98,8 @@ def load_library(path: str = LIB_PATH):
         L = ctypes.CDLL(path)
         vp, i32, u32, u64, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int64
         L.icm_ctx_create.argtypes = [ctypes.POINTER(vp), i32, vp]
+        L.icm_ctx_create_ex.argtypes = [ctypes.POINTER(vp), i32, vp, ctypes.c_size_t, vp]
+        L.icm_ctx_memory.argtypes = [vp, vp, vp]
         L.icm_ctx_destroy.argtypes = [vp]
         L.icm_last_error.argtypes = [vp]
         L.icm_last_error.restype = ctypes.c_char_p
@@ -183,18 +185,61 @@ def _ptr(a):
     raise TypeError(f"unsupported buffer type {type(a)}")
 
 
-class Context:
-    """A device and a stream (a cudaStream_t handle as int, or None)."""
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p)
 
-    def __init__(self, device: int = 0, stream=None):
+
+class _Allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
+def _torch_allocator() -> _Allocator:
+    """Hooks that hand the library's device memory to PyTorch's caching
+    allocator (blocks tied to the context's stream)."""
+    import torch
+
+    def alloc(nbytes, device, stream, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), int(device), int(stream or 0))
+        except Exception:          # out of memory: the library reports ICM_ERR_OOM
+            return None
+
+    def free(ptr, nbytes, device, stream, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return _Allocator(_ALLOC_FN(alloc), _FREE_FN(free), None)
+
+
+class Context:
+    """A device and a stream (a cudaStream_t handle as int, or None).
+
+    hbm_budget: device bytes the context's batches may hold at once (0 = no
+    limit; past it calls fail with ICM_ERR_BUDGET).  allocator: None
+    (cudaMalloc) or "torch" (PyTorch's caching allocator owns the memory)."""
+
+    def __init__(self, device: int = 0, stream=None, hbm_budget: int = 0, allocator=None):
         self._lib = load_library()
         h = ctypes.c_void_p()
         st = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
-        rc = self._lib.icm_ctx_create(ctypes.byref(h), int(device), st)
+        self._alloc = None
+        if hbm_budget or allocator is not None:
+            if allocator not in (None, "torch"):
+                raise ValueError("allocator must be None or 'torch'")
+            self._alloc = _torch_allocator() if allocator == "torch" else None
+            rc = self._lib.icm_ctx_create_ex(ctypes.byref(h), int(device), st, int(hbm_budget),
+                                             None if self._alloc is None else ctypes.byref(self._alloc))
+        else:
+            rc = self._lib.icm_ctx_create(ctypes.byref(h), int(device), st)
         if rc:
             raise IcmError(rc, "icm_ctx_create failed (no CUDA device?)")
         self._h = h
         self._batches = weakref.WeakSet()
+
+    def memory(self):
+        """(device bytes held by the context's batches, budget or 0)."""
+        used, budget = ctypes.c_size_t(), ctypes.c_size_t()
+        self.check(self._lib.icm_ctx_memory(self._h, ctypes.byref(used), ctypes.byref(budget)))
+        return used.value, budget.value
 
     def check(self, rc: int):
         if rc:
