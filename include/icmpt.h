@@ -339,7 +339,8 @@ typedef struct {
     double T_icm;
     uint64_t seed;
     uint32_t instance_id;      /* < 2^24 */
-    const void *couplings;     /* host [N_b] in bond order, int8 or float32 (copied) */
+    const void *couplings;     /* host [N_b] in bond order, int8 or float32 (copied), or NULL =
+                                  drawn from seed and instance_id (see icm_batch_create) */
     const int8_t *spins;       /* host [2 n_T][N] +-1, or NULL = all +1 (copied) */
 } icm_request;
 typedef struct {

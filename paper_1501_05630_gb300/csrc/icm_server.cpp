@@ -231,7 +231,7 @@ icm_status admit(icm_server *s)
             continue;
         }
         const int slot = c->free.back();
-        icm_status e = icm_batch_set_slot(c->batch, slot, r.couplings.data(),
+        icm_status e = icm_batch_set_slot(c->batch, slot, r.couplings.empty() ? nullptr : r.couplings.data(),
                                           r.spins.empty() ? nullptr : r.spins.data(), r.instance_id, 0);
         if (e == ICM_OK) e = icm_batch_start_window(c->batch, slot, s->cfg.quantum);   // first window [Q, 2Q)
         if (e != ICM_OK) {
@@ -351,7 +351,6 @@ icm_status icm_server_submit(icm_server *s, const icm_request *r, uint64_t *tick
     for (int k = 0; k < r->n_T; ++k)
         if (!(r->T[k] > 0.0) || !std::isfinite(r->T[k]) || (k && !(r->T[k] > r->T[k - 1])))
             return fail(s, ICM_ERR_ARG, "temperatures must be finite, > 0 and strictly ascending");
-    if (!r->couplings) return fail(s, ICM_ERR_ARG, "couplings are required");
     if (r->instance_id >= (1u << 24)) return fail(s, ICM_ERR_ARG, "instance ids must be < 2^24");
     if (class_bytes(r->lattice, N, Nb, r->n_T, r->disorder == ICM_GAUSS, s->cfg.slots_per_class) >
         s->cfg.hbm_budget)
@@ -366,7 +365,8 @@ icm_status icm_server_submit(icm_server *s, const icm_request *r, uint64_t *tick
     q.seed = r->seed;
     q.instance_id = r->instance_id;
     const size_t cb = (size_t)Nb * (r->disorder == ICM_GAUSS ? 4 : 1);
-    q.couplings.assign((const unsigned char *)r->couplings, (const unsigned char *)r->couplings + cb);
+    if (r->couplings)   // else drawn from the request's seed and instance id when it is admitted
+        q.couplings.assign((const unsigned char *)r->couplings, (const unsigned char *)r->couplings + cb);
     if (r->spins) q.spins.assign(r->spins, r->spins + (size_t)2 * r->n_T * N);
     icm_result res{};
     res.status = ICM_PENDING;

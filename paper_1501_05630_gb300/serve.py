@@ -43,7 +43,7 @@ class Request:
     T_icm: float
     seed: int
     instance_id: int
-    couplings: np.ndarray
+    couplings: np.ndarray | None   # None: drawn from seed and instance_id by the library
     spins: np.ndarray | None = None
     arrival: float = 0.0          # time.perf_counter() seconds; 0 = the submit time
 
@@ -107,11 +107,12 @@ class Server:
     # -- public API
     def submit(self, req: Request) -> int:
         T = np.ascontiguousarray(req.T, dtype=np.float64)
-        J = np.ascontiguousarray(req.couplings, dtype=np.float32 if req.disorder == icmpt.GAUSS else np.int8)
+        J = None if req.couplings is None else \
+            np.ascontiguousarray(req.couplings, dtype=np.float32 if req.disorder == icmpt.GAUSS else np.int8)
         s = None if req.spins is None else np.ascontiguousarray(req.spins, dtype=np.int8)
         r = icmpt._Request(int(req.lattice), int(req.L), int(req.disorder), len(T), T.ctypes.data,
                            float(req.T_icm), int(req.seed) & 0xFFFFFFFFFFFFFFFF, int(req.instance_id),
-                           J.ctypes.data, None if s is None else s.ctypes.data)
+                           None if J is None else J.ctypes.data, None if s is None else s.ctypes.data)
         t = ctypes.c_uint64()
         self._check(self._lib.icm_server_submit(self._h, ctypes.byref(r), ctypes.byref(t)))   # arrays copied
         if not req.arrival:

@@ -157,6 +157,31 @@ def test_server_results_equal_each_instance_alone(gpu):
 
 
 @pytest.mark.gpu
+def test_server_draws_couplings_when_none_given(gpu):
+    """Requests without couplings get the disorder drawn from their seed and
+    instance id: each result equals the instance replayed alone from a batch
+    that draws the same couplings."""
+    icmpt, ctx = gpu
+    from paper_1501_05630_gb300.serve import Request, Server
+    reqs = []
+    for i in range(6):
+        lat, L = (I.SQUARE2D, 8) if i % 2 else (I.CUBIC3D, 4)
+        reqs.append(Request(lat, L, I.PM_J, I.ladder(0.3, 1.5, 8), 1.0, 13, 2000 + i, None, None))
+    srv = Server(slots_per_class=2, quantum=16, eps_e=0.02, eps_ql=0.05, need=2, max_sweeps=256)
+    tickets = [srv.submit(r) for r in reqs]
+    srv.run_until_idle()
+    for t, q in zip(tickets, reqs):
+        r = srv.poll(t)
+        a = icmpt.Batch(ctx, q.lattice, q.L, q.disorder, None, q.T, q.T_icm, q.seed, instance_ids=[q.instance_id])
+        a.set_schedule(t_meas=r.sweeps // 2)
+        a.run(r.sweeps)
+        oa = a.read_observables(hist=False)
+        assert oa.accE[0, 0] == r.accE and oa.acc_d[0, 0] == r.acc_d and oa.n_meas[0] == r.n_meas
+        a.close()
+    srv.close()
+
+
+@pytest.mark.gpu
 def test_batch_delta_matches_host(gpu):
     icmpt, ctx = gpu
     T = I.ladder(0.5, 2.0, 6)
