@@ -206,6 +206,37 @@ def test_gauss_energy_conservation_and_consistency(icm):
     assert moves > 100
 
 
+def test_gauss_3d_L8_full_workload_invariants(icm):
+    """The 3D L=8 Gaussian workload at its full size and launch shape (1000
+    instances, 24 temperatures, ICM at 17, one launch of 256 sweeps, 128
+    threads, 7 CTAs per SM): every cluster move of the last sweep keeps
+    E_a + E_b to 1e-5 sum|J|, and every instance's device energies equal the
+    energies recomputed from its spins in fp64 to 2e-5 sum|J|."""
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 2.0, 24)
+    seed = 0x1501056300000002
+    n = 1000
+    g, J, s0, ids = _setup(O.CUBIC3D, 8, I.GAUSS, n, T, seed)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    info = b.info()
+    assert (info["threads"], info["ctas_per_sm"], info["grid"]) == (128, 7, 1000)
+    b.set_schedule(trace=1)
+    b.run(256)
+    tr = b.read_trace()
+    scale = np.abs(J).astype(np.float64).sum(1)
+    icm_k = tr["n_pre"] >= 0
+    assert icm_k.sum() == 17 * n
+    err = np.abs(tr["esum_after"] - tr["esum_before"])[icm_k]
+    assert np.all(err <= 1e-5 * np.repeat(scale[:, None], 24, 1)[icm_k])
+    spins, E = b.read_spins(), b.read_energies()
+    Jd = J.astype(np.float64)
+    for a in range(n):
+        e_ref = -((spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64) @ Jd[a])
+        assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a]), a
+    assert np.array_equal(b.read_sweeps(), np.full(n, 256))
+    b.close()
+
+
 def _stats(samples):
     s = np.asarray(samples, dtype=np.float64)
     return s.mean(0), s.std(0, ddof=1) / math.sqrt(len(s))
