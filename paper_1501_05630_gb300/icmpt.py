@@ -8,6 +8,7 @@ the library has not been built, importing works but creating a Context raises
 from __future__ import annotations
 
 import ctypes
+import sys
 import os
 import threading
 import weakref
@@ -264,10 +265,17 @@ class Context:
             self._h = None
 
     def __del__(self):
+        # at interpreter exit PyTorch may already be torn down: a context whose
+        # memory it owns is left to the process exit instead of freed through it
+        if self._alloc_is_torch() and sys.is_finalizing():
+            return
         try:
             self.close()
         except Exception:
             pass
+
+    def _alloc_is_torch(self) -> bool:
+        return getattr(self, "_alloc", None) is not None
 
 
 def largest_clusters(ctx: Context, lattice: int, L: int, masks) -> np.ndarray:
@@ -520,6 +528,8 @@ class Batch:
         self._h = None
 
     def __del__(self):
+        if self.ctx._alloc_is_torch() and sys.is_finalizing():
+            return                              # see Context.__del__
         try:
             self.close()
         except Exception:
