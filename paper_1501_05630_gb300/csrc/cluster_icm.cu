@@ -13,8 +13,10 @@
 //    barrier, every CTA adds the K shares in rank order (the same E in all);
 //  * ICM: per-CTA overlap counts, barrier, every CTA finds the seed's owner
 //    from the K counts (position order = (colour, rank, local)), the owner
-//    plants it, barrier; growth rounds end with a barrier and the OR of the
-//    K CTAs' round flags; flip, barrier, copy-a energies summed as above;
+//    plants it, barrier; growth in rounds of a few in-place scans without
+//    barriers, each round ending with a barrier after which every CTA reads
+//    the round stamp that growing warps pushed into all CTAs; flip, barrier,
+//    copy-a energies summed as above;
 //  * PT: every CTA holds the same energies and draws the same numbers, so
 //    all make the same decisions and permute their own words; barrier;
 //  * observables: per-CTA counts, barrier, rank 0 accumulates.
@@ -71,6 +73,12 @@ __device__ __forceinline__ uint32_t cl_ld(uint32_t addr)
     uint32_t v;
     asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
     return v;
+}
+
+
+__device__ __forceinline__ void cl_st(uint32_t addr, uint32_t v)
+{
+    asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
 
 template <typename T>
@@ -410,34 +418,45 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         __syncthreads();
         return;                                      // the same decision in every CTA
     }
+    // Growth in cluster rounds of kScansPerRound scans of the own sites each,
+    // updated in place; within a round the CTAs scan without barriers, reading
+    // each other's words as they are.  A warp that grew a site writes the
+    // round's stamp into the stamp word of every CTA of the cluster; after the
+    // round's barrier each CTA reads its own word, so all CTAs decide alike.
+    // The growth ends after a round in which nothing grew: every read of that
+    // round saw the state that the previous barrier published, and no site
+    // could grow from it, so it is the fixed point, each seed's component of
+    // q = -1.  Stamps are (t << 16) + round + 1 (at most N < 2^16 rounds), so
+    // words need no reset; a stale equal value could only add one empty round.
+    constexpr int kScansPerRound = 4;
     const uint32_t dC0 = (uint32_t)(L.C0 - L.s), dC1 = (uint32_t)(L.C1 - L.s);
     for (int round = 0;; ++round) {
         int grew = 0;
-        for (int li = tid; li < nls; li += nth) {
-            const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
-            const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
-            const uint32_t c0 = S.C0[li], c1 = S.C1[li];
-            if (d0 == c0 && d1 == c1) continue;
-            uint32_t nb0 = 0u, nb1 = 0u;
+        for (int scan = 0; scan < kScansPerRound; ++scan)
+            for (int li = tid; li < nls; li += nth) {
+                const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
+                const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
+                const uint32_t c0 = S.C0[li], c1 = S.C1[li];
+                if (d0 == c0 && d1 == c1) continue;
+                uint32_t nb0 = 0u, nb1 = 0u;
 #pragma unroll
-            for (int d = 0; d < Z; ++d) {
-                const uint32_t e = S.nb[li * Z + d];
-                nb0 |= cl_ld(e + dC0);
-                if (G > 1) nb1 |= cl_ld(e + dC1);
+                for (int d = 0; d < Z; ++d) {
+                    const uint32_t e = S.nb[li * Z + d];
+                    nb0 |= cl_ld(e + dC0);
+                    if (G > 1) nb1 |= cl_ld(e + dC1);
+                }
+                const uint32_t n0 = c0 | (d0 & nb0), n1 = c1 | (d1 & nb1);
+                if (n0 != c0 || n1 != c1) {
+                    S.C0[li] = n0;
+                    S.C1[li] = n1;
+                    grew = 1;
+                }
             }
-            const uint32_t n0 = c0 | (d0 & nb0), n1 = c1 | (d1 & nb1);
-            if (n0 != c0 || n1 != c1) {
-                S.C0[li] = n0;
-                S.C1[li] = n1;
-                grew = 1;
-            }
-        }
-        const int any_here = __syncthreads_or(grew);
-        if (tid == 0) S.flags[round & 1] = any_here;
+        const uint32_t stamp = (t << 16) + (uint32_t)round + 1u;
+        if (__any_sync(kFull, grew) && lane == 0)
+            for (uint32_t r = 0; r < S.K; ++r) cl_st(cl_map(S.base + L.flags + 4 * (round & 1), r), stamp);
         cl_sync();
-        int any = 0;
-        for (uint32_t r = 0; r < S.K; ++r) any |= (int)cl_ld(cl_map(S.base + L.flags + 4 * (round & 1), r));
-        if (!any) break;
+        if ((uint32_t)S.flags[round & 1] != stamp) break;
     }
 
     // (d) flip the own sites; copy-a energies of the moved pairs
@@ -653,6 +672,7 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
     const int tid = threadIdx.x, nth = blockDim.x;
     const int N = P.N, R = P.R, nT = P.nT, G = P.G, nls = S.nls, hs = S.hs, half = P.half;
 
+    if (tid < 2) S.flags[tid] = 0;   // growth round stamps (the same in every CTA at all times)
     // neighbour table: cluster-window address of each neighbour's spin word
     for (int i = tid; i < nls * Z; i += nth) {
         const int li = i / Z, d = i % Z;

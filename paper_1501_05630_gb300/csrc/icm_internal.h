@@ -132,7 +132,7 @@ struct ClusterLayout {
     int rtab;       // thresholds (+-J) or -2 beta log2(e) (Gaussian), as in SmemLayout
     int mask;       // uint32 [32][NWl]         overlap masks of the ICM pairs
     int cntloc;     // int32 [2][32]            q = -1 sites per colour block and pair (read remotely)
-    int flags;      // int32 [2]                growth-round flags, by round parity (read remotely)
+    int flags;      // uint32 [2]               growth-round stamps, by round parity (written remotely)
     int seed;       // int32 [32]               1 = the pair moves
     int esum;       // float or int32 [32]
     int flipw;      // uint32 [2]
