@@ -70,6 +70,24 @@ def test_no_cpu_fallback_without_gpu(lib_path):
         icmpt.Context(0)
 
 
+def test_context_options_checked_on_host(lib_path):
+    """Context options are validated before any device call; without a GPU a
+    budgeted context fails loudly like a plain one."""
+    import torch
+    from paper_1501_05630_gb300 import icmpt
+    with pytest.raises(ValueError):
+        icmpt.Context(0, allocator="numpy")
+    lib = ctypes.CDLL(lib_path)
+    lib.icm_ctx_create_ex.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]
+    assert lib.icm_ctx_create_ex(None, 0, None, 0, None) == -1            # ICM_ERR_ARG: no out pointer
+    bad = (ctypes.c_void_p * 3)(None, None, None)                        # allocator without its functions
+    h = ctypes.c_void_p()
+    assert lib.icm_ctx_create_ex(ctypes.byref(h), 0, None, 0, ctypes.byref(bad)) == -1
+    if not torch.cuda.is_available():
+        with pytest.raises(icmpt.IcmError):
+            icmpt.Context(0, hbm_budget=1 << 20)
+
+
 def test_missing_library_fails_loudly(tmp_path):
     from paper_1501_05630_gb300 import icmpt
     with pytest.raises(RuntimeError):
