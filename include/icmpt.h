@@ -266,6 +266,12 @@ icm_status icm_clear_observables(icm_batch *b);
 icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t *seed_site,
                           int32_t *csize, double *esum_before, double *esum_after,
                           uint8_t *swap_acc, uint32_t flags);
+/* The moved clusters of the last traced sweep: out [n_inst][n_T][N] uint8
+ * (host), 1 where site i (site order) belongs to the cluster that step 2b
+ * flipped at temperature position k; all 0 at a k without a move.  Needs a
+ * run with the schedule's trace flag set (ICM_ERR_STATE otherwise); the
+ * trace then keeps 8 N bytes per instance of device memory.               */
+icm_status icm_read_cluster_masks(icm_batch *b, uint8_t *out);
 
 /* ---------------------------------------------------------------- serving
  * Continuous batching: a batch is a table of slots.  One slot can be

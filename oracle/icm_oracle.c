@@ -221,6 +221,7 @@ typedef struct {                  /* the last sweep only */
     double *esum_before;          /* [nT] E_a + E_b before the cluster move */
     double *esum_after;           /* [nT] E_a + E_b after the cluster move */
     uint8_t *swap_acc;            /* [2][nT-1] */
+    uint8_t *cmask;               /* [nT][N] 1 = site in the moved cluster at k, or NULL */
 } orc_trace;
 
 /* Adjacency built from the bond list: for every site its incident bonds.
@@ -356,6 +357,8 @@ static void cluster_move(const orc_problem *P, orc_state *S, const adjacency *A,
             sb[i] = (int8_t)(-sb[i]);
         }
         if (tr) { tr->seed_site[k] = seed_site; tr->csize[k] = tail; }
+        if (tr && tr->cmask)
+            for (int q = 0; q < tail; ++q) tr->cmask[(size_t)k * N + queue[q]] = 1;
     }
     if (tr) tr->esum_after[k] = energy(P, sa) + energy(P, sb);
 }
@@ -445,6 +448,7 @@ int orc_run(const orc_problem *P, orc_state *S, uint32_t n_sweeps, const orc_tra
                 trs->esum_before[k] = 0.0; trs->esum_after[k] = 0.0;
             }
             for (int q = 0; q < 2 * (nT - 1); ++q) trs->swap_acc[q] = 0;
+            if (trs->cmask) memset(trs->cmask, 0, (size_t)nT * N);
         }
         if (P->enable_metropolis) metropolis_sweep(P, S, &A, diluted); /* step 1 */
         if (P->icm_every > 0 && S->t % (uint32_t)P->icm_every == 0)   /* steps 2a, 2b */

@@ -58,7 +58,7 @@ class _Trace(ctypes.Structure):
     _fields_ = [
         ("n_pre", ctypes.c_void_p), ("flip2a", ctypes.c_void_p), ("seed_site", ctypes.c_void_p),
         ("csize", ctypes.c_void_p), ("esum_before", ctypes.c_void_p), ("esum_after", ctypes.c_void_p),
-        ("swap_acc", ctypes.c_void_p),
+        ("swap_acc", ctypes.c_void_p), ("cmask", ctypes.c_void_p),
     ]
 
 
@@ -177,9 +177,10 @@ class Instance:
             tr = dict(n_pre=np.zeros(nT, np.int32), flip2a=np.zeros(nT, np.int32),
                       seed_site=np.zeros(nT, np.int32), csize=np.zeros(nT, np.int32),
                       esum_before=np.zeros(nT), esum_after=np.zeros(nT),
-                      swap_acc=np.zeros((2, max(nT - 1, 1)), np.uint8))
+                      swap_acc=np.zeros((2, max(nT - 1, 1)), np.uint8),
+                      cmask=np.zeros((nT, self.g.N), np.uint8))
             ct = _Trace(*[_p(tr[f]) for f in ("n_pre", "flip2a", "seed_site", "csize",
-                                              "esum_before", "esum_after", "swap_acc")])
+                                              "esum_before", "esum_after", "swap_acc", "cmask")])
             ptr = ctypes.byref(ct)
         else:
             ptr = None

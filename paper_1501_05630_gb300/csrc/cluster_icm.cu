@@ -464,9 +464,15 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         const uint32_t c0 = S.C0[li], c1 = S.C1[li];
         if (c0) S.s[li] ^= c0 | (c0 << 1);
         if (c1) S.s[nls + li] ^= c1 | (c1 << 1);
-        if (trace)
+        if (trace) {
             for (int w = 0; w < 2; ++w)
                 for (uint32_t b = w ? c1 : c0; b; b &= b - 1u) atomicAdd(&S.csz[16 * w + ((__ffs(b) - 1) >> 1)], 1);
+            if (P.tr_cmask) {
+                uint32_t *cm = P.tr_cmask + ((size_t)slot * N + pos_of(P, S, li)) * 2;
+                cm[0] = c0;
+                cm[1] = c1;
+            }
+        }
     }
     cl_sync();                                       // flipped words of other CTAs are read below
     ET *part = (ET *)S.Epart;
@@ -732,6 +738,12 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
                 }
                 for (int i = tid; i < 2 * (nT - 1); i += nth) P.tr_swap[(size_t)slot * 2 * (nT - 1) + i] = 0;
             }
+            if (trace && P.tr_cmask)                 // every CTA clears its own positions
+                for (int li = tid; li < nls; li += nth) {
+                    uint32_t *cm = P.tr_cmask + ((size_t)slot * N + pos_of(P, S, li)) * 2;
+                    cm[0] = 0u;
+                    cm[1] = 0u;
+                }
             cl_sync();                               // buffers read remotely in the last step are free again
             if (P.enable_metropolis) cl_metropolis<GAUSS, Z>(P, L, S, t, inst);
             if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)

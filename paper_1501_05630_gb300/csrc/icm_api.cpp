@@ -272,6 +272,7 @@ struct icm_batch {
     size_t thr_swap_cap = 0;      // entries allocated for the +-J swap thresholds
     int64_t launches = 0;
     std::vector<std::pair<void *, size_t>> allocs;   // device blocks and their sizes
+    std::vector<uint16_t> h_pos2site;  // [N] site of each colour-major position
     // staging buffers for loads and reads
     void *raw_coup = nullptr;     // [n_inst][Nb] int8 or float
     int8_t *raw_spins = nullptr;  // [n_inst][R][N]
@@ -810,6 +811,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     cudaError_t e = cudaSuccess;
     if (e == cudaSuccess) e = UP(d_nbr, nbr);
     if (e == cudaSuccess) e = UP(d_pos2site, pos2site);
+    b->h_pos2site = pos2site;
     if (e == cudaSuccess) e = UP(d_zdeg, zdeg);
     if (e == cudaSuccess) e = UP(b->edge_bond, edge_bond);
     if (e == cudaSuccess) e = UP(d_id, ids);
@@ -870,6 +872,13 @@ icm_status icm_set_schedule(icm_batch *b, const icm_schedule *s)
 {
     if (!b || !s) return ICM_ERR_ARG;
     if (s->icm_every < 0 || s->swap_every < 0) return fail(b->ctx, ICM_ERR_ARG, "negative schedule period");
+    if (s->trace && !b->kp.tr_cmask) {       // the cluster words of the trace, allocated on first use
+        uint32_t *cm = nullptr;
+        icm_status st = dalloc(b, &cm, (size_t)b->n_inst * 2 * b->kp.N);
+        if (st) return st;
+        ICM_CUDA(b->ctx, cudaMemsetAsync(cm, 0, (size_t)b->n_inst * 2 * b->kp.N * 4, b->ctx->stream));
+        b->kp.tr_cmask = cm;
+    }
     b->sched = *s;
     return ICM_OK;
 }
@@ -1016,6 +1025,26 @@ icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t
         if (esum_before) esum_before[i] = eb[i];
         if (esum_after) esum_after[i] = ea[i];
     }
+    return ICM_OK;
+}
+
+icm_status icm_read_cluster_masks(icm_batch *b, uint8_t *out)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    icm::KParams &P = b->kp;
+    if (!P.tr_cmask) return fail(b->ctx, ICM_ERR_STATE, "no trace recorded (set the schedule's trace flag)");
+    const size_t N = (size_t)P.N;
+    std::vector<uint32_t> w((size_t)b->n_inst * 2 * N);
+    icm_status st = copy_out(b->ctx, w.data(), P.tr_cmask, w.size() * 4, 0u);
+    if (st) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    for (int i = 0; i < b->n_inst; ++i)
+        for (int k = 0; k < P.nT; ++k) {
+            uint8_t *o = out + ((size_t)i * P.nT + k) * N;
+            const int word = k >> 4, bit = 2 * (k & 15);
+            for (size_t p = 0; p < N; ++p)
+                o[b->h_pos2site[p]] = (uint8_t)((w[((size_t)i * N + p) * 2 + word] >> bit) & 1u);
+        }
     return ICM_OK;
 }
 

@@ -98,6 +98,7 @@ struct KParams {
     int32_t *tr_n_pre, *tr_flip2a, *tr_seed, *tr_csize;  // [n_inst][nT]
     float *tr_eb, *tr_ea;                                // [n_inst][nT]
     uint8_t *tr_swap;                                    // [n_inst][2][nT-1]
+    uint32_t *tr_cmask;   // [n_inst][N][2] cluster words of the traced sweep, by position (NULL = off)
     SmemLayout sm;
 };
 

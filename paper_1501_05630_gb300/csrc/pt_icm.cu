@@ -604,10 +604,11 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         return;
     }
     if (trace) {
-        // cluster sizes: counted once per cluster site
+        // cluster sizes: counted once per cluster site; the cluster words themselves
         for (int i = tid; i < 2 * N; i += nth) {
             const uint32_t c = S.C[i];   // word i & 1 of site i >> 1
             for (uint32_t b = c; b; b &= b - 1u) atomicAdd(&S.cnt_d[16 * (i & 1) + ((__ffs(b) - 1) >> 1)], 1);
+            if (P.tr_cmask) P.tr_cmask[(size_t)slot * 2 * N + i] = c;
         }
     }
     __syncthreads();
@@ -851,6 +852,8 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
                     P.tr_ea[o] = 0.f;
                 }
                 for (int i = tid; i < 2 * (nT - 1); i += nth) P.tr_swap[(size_t)slot * 2 * (nT - 1) + i] = 0;
+                if (P.tr_cmask)
+                    for (int i = tid; i < 2 * N; i += nth) P.tr_cmask[(size_t)slot * 2 * N + i] = 0u;
                 __syncthreads();
             }
             if (P.enable_metropolis) {  // step 1

@@ -63,8 +63,10 @@ def _compare(icm, kind, L, nT, T_hi, T_icm, n_inst, sweeps, seed, dilution=0.0, 
         trs = [r.run(step, trace=True) for r in refs]
         done += step
         spins, E, tr = b.read_spins(), b.read_energies(), b.read_trace()
+        cm = b.read_cluster_masks()
         for a, r in enumerate(refs):
             assert np.array_equal(spins[a], r.s), (a, done, "spins")
+            assert np.array_equal(cm[a], trs[a]["cmask"]), (a, done, "cluster masks")
             assert np.array_equal(E[a], r.E), (a, done, E[a], r.E)
             for key in TRACE_KEYS:
                 assert np.array_equal(tr[key][a], trs[a][key]), (a, done, key, tr[key][a], trs[a][key])

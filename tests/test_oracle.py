@@ -382,3 +382,35 @@ def test_binder_crossing_near_printed_threshold(name, kind, sizes, half_window, 
     cross = [ps[j] - d[j] * (ps[j + 1] - ps[j]) / (d[j + 1] - d[j]) for j in i]
     best = min(cross, key=lambda c: abs(c - pc))
     assert abs(best - pc) < tol, (cross, pc)
+
+
+def test_trace_cluster_masks_are_the_moved_components():
+    """The oracle's traced cluster of each move: csize sites, including the
+    seed, connected through bonds present, all with q = -1 in the final state
+    (both copies flip, so the overlap of a moved site stays -1); without PT
+    the configurations stay at their temperatures, so this is checkable."""
+    scipy_sparse = pytest.importorskip("scipy.sparse")
+    from scipy.sparse.csgraph import connected_components
+    g = O.Geometry(O.SQUARE2D, 8)
+    T = I.ladder(0.3, 1.5, 8)
+    J = I.couplings(g.Nb, I.PM_J, 5, [0])[0].astype(np.float64)
+    s0 = I.initial_spins(g.N, 16, 5, [0])[0]
+    r = O.Instance(g, J, T, s0, pm=True, T_icm=1.2, seed=5, inst=0, swap_every=0)
+    moved = 0
+    for _ in range(20):
+        tr = r.run(1, trace=True)
+        for k in range(len(T)):
+            m = tr["cmask"][k].astype(bool)
+            assert m.sum() == tr["csize"][k]
+            if tr["csize"][k] == 0:
+                continue
+            moved += 1
+            assert m[tr["seed_site"][k]]
+            q = r.s[2 * k] * r.s[2 * k + 1]
+            assert np.all(q[m] == -1)
+            sel = np.flatnonzero(m)
+            keep = m[g.bi] & m[g.bj]
+            A = scipy_sparse.coo_matrix((np.ones(keep.sum()), (g.bi[keep], g.bj[keep])), shape=(g.N, g.N))
+            _, lab = connected_components(A, directed=False)
+            assert len(set(lab[sel])) == 1
+    assert moved > 20
