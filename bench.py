@@ -511,15 +511,16 @@ def run_annealing(args):
 
 
 def run_percolation(args):
-    """Binder ratio of the largest-cluster fraction on chimera C_8, C_16, C_32
-    (device-drawn masks) and the crossing estimate of p_c (Supplemental
-    Material prints p_c = 0.3866(3))."""
+    """Binder ratio of the largest-cluster fraction on chimera C_8 .. C_48
+    (device-drawn masks), the crossing estimate of p_c and the exponent nu
+    from the growth of the slope dg/dp with M (the Supplemental Material
+    prints p_c = 0.3866(3), nu = 1.39(1))."""
     import torch
     from paper_1501_05630_gb300 import build, icmpt
     torch.cuda.set_device(0)
     build.build()
     ctx = icmpt.Context(0)
-    sizes, n = (8, 16, 32), args.masks
+    sizes, n = (8, 16, 32, 48), args.masks
     ps = np.round(np.linspace(0.370, 0.400, 7), 4)
     g = {}
     total_sites, t0 = 0, time.perf_counter()
@@ -542,8 +543,24 @@ def run_percolation(args):
            "config": {"workload": "percolation", "lattice": "chimera", "sizes": list(sizes), "masks_per_p": n,
                       "p": ps.tolist()},
            "binder": {f"C{M}": [round(float(x), 4) for x in g[M]] for M in sizes},
-           "crossing_C8_C16": cross(g[8], g[16]), "crossing_C16_C32": cross(g[16], g[32]),
+           "crossings": {f"C{a}_C{b}": cross(g[a], g[b]) for a, b in zip(sizes[:-1], sizes[1:])},
            "paper_pc": 0.3866, "wall_s": wall}
+    # finite-size scaling: near p_c, g depends on (p - p_c) M^(1/nu), so the
+    # slope dg/dp at p_c grows as M^(1/nu).  Slopes: derivative of a cubic fit
+    # of g(p) at the crossing of the two largest sizes; nu from a line through
+    # (log M, log slope) over all sizes but the smallest (the largest
+    # corrections to scaling are there)
+    last = out["crossings"][f"C{sizes[-2]}_C{sizes[-1]}"]
+    p0 = last[0] if last else 0.3866
+    slope = {M: float(np.polyval(np.polyder(np.polyfit(ps, g[M], 3)), p0)) for M in sizes}
+    lm = np.log(np.array(sizes[1:], dtype=np.float64))
+    ls = np.log(np.abs([slope[M] for M in sizes[1:]]))
+    out["binder_slope_at"] = round(float(p0), 4)
+    out["binder_slope"] = {f"C{M}": round(slope[M], 3) for M in sizes}
+    out["nu_pairs"] = {f"C{a}_C{b}": round(float(np.log(b / a) / np.log(slope[b] / slope[a])), 3)
+                       for a, b in zip(sizes[:-1], sizes[1:])}
+    out["nu_fit"] = round(float(1.0 / np.polyfit(lm, ls, 1)[0]), 3)
+    out["paper_nu"] = 1.39
     print(json.dumps(out))
 
 
@@ -562,7 +579,7 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--serving-nT", default="16,24,32")
     ap.add_argument("--alone-sample", type=int, default=1, help="serving: one-at-a-time requests per menu kind")
-    ap.add_argument("--masks", type=int, default=40000)
+    ap.add_argument("--masks", type=int, default=200000)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--log2-max", type=int, default=17)
     ap.add_argument("--log2-max-fig1", type=int, default=14, help="fig1: sweeps = 2^this, measured over the second half")
