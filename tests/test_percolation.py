@@ -24,7 +24,7 @@ def env():
 
 
 @pytest.mark.parametrize("kind,L", [(O.SQUARE2D, 6), (O.SQUARE2D, 32), (O.CUBIC3D, 4), (O.CUBIC3D, 8),
-                                    (O.CHIMERA, 1), (O.CHIMERA, 3), (O.CHIMERA, 16)])
+                                    (O.CHIMERA, 1), (O.CHIMERA, 3), (O.CHIMERA, 16), (O.CHIMERA, 48)])
 def test_largest_clusters_equal_oracle(env, kind, L):
     icmpt, ctx = env
     g = O.Geometry(kind, L)
