@@ -424,6 +424,57 @@ def run_thermalization(args):
     print(json.dumps(out))
 
 
+# Fig. 3 systems: the Table I sizes that 256 instances thermalize within 2^18 sweeps under plain PT
+FIG3 = [
+    dict(name="2D", lattice=I.SQUARE2D, Ls=(16, 24), T=(0.2120, 1.6325, 30), n_c=30),
+    dict(name="chimera", lattice=I.CHIMERA, Ls=(4, 6, 8), T=(0.2120, 1.6325, 30), n_c=19),
+    dict(name="3D", lattice=I.CUBIC3D, Ls=(4, 6, 8), T=(0.4200, 1.8000, 26), n_c=13),
+]
+
+
+def run_fig3(args):
+    """Thermalization times of plain PT and PT+ICM against the system size
+    (reduced Fig. 3): Delta(t) of Eq. 2 over doubling windows up to
+    2^log2_max_fig3 sweeps, thermalization time = first window end from which
+    |Delta| stays within 2 standard errors; a time that is not reached is
+    reported as None (the ratio is then a bound)."""
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    from paper_1501_05630_gb300.experiments import delta_curve, thermalization_time
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = icmpt.Context(0)
+    lm = args.log2_max_fig3
+    out = {"metric": "thermalization_speedup_vs_N", "unit": "PT sweeps / PT+ICM sweeps", "higher_is_better": True,
+           "n_gpus": 1, "data": "synthetic", "config": {"workload": "fig3", "instances": args.instances,
+                                                       "log2_sweeps": [4, lm], "disorder": "Gaussian"},
+           "systems": {}}
+    t0 = time.perf_counter()
+    for sysd in FIG3:
+        T = I.ladder(*sysd["T"])
+        T_icm = float(T[sysd["n_c"] - 1]) + 1e-9
+        rows = []
+        for L in sysd["Ls"]:
+            N, Nb = icmpt.lattice_size(sysd["lattice"], L)
+            seed = 0x1501056300000009 + L
+            J = I.couplings(Nb, I.GAUSS, seed, range(args.instances))
+            s0 = I.initial_spins(N, 2 * len(T), seed, range(args.instances))
+            tt = {}
+            for m in ("pt", "icm"):
+                c = delta_curve(ctx, sysd["lattice"], L, I.GAUSS, J, s0, T, T_icm, seed, m, 4, lm)
+                tt[m] = thermalization_time(c, nsig=2.0)
+            ratio = (tt["pt"] / tt["icm"]) if (tt["pt"] and tt["icm"]) else None
+            row = {"N": N, "t_pt": tt["pt"], "t_icm": tt["icm"], "ratio": ratio}
+            if tt["pt"] is None and tt["icm"]:
+                row["ratio_at_least"] = (1 << lm) / tt["icm"]     # PT not thermalized by the last window
+            rows.append(row)
+        out["systems"][sysd["name"]] = rows
+    largest = [r[-1]["ratio"] for r in out["systems"].values() if r[-1]["ratio"]]
+    out["value"] = float(np.exp(np.mean(np.log(largest)))) if largest else None
+    out["wall_s"] = time.perf_counter() - t0
+    print(json.dumps(out))
+
+
 # Fig. 1 systems: Table I ladders and sizes (N_c cluster temperatures), Gaussian
 # disorder; p_c = site-percolation thresholds the paper quotes
 FIG1 = [
@@ -571,7 +622,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation", "thermalization",
-                                                                   "annealing", "fig1"])
+                                                                   "annealing", "fig1", "fig3"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -583,6 +634,7 @@ def main():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--log2-max", type=int, default=17)
     ap.add_argument("--log2-max-fig1", type=int, default=14, help="fig1: sweeps = 2^this, measured over the second half")
+    ap.add_argument("--log2-max-fig3", type=int, default=18, help="fig3: the last doubling window ends at 2^this")
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--cluster", type=int, default=0, help="run each instance on a thread-block cluster of K CTAs")
     ap.add_argument("--cluster-threads", type=int, default=512)
@@ -598,6 +650,10 @@ def main():
     if args.workload == "thermalization":
         if int(os.environ.get("RANK", "0")) == 0:
             run_thermalization(args)
+        return
+    if args.workload == "fig3":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_fig3(args)
         return
     if args.workload == "fig1":
         if int(os.environ.get("RANK", "0")) == 0:
