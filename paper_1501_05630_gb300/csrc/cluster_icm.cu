@@ -171,9 +171,9 @@ __device__ __forceinline__ int pos_of(const KParams &P, const CS &S, int li)
 // Step 1, one 16-bit pass of colour COLOR over word g (see sweep_pass in
 // pt_icm.cu: the same arithmetic, with neighbour words read through the
 // cluster window).
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uint32_t t, uint32_t inst, int g,
-                                              int COLOR, int H)
+                                              int COLOR, int H, bool tie)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nth = blockDim.x;
@@ -221,7 +221,11 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
                         const float sh = ((sw >> b) & 1u) ? -h : h;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
                         const uint32_t thr = __float2uint_rz(ex2_approx(fmaf(b2l[b], sh, 32.f)));
-                        const bool a = (sh <= 0.f) || (xr < thr);
+                        bool a;
+                        if constexpr (DIL)   // diluted instance: Delta E = 0 accepted with probability 1/2
+                            a = (sh < 0.f) || (sh == 0.f ? (!tie || xr < 0x80000000u) : (xr < thr));
+                        else
+                            a = (sh <= 0.f) || (xr < thr);
                         f8 |= (uint32_t)a << i;
                         acc[b] -= sh;
                         if (a) acc[b] += 2.f * sh;
@@ -244,8 +248,11 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
             c0 >>= sh0;
             c1 >>= sh0;
             c2 >>= sh0;
-            const int z = P.const_z ? P.const_z : (int)S.zdeg[li];
-            flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
+            const int z = (!DIL && P.const_z) ? P.const_z : (int)S.zdeg[li];   // bonds present
+            // always accepted: m = z - 2u <= 0; on a diluted instance only m < 0
+            // (m = 0 takes the threshold entry 2^31, probability 1/2)
+            if constexpr (DIL) flip = ge_bitsliced(c0, c1, c2, 0u, tie ? (z >> 1) + 1 : (z + 1) >> 1) & 0xFFFFu;
+            else flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
             constexpr int TS = thr_stride(Z);
             const uint32_t *thr = S.thr + rbase * TS;
 #pragma unroll
@@ -277,9 +284,9 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
 
 // Step 1 for all replicas; then every CTA's share of the energies, summed
 // over the cluster in rank order.
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 __device__ __forceinline__ void cl_metropolis(const KParams &P, const ClusterLayout &L, const CS &S, uint32_t t,
-                                              uint32_t inst)
+                                              uint32_t inst, bool tie)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int npass = (P.R + 15) >> 4;
@@ -287,7 +294,7 @@ __device__ __forceinline__ void cl_metropolis(const KParams &P, const ClusterLay
     for (int it = 0; it < 2 * npass; ++it) {
         const int color = it >= npass;
         const int pass = it - color * npass;
-        cl_sweep_pass<GAUSS, Z>(P, S, t, inst, pass >> 1, color, pass & 1);
+        cl_sweep_pass<GAUSS, Z, DIL>(P, S, t, inst, pass >> 1, color, pass & 1, tie);
         if (pass == npass - 1) {
             if (color == 0) cl_sync();            // colour 1 reads colour-0 words of other CTAs
             else __syncthreads();
@@ -542,7 +549,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     for (int k = tid; k < nicm; k += nth) {
         if (!S.seed[k]) continue;
         ET ea = cl_sum<ET>(S, L.Epair + 4 * k);
-        if constexpr (!GAUSS) ea = 2 * ea - P.Nb;    // E = 2 U - N_b
+        if constexpr (!GAUSS) ea = 2 * ea - (P.diluted ? P.nb_inst[slot] : P.Nb);   // E = 2 U - N_b (bonds present)
         E[2 * k] = ea;
         E[2 * k + 1] = esum[k] - ea;
         if (trace && S.rank == 0) {
@@ -668,7 +675,7 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
 }
 
 // ---------------------------------------------------------------------------
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KParams P, const ClusterLayout L,
                                                                     uint32_t n_sweeps)
 {
@@ -680,17 +687,21 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
 
     if (tid < 2) S.flags[tid] = 0;   // growth round stamps (the same in every CTA at all times)
     // neighbour table: cluster-window address of each neighbour's spin word
-    for (int i = tid; i < nls * Z; i += nth) {
-        const int li = i / Z, d = i % Z;
-        const int q = P.nbr[pos_of(P, S, li) * Z + d];
-        const int cq = q >= half;
-        const int hq = q - cq * half;
-        const uint32_t rq = (uint32_t)(hq / hs);
-        const int lq = cq * hs + hq % hs;
-        S.nb[i] = cl_map(S.base + L.s, rq) + 4u * (uint32_t)lq;
-    }
-    if (!GAUSS && !P.const_z)
-        for (int li = tid; li < nls; li += nth) S.zdeg[li] = P.zdeg[pos_of(P, S, li)];
+    // (of the batch's lattice here; per instance for diluted batches, below)
+    auto neighbour_table = [&](const uint16_t *nbr, const uint8_t *zdeg) {
+        for (int i = tid; i < nls * Z; i += nth) {
+            const int li = i / Z, d = i % Z;
+            const int q = nbr[pos_of(P, S, li) * Z + d];
+            const int cq = q >= half;
+            const int hq = q - cq * half;
+            const uint32_t rq = (uint32_t)(hq / hs);
+            const int lq = cq * hs + hq % hs;
+            S.nb[i] = cl_map(S.base + L.s, rq) + 4u * (uint32_t)lq;
+        }
+        if (!GAUSS && (DIL || !P.const_z))
+            for (int li = tid; li < nls; li += nth) S.zdeg[li] = zdeg[pos_of(P, S, li)];
+    };
+    if constexpr (!DIL) neighbour_table(P.nbr, P.zdeg);
     if constexpr (GAUSS) {
         for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
     } else {
@@ -719,6 +730,14 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
             }
             if (tid == 0) S.nmeas[0] = P.n_meas[slot];
         }
+        // a diluted instance: its own neighbour table (absent bonds point at the
+        // site itself) and degrees, and zero-energy proposals accepted with
+        // probability 1/2
+        bool tie = false;
+        if constexpr (DIL) {
+            neighbour_table(P.nbr_inst + (size_t)slot * N * Z, P.zdeg_inst + (size_t)slot * N);
+            tie = P.nb_inst[slot] < P.Nb;
+        }
         const uint32_t inst = P.inst_id[slot];
         const long long t_meas = P.t_meas_inst ? P.t_meas_inst[slot] : P.t_meas;
         uint32_t t = P.tsweep[slot];
@@ -745,7 +764,7 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
                     cm[1] = 0u;
                 }
             cl_sync();                               // buffers read remotely in the last step are free again
-            if (P.enable_metropolis) cl_metropolis<GAUSS, Z>(P, L, S, t, inst);
+            if (P.enable_metropolis) cl_metropolis<GAUSS, Z, DIL>(P, L, S, t, inst, tie);
             if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)
                 cl_cluster_moves<GAUSS, Z>(P, L, S, t, inst, slot, trace);
             if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1) cl_pt_pass<GAUSS>(P, S, t, inst, slot, trace);
@@ -775,11 +794,11 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
     }
 }
 
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 cudaError_t launch_cluster_t(const KParams &P, const ClusterLayout &L, int threads, int n_clusters, uint32_t n_sweeps,
                              cudaStream_t st)
 {
-    auto kern = cluster_kernel<GAUSS, Z>;
+    auto kern = cluster_kernel<GAUSS, Z, DIL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -797,10 +816,10 @@ cudaError_t launch_cluster_t(const KParams &P, const ClusterLayout &L, int threa
     return cudaLaunchKernelEx(&cfg, kern, P, L, n_sweeps);
 }
 
-template <bool GAUSS, int Z>
+template <bool GAUSS, int Z, bool DIL>
 cudaError_t cluster_occupancy_t(int K, int threads, int smem, int *clusters)
 {
-    auto kern = cluster_kernel<GAUSS, Z>;
+    auto kern = cluster_kernel<GAUSS, Z, DIL>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
@@ -870,20 +889,25 @@ ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwar
 cudaError_t launch_cluster(const KParams &P, const ClusterLayout &L, bool gauss, int threads, int n_clusters,
                            uint32_t n_sweeps, cudaStream_t st)
 {
-    if (threads > kMaxThreadsWide || L.K < 1 || L.hs % 32 || P.diluted) return cudaErrorInvalidValue;
-    if (gauss) return P.Z == 4 ? launch_cluster_t<true, 4>(P, L, threads, n_clusters, n_sweeps, st)
-                               : launch_cluster_t<true, 6>(P, L, threads, n_clusters, n_sweeps, st);
-    return P.Z == 4 ? launch_cluster_t<false, 4>(P, L, threads, n_clusters, n_sweeps, st)
-                    : launch_cluster_t<false, 6>(P, L, threads, n_clusters, n_sweeps, st);
+    if (threads > kMaxThreadsWide || L.K < 1 || L.hs % 32) return cudaErrorInvalidValue;
+    if (P.diluted && (!P.nbr_inst || !P.zdeg_inst || !P.nb_inst)) return cudaErrorInvalidValue;
+#define ICM_LAUNCH_CL(G_, Z_)                                                                          \
+    (P.diluted ? launch_cluster_t<G_, Z_, true>(P, L, threads, n_clusters, n_sweeps, st)               \
+               : launch_cluster_t<G_, Z_, false>(P, L, threads, n_clusters, n_sweeps, st))
+    if (gauss) return P.Z == 4 ? ICM_LAUNCH_CL(true, 4) : ICM_LAUNCH_CL(true, 6);
+    return P.Z == 4 ? ICM_LAUNCH_CL(false, 4) : ICM_LAUNCH_CL(false, 6);
+#undef ICM_LAUNCH_CL
 }
 
-cudaError_t cluster_occupancy(bool gauss, int Z, int K, int threads, int smem, int *clusters)
+cudaError_t cluster_occupancy(bool gauss, int Z, bool dil, int K, int threads, int smem, int *clusters)
 {
     if (Z != 4 && Z != 6) return cudaErrorInvalidValue;
-    if (gauss) return Z == 4 ? cluster_occupancy_t<true, 4>(K, threads, smem, clusters)
-                             : cluster_occupancy_t<true, 6>(K, threads, smem, clusters);
-    return Z == 4 ? cluster_occupancy_t<false, 4>(K, threads, smem, clusters)
-                  : cluster_occupancy_t<false, 6>(K, threads, smem, clusters);
+#define ICM_OCC_CL(G_, Z_)                                                                             \
+    (dil ? cluster_occupancy_t<G_, Z_, true>(K, threads, smem, clusters)                                \
+         : cluster_occupancy_t<G_, Z_, false>(K, threads, smem, clusters))
+    if (gauss) return Z == 4 ? ICM_OCC_CL(true, 4) : ICM_OCC_CL(true, 6);
+    return Z == 4 ? ICM_OCC_CL(false, 4) : ICM_OCC_CL(false, 6);
+#undef ICM_OCC_CL
 }
 
 }  // namespace icm

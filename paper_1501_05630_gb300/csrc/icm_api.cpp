@@ -301,6 +301,7 @@ struct icm_batch {
 
 extern "C" {
 static icm_status apply_threads(icm_batch *b, int threads);   // defined with the ABI functions
+static icm_status apply_cluster(icm_batch *b, int K, int threads);
 }
 
 namespace {
@@ -415,11 +416,13 @@ icm_status refresh_dilution(icm_batch *b, int first, int count)
     ICM_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     bool diluted = false;
     for (int32_t v : b->h_nb) diluted |= v < P.Nb;
+    const bool was_diluted = P.diluted != 0;
     P.diluted = diluted ? 1 : 0;
     P.const_z = diluted ? 0 : b->uniform_z;
-    if (diluted && b->cluster_k) {
-        // the cluster layout has no per-instance neighbour tables: back to one CTA per instance
-        icm_status st = apply_threads(b, icm::fused_threads_wide(P.N));
+    if (b->cluster_k && diluted != was_diluted) {
+        // the cluster layout switches to its kernels with per-instance tables
+        // (or back): the clusters that fit are counted again
+        icm_status st = apply_cluster(b, b->cluster_k, b->threads);
         if (st) return st;
     }
     long long n_bad = 0;
@@ -1289,7 +1292,6 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     if (threads < 32 || threads > icm::kMaxThreadsWide || threads % 32)
         return fail(b->ctx, ICM_ERR_ARG, "threads per CTA must be a multiple of 32 in 32..1024");
     if (P.Z != 4 && P.Z != 6) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "the cluster layout takes degrees 4 and 6");
-    if (P.diluted) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "the cluster layout takes undiluted batches");
     const int half = P.N / 2;
     if (half % K || (half / K) % 32)
         return fail(b->ctx, ICM_ERR_UNSUPPORTED, "sites per colour must split into K blocks of a multiple of 32");
@@ -1299,7 +1301,7 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     const icm::ClusterLayout L = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss);
     if (L.total > b->ctx->max_smem_optin) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster slice exceeds shared memory");
     int clusters = 0;
-    cudaError_t e = icm::cluster_occupancy(b->gauss, P.Z, K, threads, L.total, &clusters);
+    cudaError_t e = icm::cluster_occupancy(b->gauss, P.Z, P.diluted != 0, K, threads, L.total, &clusters);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "cluster occupancy");
     if (clusters < 1) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster does not fit");
     b->cluster_k = K;

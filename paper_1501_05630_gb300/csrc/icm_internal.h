@@ -146,7 +146,7 @@ struct ClusterLayout {
 ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss);
 cudaError_t launch_cluster(const KParams &P, const ClusterLayout &CL, bool gauss, int threads, int n_clusters,
                            uint32_t n_sweeps, cudaStream_t st);
-cudaError_t cluster_occupancy(bool gauss, int Z, int K, int threads, int smem, int *clusters);
+cudaError_t cluster_occupancy(bool gauss, int Z, bool dil, int K, int threads, int smem, int *clusters);
 int fused_threads(int N);
 int fused_threads_wide(int N);
 // uint32 words of per-CTA scratch of the wide layout (2 N cluster words, 32

@@ -124,17 +124,23 @@ def test_group_with_cluster_batch_equals_separate_launches(icm):
     grp.close()
 
 
-def test_dilution_leaves_cluster_layout(icm):
+def test_diluted_couplings_keep_the_cluster_layout(icm):
+    """Loading diluted couplings into a clustered batch keeps it on clusters
+    (kernels with per-instance tables); the chain equals the oracle's."""
     icmpt, ctx = icm
     T = I.ladder(0.3, 2.0, 8)
     g, J, s0, ids = _setup(O.CUBIC3D, 8, I.PM_J, 2, T, 5)
     b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.PM_J, J, T, 1.0, 5, spins=s0)
     b.set_cluster(4, 64)
-    b.run(2)
     Jd = I.dilute(J, 0.2, 5, ids)
     b.load(couplings=Jd)
-    assert b.cluster() == 0
-    b.run(2)
-    with pytest.raises(icmpt.IcmError):
-        b.set_cluster(4, 64)
+    assert b.cluster() == 4
+    b.run(9)
+    spins, E = b.read_spins(), b.read_energies()
+    for a in range(2):
+        r = O.Instance(g, Jd[a].astype(np.float64), T, s0[a], pm=True, T_icm=1.0, seed=5, inst=a)
+        r.run(9)
+        assert np.array_equal(spins[a], r.s) and np.array_equal(E[a], r.E)
+    b.load(couplings=J)                                   # back to undiluted couplings
+    assert b.cluster() == 4
     b.close()

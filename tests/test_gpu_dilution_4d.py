@@ -42,7 +42,7 @@ def _couplings(g, dis, seed, ids, dilution, diluted_rows):
 
 
 def _compare(icm, kind, L, nT, T_hi, T_icm, n_inst, sweeps, seed, dilution=0.0, diluted_rows=None,
-             threads=None, check_every=1):
+             threads=None, check_every=1, cluster=None):
     icmpt, ctx = icm
     T = I.ladder(0.2, T_hi, nT)
     g = O.Geometry(kind, L)
@@ -52,6 +52,9 @@ def _compare(icm, kind, L, nT, T_hi, T_icm, n_inst, sweeps, seed, dilution=0.0, 
     b = icmpt.Batch(ctx, kind, L, I.PM_J, J, T, T_icm, seed, spins=s0)
     if threads is not None:
         b.set_threads(threads)
+    if cluster is not None:
+        b.set_cluster(*cluster)
+        assert b.cluster() == cluster[0]
     b.set_schedule(trace=1, t_meas=sweeps // 3)
     assert np.array_equal(b.bond_counts(), np.count_nonzero(J, axis=1))
     refs = [O.Instance(g, J[a].astype(np.float64), T, s0[a], pm=True, T_icm=T_icm, seed=seed, inst=a,
@@ -114,6 +117,20 @@ def test_fully_diluted_every_swap_accepted(icm):
     _compare(icm, O.SQUARE2D, 4, 2, 1.5, 1.0, 1, 6, 0xF1, dilution=1.0)   # one pair: a run of one swap
 
 
+@pytest.mark.parametrize("kind,L,nT,T_hi,T_icm,dilution,rows,cluster", [
+    (O.SQUARE2D, 16, 12, 1.5, 1.0, 0.3, None, (4, 64)),
+    (O.SQUARE2D, 16, 16, 1.5, 1.0, 0.3, [1], (2, 128)),      # diluted and undiluted instances together
+    (O.CUBIC3D, 8, 24, 2.0, 1.0, 0.25, None, (8, 32)),      # two spin words; every z-neighbour remote
+    (O.CHIMERA, 4, 20, 3.0, 1.5, 0.2, None, (2, 64)),       # per-site degrees below 4
+    (O.SQUARE2D, 16, 8, 1.5, 1.0, 0.9, None, (4, 32)),      # mostly isolated sites
+])
+def test_diluted_cluster_layout_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, dilution, rows, cluster):
+    """Diluted batches on thread-block clusters: per-instance neighbour
+    tables in every CTA's slice, bit-exact with the oracle sweep by sweep."""
+    _compare(icm, kind, L, nT, T_hi, T_icm, 3, 24, 0xC1D + L, dilution=dilution, diluted_rows=rows,
+             cluster=cluster)
+
+
 def test_diluted_instance_admitted_into_undiluted_batch(icm):
     """A slot replaced by a diluted instance switches the batch to its diluted
     kernels; every slot still evolves like its instance alone."""
@@ -172,6 +189,37 @@ def test_diluted_gauss_statistics_and_conservation(icm):
         d = gpu[key] - np.asarray(cpu[key])
         mu, se = d.mean(0), d.std(0, ddof=1) / math.sqrt(n)
         assert np.all(np.abs(mu) <= 3.5 * se + 1e-9), (key, mu, se)
+
+
+def test_diluted_gauss_cluster_layout_conservation(icm):
+    """3D L=8 Gaussian with 30% of the bonds absent on clusters of 8 CTAs:
+    every cluster move keeps E_a + E_b to 1e-5 sum|J|, and the device
+    energies equal fp64 energies of the spins over the bonds present."""
+    icmpt, ctx = icm
+    T = I.ladder(0.3, 2.0, 12)
+    seed, n = 778, 4
+    g = O.Geometry(O.CUBIC3D, 8)
+    ids = list(range(n))
+    J = I.dilute(I.couplings(g.Nb, I.GAUSS, seed, ids), 0.3, seed, ids)
+    s0 = I.initial_spins(g.N, 24, seed, ids)
+    b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_cluster(8, 32)
+    assert b.cluster() == 8
+    b.set_schedule(trace=1)
+    scale = np.abs(J).astype(np.float64).sum(1)
+    moves = 0
+    for _ in range(5):
+        b.run(9)
+        tr = b.read_trace()
+        k = tr["n_pre"] >= 0
+        moves += int((tr["csize"] > 0).sum())
+        assert np.all(np.abs(tr["esum_after"] - tr["esum_before"])[k] <= 1e-5 * np.repeat(scale[:, None], 12, 1)[k])
+        spins, E = b.read_spins(), b.read_energies()
+        for a in range(n):
+            e_ref = -((spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64) @ J[a].astype(np.float64))
+            assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a])
+    assert moves > 20
+    b.close()
 
 
 def test_percolation_4d_matches_oracle(icm):
