@@ -479,11 +479,11 @@ icm_status icm_load(icm_batch *b, const void *buf, size_t len);
  * its shared memory and reading its neighbours' words through the cluster's
  * distributed shared memory.  The arithmetic and random keys are those of
  * the one-CTA layouts (the same chain, bit for bit for +-J); a single large
- * instance finishes its sweeps up to K times sooner.  Needs degree 4 or 6
- * lattices (2D, 3D, chimera), an undiluted batch and N/2 divisible into K
- * blocks of a multiple of 32 sites.  K = 0 returns to one CTA per instance
- * (CTA width `threads`, as icm_batch_set_threads).  A batch that becomes
- * diluted returns to one CTA per instance by itself.                      */
+ * instance finishes its sweeps up to K times sooner.  Any lattice kind
+ * (2D, 3D, chimera, 4D), diluted or not, with N/2 divisible into K blocks
+ * of a multiple of 32 sites.  K = 0 returns to one CTA per instance (CTA
+ * width `threads`, as icm_batch_set_threads).  A batch keeps the layout when
+ * couplings with absent bonds are loaded (its kernels change).            */
 icm_status icm_batch_set_cluster(icm_batch *b, int32_t K, int32_t threads);
 icm_status icm_batch_cluster(const icm_batch *b, int32_t *K);
 

@@ -234,7 +234,7 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
                 }
             }
         } else {
-            uint32_t c0 = 0, c1 = 0, c2 = 0;
+            uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;   // bit-planes of u = # unsatisfied bonds
             const uint32_t jb = S.Jb[li];
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
@@ -243,15 +243,23 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
                 c0 ^= u;
                 const uint32_t t1 = c1 & t0;
                 c1 ^= t0;
-                c2 |= t1;
+                if constexpr (Z > 7) {              // u up to 8: a fourth plane
+                    const uint32_t t2 = c2 & t1;
+                    c2 ^= t1;
+                    c3 |= t2;
+                } else {
+                    c2 |= t1;
+                }
             }
             c0 >>= sh0;
             c1 >>= sh0;
             c2 >>= sh0;
+            c3 >>= sh0;
             const int z = (!DIL && P.const_z) ? P.const_z : (int)S.zdeg[li];   // bonds present
             // always accepted: m = z - 2u <= 0; on a diluted instance only m < 0
             // (m = 0 takes the threshold entry 2^31, probability 1/2)
-            if constexpr (DIL) flip = ge_bitsliced(c0, c1, c2, 0u, tie ? (z >> 1) + 1 : (z + 1) >> 1) & 0xFFFFu;
+            if constexpr (DIL) flip = ge_bitsliced(c0, c1, c2, c3, tie ? (z >> 1) + 1 : (z + 1) >> 1) & 0xFFFFu;
+            else if constexpr (Z > 7) flip = (c3 | c2) & 0xFFFFu;   // z = 8: u >= 4
             else flip = ((z <= 4) ? (c2 | c1) : (c2 | (c1 & c0))) & 0xFFFFu;
             constexpr int TS = thr_stride(Z);
             const uint32_t *thr = S.thr + rbase * TS;
@@ -263,7 +271,8 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;
-                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                        const int u = (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2) |
+                                            (((c3 >> b) & 1u) << 3));
                         const int m = z - 2 * u;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
                         const uint32_t th = thr[b * TS + (m > 0 ? m : 0)];
@@ -517,7 +526,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                     acc[jj] += ((sw >> b) & 1u) ? h : -h;
                 }
             } else {
-                uint32_t c0 = 0, c1 = 0, c2 = 0;
+                uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
                 const uint32_t jb = S.Jb[li];
 #pragma unroll
                 for (int d = 0; d < Z; ++d) {
@@ -526,12 +535,19 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                     c0 ^= u;
                     const uint32_t t1 = c1 & t0;
                     c1 ^= t0;
-                    c2 |= t1;
+                    if constexpr (Z > 7) {
+                        const uint32_t t2 = c2 & t1;
+                        c2 ^= t1;
+                        c3 |= t2;
+                    } else {
+                        c2 |= t1;
+                    }
                 }
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                     const int b = 2 * jj;
-                    acc[jj] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2));
+                    acc[jj] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2) |
+                                     (((c3 >> b) & 1u) << 3));
                 }
             }
         }
@@ -894,19 +910,19 @@ cudaError_t launch_cluster(const KParams &P, const ClusterLayout &L, bool gauss,
 #define ICM_LAUNCH_CL(G_, Z_)                                                                          \
     (P.diluted ? launch_cluster_t<G_, Z_, true>(P, L, threads, n_clusters, n_sweeps, st)               \
                : launch_cluster_t<G_, Z_, false>(P, L, threads, n_clusters, n_sweeps, st))
-    if (gauss) return P.Z == 4 ? ICM_LAUNCH_CL(true, 4) : ICM_LAUNCH_CL(true, 6);
-    return P.Z == 4 ? ICM_LAUNCH_CL(false, 4) : ICM_LAUNCH_CL(false, 6);
+    if (gauss) return P.Z == 4 ? ICM_LAUNCH_CL(true, 4) : P.Z == 6 ? ICM_LAUNCH_CL(true, 6) : ICM_LAUNCH_CL(true, 8);
+    return P.Z == 4 ? ICM_LAUNCH_CL(false, 4) : P.Z == 6 ? ICM_LAUNCH_CL(false, 6) : ICM_LAUNCH_CL(false, 8);
 #undef ICM_LAUNCH_CL
 }
 
 cudaError_t cluster_occupancy(bool gauss, int Z, bool dil, int K, int threads, int smem, int *clusters)
 {
-    if (Z != 4 && Z != 6) return cudaErrorInvalidValue;
+    if (Z != 4 && Z != 6 && Z != 8) return cudaErrorInvalidValue;
 #define ICM_OCC_CL(G_, Z_)                                                                             \
     (dil ? cluster_occupancy_t<G_, Z_, true>(K, threads, smem, clusters)                                \
          : cluster_occupancy_t<G_, Z_, false>(K, threads, smem, clusters))
-    if (gauss) return Z == 4 ? ICM_OCC_CL(true, 4) : ICM_OCC_CL(true, 6);
-    return Z == 4 ? ICM_OCC_CL(false, 4) : ICM_OCC_CL(false, 6);
+    if (gauss) return Z == 4 ? ICM_OCC_CL(true, 4) : Z == 6 ? ICM_OCC_CL(true, 6) : ICM_OCC_CL(true, 8);
+    return Z == 4 ? ICM_OCC_CL(false, 4) : Z == 6 ? ICM_OCC_CL(false, 6) : ICM_OCC_CL(false, 8);
 #undef ICM_OCC_CL
 }
 

@@ -1291,7 +1291,7 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     if (K != 2 && K != 4 && K != 8) return fail(b->ctx, ICM_ERR_ARG, "cluster size must be 2, 4 or 8");
     if (threads < 32 || threads > icm::kMaxThreadsWide || threads % 32)
         return fail(b->ctx, ICM_ERR_ARG, "threads per CTA must be a multiple of 32 in 32..1024");
-    if (P.Z != 4 && P.Z != 6) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "the cluster layout takes degrees 4 and 6");
+    if (P.Z != 4 && P.Z != 6 && P.Z != 8) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "the cluster layout takes degrees 4, 6 and 8");
     const int half = P.N / 2;
     if (half % K || (half / K) % 32)
         return fail(b->ctx, ICM_ERR_UNSUPPORTED, "sites per colour must split into K blocks of a multiple of 32");

@@ -123,10 +123,13 @@ def test_fully_diluted_every_swap_accepted(icm):
     (O.CUBIC3D, 8, 24, 2.0, 1.0, 0.25, None, (8, 32)),      # two spin words; every z-neighbour remote
     (O.CHIMERA, 4, 20, 3.0, 1.5, 0.2, None, (2, 64)),       # per-site degrees below 4
     (O.SQUARE2D, 16, 8, 1.5, 1.0, 0.9, None, (4, 32)),      # mostly isolated sites
+    (O.HYPERCUBIC4D, 4, 12, 3.0, 1.5, 0.3, [0], (4, 32)),   # 4D (Z = 8), one diluted instance
+    (O.HYPERCUBIC4D, 8, 8, 3.0, 1.5, 0.0, None, (8, 64)),   # 4D L=8 undiluted, 4096 sites
 ])
 def test_diluted_cluster_layout_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, dilution, rows, cluster):
-    """Diluted batches on thread-block clusters: per-instance neighbour
-    tables in every CTA's slice, bit-exact with the oracle sweep by sweep."""
+    """Diluted batches and 4D lattices on thread-block clusters: per-instance
+    neighbour tables in every CTA's slice, a fourth bit-plane for Z = 8;
+    bit-exact with the oracle sweep by sweep."""
     _compare(icm, kind, L, nT, T_hi, T_icm, 3, 24, 0xC1D + L, dilution=dilution, diluted_rows=rows,
              cluster=cluster)
 
