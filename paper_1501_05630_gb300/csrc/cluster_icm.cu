@@ -391,7 +391,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                                 if (rank < pc) {
                                     for (uint32_t q = 0; q < rank; ++q) w &= w - 1u;
                                     const int li = 32 * m + __ffs(w) - 1;
-                                    atomicOr((k < 16 ? S.C0 : S.C1) + li, 1u << (2 * (k & 15)));
+                                    atomicOr((k < 16 ? S.C0 : S.C1) + ICM_IDX(li, nls, 21), 1u << (2 * (k & 15)));
                                     if (trace) P.tr_seed[(size_t)slot * P.nT + k] = (int)__ldg(P.pos2site + pos_of(P, S, li));
                                     break;
                                 }
@@ -683,7 +683,7 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
             S.acc64[1 * nT + k] += (N - 2 * n) * (N - 2 * n);
             S.acc64[2 * nT + k] += n < N - n ? n : N - n;
             S.acc64[3 * nT + k] += d;
-            atomicAdd(&P.hist[((size_t)slot * nT + k) * (N + 1) + n], 1ull);
+            atomicAdd(&P.hist[((size_t)slot * nT + k) * (N + 1) + ICM_IDX(n, N + 1, 22)], 1ull);
         }
         if (threadIdx.x == 0) S.nmeas[0] += 1;
     }
@@ -707,7 +707,7 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
     auto neighbour_table = [&](const uint16_t *nbr, const uint8_t *zdeg) {
         for (int i = tid; i < nls * Z; i += nth) {
             const int li = i / Z, d = i % Z;
-            const int q = nbr[pos_of(P, S, li) * Z + d];
+            const int q = ICM_IDX(nbr[pos_of(P, S, li) * Z + d], N, 20);
             const int cq = q >= half;
             const int hq = q - cq * half;
             const uint32_t rq = (uint32_t)(hq / hs);
@@ -927,3 +927,18 @@ cudaError_t cluster_occupancy(bool gauss, int Z, bool dil, int K, int threads, i
 }
 
 }  // namespace icm
+
+#ifdef ICM_CHECKED
+// Checked builds: the check word of the thread-block-cluster kernels (guarded
+// neighbour positions, seed sites and histogram bins; site codes 20-22), read
+// like icm_debug_check reads those of the fused kernels.
+extern "C" int icm_debug_check_cluster(unsigned int *out, int reset)
+{
+    if (cudaMemcpyFromSymbol(out, icm::g_icm_check, sizeof(unsigned int) * 4) != cudaSuccess) return -4;
+    if (reset) {
+        unsigned int z[4] = {};
+        if (cudaMemcpyToSymbol(icm::g_icm_check, z, sizeof(z)) != cudaSuccess) return -4;
+    }
+    return 0;
+}
+#endif

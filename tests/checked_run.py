@@ -1,8 +1,8 @@
 """Run by tests/test_checked_build.py in a child process (it is not a test
 module): loads the checked build of the library (every guarded index of the
-fused kernel tested against its bound), runs +-J cases of several shapes and
-layouts against the oracle, bit for bit, and a Gaussian case, then prints the
-check word as JSON.  A child process, so that the checked library is the only
+fused and cluster kernels tested against its bound), runs +-J cases of several
+shapes and layouts against the oracle, bit for bit, and a Gaussian case, then
+prints the check words as JSON.  A child process, so that the checked library is the only
 one loaded."""
 import ctypes
 import json
@@ -20,15 +20,20 @@ from paper_1501_05630_gb300 import build, icmpt, inputs as I  # noqa: E402
 lib = icmpt.load_library(build.build(checked=True))
 lib.icm_debug_check.argtypes = [ctypes.c_void_p, ctypes.c_int]
 lib.icm_debug_check.restype = ctypes.c_int
+lib.icm_debug_check_cluster.argtypes = [ctypes.c_void_p, ctypes.c_int]
+lib.icm_debug_check_cluster.restype = ctypes.c_int
 ctx = icmpt.Context(0)
 
-CASES = [  # lattice, L, n_T, T_max, T_icm, dilution, threads
+CASES = [  # lattice, L, n_T, T_max, T_icm, dilution, threads or (K, threads) of a thread-block cluster
     (O.SQUARE2D, 8, 16, 1.5, 1.0, 0.0, None),
     (O.CUBIC3D, 4, 24, 2.0, 1.0, 0.0, None),
     (O.CHIMERA, 3, 30, 3.0, 1.5, 0.0, None),
     (O.HYPERCUBIC4D, 4, 8, 3.0, 1.5, 0.0, None),
     (O.SQUARE2D, 8, 12, 1.5, 1.0, 0.3, None),
     (O.CUBIC3D, 6, 10, 2.0, 1.0, 0.0, 256),
+    (O.SQUARE2D, 16, 16, 1.5, 1.0, 0.0, (4, 64)),
+    (O.CUBIC3D, 8, 10, 2.0, 1.0, 0.3, (2, 128)),
+    (O.HYPERCUBIC4D, 4, 8, 3.0, 1.5, 0.0, (4, 32)),
 ]
 mismatch = []
 for ci, (lat, L, nT, th, ticm, dil, threads) in enumerate(CASES):
@@ -39,7 +44,9 @@ for ci, (lat, L, nT, th, ticm, dil, threads) in enumerate(CASES):
         J = I.dilute(J, dil, 50 + ci, range(2))
     s0 = I.initial_spins(g.N, 2 * nT, 50 + ci, range(2))
     b = icmpt.Batch(ctx, lat, L, I.PM_J, J, T, ticm, 50 + ci, spins=s0)
-    if threads:
+    if isinstance(threads, tuple):
+        b.set_cluster(*threads)
+    elif threads:
         b.set_threads(threads)
     b.set_schedule(trace=1, t_meas=5)
     b.run(20)
@@ -60,4 +67,7 @@ b.read_trace()
 ctx.sync()
 word = (ctypes.c_uint * 4)()
 rc = lib.icm_debug_check(word, 1)
-print(json.dumps({"rc": rc, "check": list(word), "mismatch": mismatch}))
+cword = (ctypes.c_uint * 4)()
+rc_cluster = lib.icm_debug_check_cluster(cword, 1)
+print(json.dumps({"rc": rc, "check": list(word), "rc_cluster": rc_cluster, "check_cluster": list(cword),
+                  "mismatch": mismatch}))
