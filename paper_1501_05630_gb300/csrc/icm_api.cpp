@@ -715,6 +715,13 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     int n_icm = 0;
     while (n_icm < n_T && T[n_icm] <= T_icm) ++n_icm;
     int threads = icm::fused_threads(N);
+    if (n_inst < ctx->num_sms) {
+        // few instances: each CTA alone on its SM is latency-bound, so a tiny
+        // instance gets a warp group per 16-bit pass (the passes run at once)
+        const int gthr = (N / 2 + 31) / 32 * 32, npass = (R + 15) / 16;
+        const int t = gthr * npass < icm::kMaxThreads ? gthr * npass : icm::kMaxThreads / gthr * gthr;
+        if (t > threads) threads = t;
+    }
     {
         const icm::SmemLayout sm0 = icm::smem_layout(N, Z, R, G, n_T, n_icm, threads / 32, b->gauss, false);
         bool wide = sm0.total > ctx->max_smem_optin;

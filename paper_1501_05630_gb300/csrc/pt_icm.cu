@@ -162,10 +162,13 @@ __device__ __forceinline__ void load_nbrs(const uint16_t *nbr, int p, int (&q)[Z
 // colour.  Bits at or above R ("ghost" replicas of a partly used last word)
 // are updated at beta = 0 and never read, so the inner loop has no guards.
 // Two Philox4x32-10 blocks are generated together (8 draws) so that their
-// dependency chains interleave.
-template <bool GAUSS, int Z, bool WIDE, bool DIL>
+// dependency chains interleave.  The sites are taken by threads j0, j0 +
+// jstride, ...; when other threads run another pass over the same words at
+// the same time (tiny instances), the flips go in by atomic XOR (each pass
+// owns its 16 bits, so the result does not depend on the order).
+template <bool GAUSS, int Z, bool WIDE, bool DIL, bool SHARED>
 __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g, int COLOR,
-                                           int H)
+                                           int H, int j0, int jstride)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -177,7 +180,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
     ET acc[16];
 #pragma unroll
     for (int b = 0; b < 16; ++b) acc[b] = ET(0);
-    for (int j = threadIdx.x; j < half; j += nth) {
+    for (int j = j0; j < half; j += jstride) {
         const int p = COLOR * half + j;
         const uint32_t sw0 = sg[p];
         const uint32_t sw = sw0 >> sh0;                 // this pass's bits at 0..15: constant shifts below
@@ -286,12 +289,37 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
                 }
             }
         }
-        sg[p] = sw0 ^ (flip << sh0);
+        if constexpr (SHARED) atomicXor(sg + p, flip << sh0);
+        else sg[p] = sw0 ^ (flip << sh0);
     }
     if (COLOR == 1) {   // energies: every bond touches exactly one colour-1 site
         const ET v = transpose_reduce16(acc, lane);
         const int r = rbase + (lane >> 1);
         if (!(lane & 1) && r < P.R) ((ET *)S.Epart)[ICM_IDX(warp * P.R + r, (nth >> 5) * (P.R > 32 ? P.R : 32), 5)] = v;
+    }
+}
+
+// Tiny instances with at least twice the threads a colour needs: the
+// threads split into groups of whole warps that run different passes at the
+// same time; every warp writes its energy slots, the ones of passes it did not
+// run as 0.
+template <bool GAUSS, int Z, bool WIDE, bool DIL>
+__device__ __forceinline__ void metropolis_sweep_concurrent(const KParams &P, const Sm &S, uint32_t t, uint32_t inst,
+                                                         int npass, int gthr, int conc)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    const int group = (int)threadIdx.x / gthr;
+    const int nslot = (int)(blockDim.x >> 5) * P.R;
+    for (int i = threadIdx.x; i < nslot; i += blockDim.x) ((ET *)S.Epart)[i] = ET(0);
+    __syncthreads();
+    for (int color = 0; color < 2; ++color) {
+        for (int p0 = 0; p0 < npass; p0 += conc) {
+            const int pass = p0 + group;
+            if (group < conc && pass < npass)    // whole warps: gthr is a multiple of 32
+                sweep_pass<GAUSS, Z, WIDE, DIL, true>(P, S, t, inst, pass >> 1, color, pass & 1,
+                                                      (int)threadIdx.x - group * gthr, gthr);
+        }
+        __syncthreads();
     }
 }
 
@@ -302,10 +330,16 @@ template <bool GAUSS, int Z, bool WIDE, bool DIL>
 __device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
 {
     const int npass = (P.R + 15) >> 4;          // 16-bit passes per colour
+    const int gthr = (P.half + 31) & ~31;        // threads of one pass
+    const int conc = min((int)blockDim.x / gthr, npass);   // passes at a time
+    if (conc >= 2) {
+        metropolis_sweep_concurrent<GAUSS, Z, WIDE, DIL>(P, S, t, inst, npass, gthr, conc);
+        return;
+    }
     for (int it = 0; it < 2 * npass; ++it) {
         const int color = it >= npass;
         const int pass = it - color * npass;
-        sweep_pass<GAUSS, Z, WIDE, DIL>(P, S, t, inst, pass >> 1, color, pass & 1);
+        sweep_pass<GAUSS, Z, WIDE, DIL, false>(P, S, t, inst, pass >> 1, color, pass & 1, threadIdx.x, blockDim.x);
         if (pass == npass - 1) __syncthreads();
     }
 }
