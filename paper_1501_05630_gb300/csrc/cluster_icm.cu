@@ -642,12 +642,12 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
         const int npair = min(16, nT - 16 * g);
         const uint32_t goff = (uint32_t)(g * nls * 4);
         const uint32_t *sg = S.s + g * nls;
-        uint32_t pn[kPlanes], pd[kPlanes];
+        uint32_t pl[kPlanes];   // even bit 2k: q = -1 sites of pair k; odd bit 2k+1: its q_i q_j = -1 bonds
 #pragma unroll
-        for (int i = 0; i < kPlanes; ++i) pn[i] = pd[i] = 0u;
+        for (int i = 0; i < kPlanes; ++i) pl[i] = 0u;
         for (int li = threadIdx.x; li < nls; li += blockDim.x) {
             const uint32_t w = sg[li];
-            vadd(pn, (w ^ (w >> 1)) & 0x55555555u);
+            vadd(pl, (w ^ (w >> 1)) & 0x55555555u);
         }
         for (int li = hs + threadIdx.x; li < nls; li += blockDim.x) {
             const uint32_t w = sg[li];
@@ -657,17 +657,11 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
                 const uint32_t e = S.nb[li * Z + d];
                 if (e == self0 + 4u * (uint32_t)li) continue;      // padding entry
                 const uint32_t wq = cl_ld(e + goff);
-                vadd(pd, qp ^ ((wq ^ (wq >> 1)) & 0x55555555u));
+                vadd(pl, (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1);
             }
         }
-        for (int j = 0; j < npair; ++j) {
-            const int cn = __reduce_add_sync(kFull, vget(pn, 2 * j));
-            const int cd = __reduce_add_sync(kFull, vget(pd, 2 * j));
-            if (lane == 0) {
-                atomicAdd(&S.cnt_n[16 * g + j], cn);
-                atomicAdd(&S.cnt_d[16 * g + j], cd);
-            }
-        }
+        const int v = warp_vsum(pl, lane);   // lane 2k: n of pair k, lane 2k+1: d of pair k
+        if (lane < 2 * npair) atomicAdd(((lane & 1) ? S.cnt_d : S.cnt_n) + 16 * g + (lane >> 1), v);
     }
     cl_sync();
     if (S.rank == 0) {

@@ -239,12 +239,33 @@ __device__ __forceinline__ void vadd(uint32_t (&pl)[NPL], uint32_t w)
     }
 }
 
+// Warp totals of vertical counters.  Every lane holds 32 counters as NPL
+// bit-planes (bit b of plane i = binary digit i of counter b).  Five
+// butterfly steps add the lanes' counters plane by plane (a ripple-carry
+// adder on whole words, one plane wider per step), so every lane ends with
+// the warp totals in NPL + 5 planes; lane b returns total b.
 template <int NPL>
-__device__ __forceinline__ int vget(const uint32_t (&pl)[NPL], int bit)
+__device__ __forceinline__ int warp_vsum(const uint32_t (&pl)[NPL], int lane)
 {
+    uint32_t a[NPL + 5];
+#pragma unroll
+    for (int i = 0; i < NPL + 5; ++i) a[i] = i < NPL ? pl[i] : 0u;
+#pragma unroll
+    for (int st = 0; st < 5; ++st) {
+        uint32_t c = 0u;
+#pragma unroll
+        for (int i = 0; i < NPL + st; ++i) {
+            const uint32_t o = __shfl_xor_sync(kFull, a[i], 16 >> st);
+            const uint32_t x = a[i] ^ o;
+            const uint32_t cn = (a[i] & o) | (c & x);
+            a[i] = x ^ c;
+            c = cn;
+        }
+        a[NPL + st] = c;
+    }
     int v = 0;
 #pragma unroll
-    for (int i = 0; i < NPL; ++i) v |= (int)((pl[i] >> bit) & 1u) << i;
+    for (int i = 0; i < NPL + 5; ++i) v |= (int)((a[i] >> lane) & 1u) << i;
     return v;
 }
 

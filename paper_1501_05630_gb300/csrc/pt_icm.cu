@@ -172,7 +172,8 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int N = P.N, half = P.half, nth = blockDim.x;
+    const int N = P.N, half = P.half;
+    [[maybe_unused]] const int nth = blockDim.x;   // the bound of a checked index
     const int rbase = 32 * g + 16 * H;
     const int sh0 = 16 * H;                       // first bit of this pass inside the word
     const int npairs8 = (P.R - rbase + 7) >> 3;   // 8-bit groups holding at least one live replica (1 or 2)
@@ -728,12 +729,12 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
     for (int g = 0; g < P.G; ++g) {
         const int npair = min(16, nT - 16 * g);
         const uint32_t *sg = S.s + g * N;
-        uint32_t pn[NPL], pd[NPL];
+        uint32_t pl[NPL];   // even bit 2k: q = -1 sites of pair k; odd bit 2k+1: its q_i q_j = -1 bonds
 #pragma unroll
-        for (int i = 0; i < NPL; ++i) pn[i] = pd[i] = 0u;
+        for (int i = 0; i < NPL; ++i) pl[i] = 0u;
         for (int p = threadIdx.x; p < N; p += blockDim.x) {
             const uint32_t w = sg[p];
-            vadd(pn, (w ^ (w >> 1)) & 0x55555555u);
+            vadd(pl, (w ^ (w >> 1)) & 0x55555555u);
         }
         for (int p = half + threadIdx.x; p < N; p += blockDim.x) {
             const uint32_t w = sg[p];
@@ -745,17 +746,11 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
                 const int q = qn[d];
                 if (q == p) continue;
                 const uint32_t wq = sg[ICM_IDX(q, N, 13)];
-                vadd(pd, qp ^ ((wq ^ (wq >> 1)) & 0x55555555u));
+                vadd(pl, (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1);
             }
         }
-        for (int j = 0; j < npair; ++j) {
-            const int cn = __reduce_add_sync(kFull, vget(pn, 2 * j));
-            const int cd = __reduce_add_sync(kFull, vget(pd, 2 * j));
-            if (lane == 0) {
-                atomicAdd(&S.cnt_n[16 * g + j], cn);
-                atomicAdd(&S.cnt_d[16 * g + j], cd);
-            }
-        }
+        const int v = warp_vsum(pl, lane);   // lane 2k: n of pair k, lane 2k+1: d of pair k
+        if (lane < 2 * npair) atomicAdd(((lane & 1) ? S.cnt_d : S.cnt_n) + 16 * g + (lane >> 1), v);
     }
     __syncthreads();
     for (int k = threadIdx.x; k < nT; k += blockDim.x) {
