@@ -389,8 +389,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                                 if (flipped) w = ~w;
                                 const uint32_t pc = (uint32_t)__popc(w);
                                 if (rank < pc) {
-                                    for (uint32_t q = 0; q < rank; ++q) w &= w - 1u;
-                                    const int li = 32 * m + __ffs(w) - 1;
+                                    const int li = 32 * m + nth_set_bit(w, rank);
                                     atomicOr((k < 16 ? S.C0 : S.C1) + ICM_IDX(li, nls, 21), 1u << (2 * (k & 15)));
                                     if (trace) P.tr_seed[(size_t)slot * P.nT + k] = (int)__ldg(P.pos2site + pos_of(P, S, li));
                                     break;
@@ -601,23 +600,11 @@ __device__ void cl_pt_pass(const KParams &P, const CS &S, uint32_t t, uint32_t i
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {
-        const uint64_t D = S.swap_mask[0] | S.swap_mask[1];
-        uint64_t U = 0;
-        for (int j = 0; j < n0; ++j) U |= 1ull << (S.swap_list[j] >> 8);
-        for (int j = 0; j < n1; ++j) U |= 1ull << (S.swap_list[32 + j] >> 8);
-        const uint64_t keep = ~(D | U);
+        const SwapMasks m = swap_masks(S.swap_list, n0, n1, S.swap_mask);
         const bool two = P.G > 1;
         for (int li = threadIdx.x; li < nls; li += blockDim.x) {
             const uint64_t x = (uint64_t)S.s[li] | (two ? (uint64_t)S.s[nls + li] << 32 : 0ull);
-            uint64_t y = (x & keep) | ((x & D) >> 2);
-            for (int j = 0; j < n0; ++j) {
-                const int mv = S.swap_list[j];
-                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
-            }
-            for (int j = 0; j < n1; ++j) {
-                const int mv = S.swap_list[32 + j];
-                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
-            }
+            const uint64_t y = swap_apply(m, x);
             S.s[li] = (uint32_t)y;
             if (two) S.s[nls + li] = (uint32_t)(y >> 32);
         }

@@ -185,6 +185,63 @@ __device__ __forceinline__ void pt_warp(ET *E, int R, int np, const uint32_t *w,
     }
 }
 
+// Bit position of the rank-th set bit of w, counting from bit 0 (rank <
+// popc(w)): five halvings of the window by the popcount of its lower half.
+__device__ __forceinline__ int nth_set_bit(uint32_t w, uint32_t rank)
+{
+    int pos = 0;
+#pragma unroll
+    for (int hw = 16; hw >= 1; hw >>= 1) {
+        const uint32_t lo = w & ((1u << hw) - 1u);
+        const uint32_t cl = (uint32_t)__popc(lo);
+        if (rank >= cl) {
+            rank -= cl;
+            w >>= hw;
+            pos += hw;
+        } else {
+            w = lo;
+        }
+    }
+    return pos;
+}
+
+// The configuration moves of one PT pass as masks of the 64 replica bits of a
+// site (two words).  A run of accepted swaps k..m, list entry
+// (2k + c) << 8 | 2(m + 1) + c, moves the configuration at bit s = 2k + c up
+// to e = 2(m + 1) + c, and the others of the run down one position (mask
+// down).  With fw = the sum of 2^e - 2^s over the runs of copy c,
+// ((x & st) + fw) & en carries every start bit to its end bit at once: the
+// runs of one copy cover disjoint bit ranges, so no carry leaves its run.
+struct SwapMasks {
+    uint64_t keep, down, st[2], fw[2], en[2];
+};
+
+__device__ __forceinline__ SwapMasks swap_masks(const int *list, int n0, int n1, const uint64_t *down)
+{
+    SwapMasks m;
+    m.down = down[0] | down[1];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        m.st[c] = m.fw[c] = m.en[c] = 0ull;
+        const int n = c ? n1 : n0;
+        for (int j = 0; j < n; ++j) {
+            const int mv = list[32 * c + j];
+            const uint64_t s = 1ull << (mv >> 8), e = 1ull << (mv & 0xff);
+            m.st[c] |= s;
+            m.en[c] |= e;
+            m.fw[c] += e - s;
+        }
+    }
+    m.keep = ~(m.down | m.st[0] | m.st[1]);
+    return m;
+}
+
+__device__ __forceinline__ uint64_t swap_apply(const SwapMasks &m, uint64_t x)
+{
+    return (x & m.keep) | ((x & m.down) >> 2) | (((x & m.st[0]) + m.fw[0]) & m.en[0]) |
+           (((x & m.st[1]) + m.fw[1]) & m.en[1]);
+}
+
 // Sum of a[j] over the 32 lanes, delivered to lane j (31 shuffles).
 template <typename T>
 __device__ __forceinline__ T transpose_reduce(T (&a)[32], int lane)

@@ -486,11 +486,10 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             philox10((uint32_t)k, t, 0u, (1u << 24) | inst, P.seed_lo, P.seed_hi, x);
             uint32_t rank = (uint32_t)(((uint64_t)x[0] * (uint32_t)n) >> 32);
             for (int m = 0; m < NW; ++m) {
-                uint32_t w = Mk[m];
+                const uint32_t w = Mk[m];
                 const uint32_t c = (uint32_t)__popc(w);
                 if (rank < c) {
-                    for (uint32_t r = 0; r < rank; ++r) w &= w - 1u;
-                    seed = 32 * m + __ffs(w) - 1;
+                    seed = 32 * m + nth_set_bit(w, rank);
                     break;
                 }
                 rank -= c;
@@ -694,23 +693,11 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
     __syncthreads();
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {
-        const uint64_t D = S.swap_mask[0] | S.swap_mask[1];
-        uint64_t U = 0;
-        for (int j = 0; j < n0; ++j) U |= 1ull << (S.swap_list[j] >> 8);
-        for (int j = 0; j < n1; ++j) U |= 1ull << (S.swap_list[32 + j] >> 8);
-        const uint64_t keep = ~(D | U);
+        const SwapMasks m = swap_masks(S.swap_list, n0, n1, S.swap_mask);
         const bool two = P.G > 1;
         for (int p = threadIdx.x; p < N; p += blockDim.x) {
             const uint64_t x = (uint64_t)S.s[p] | (two ? (uint64_t)S.s[N + p] << 32 : 0ull);
-            uint64_t y = (x & keep) | ((x & D) >> 2);
-            for (int j = 0; j < n0; ++j) {
-                const int mv = S.swap_list[j];
-                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
-            }
-            for (int j = 0; j < n1; ++j) {
-                const int mv = S.swap_list[32 + j];
-                y |= ((x >> (mv >> 8)) & 1ull) << (mv & 0xff);
-            }
+            const uint64_t y = swap_apply(m, x);
             S.s[p] = (uint32_t)y;
             if (two) S.s[N + p] = (uint32_t)(y >> 32);
         }
