@@ -236,21 +236,10 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
         } else {
             uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;   // bit-planes of u = # unsatisfied bonds
             const uint32_t jb = S.Jb[li];
+            uint32_t u[Z];
 #pragma unroll
-            for (int d = 0; d < Z; ++d) {
-                const uint32_t u = sw0 ^ nw[d] ^ (0u - ((jb >> d) & 1u));
-                const uint32_t t0 = c0 & u;
-                c0 ^= u;
-                const uint32_t t1 = c1 & t0;
-                c1 ^= t0;
-                if constexpr (Z > 7) {              // u up to 8: a fourth plane
-                    const uint32_t t2 = c2 & t1;
-                    c2 ^= t1;
-                    c3 |= t2;
-                } else {
-                    c2 |= t1;
-                }
-            }
+            for (int d = 0; d < Z; ++d) u[d] = sw0 ^ nw[d] ^ (0u - ((jb >> d) & 1u));
+            csa_count<Z>(u, c0, c1, c2, c3);
             c0 >>= sh0;
             c1 >>= sh0;
             c2 >>= sh0;
@@ -527,21 +516,10 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
             } else {
                 uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
                 const uint32_t jb = S.Jb[li];
+                uint32_t u[Z];
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const uint32_t u = sw ^ nw[d] ^ (0u - ((jb >> d) & 1u));
-                    const uint32_t t0 = c0 & u;
-                    c0 ^= u;
-                    const uint32_t t1 = c1 & t0;
-                    c1 ^= t0;
-                    if constexpr (Z > 7) {
-                        const uint32_t t2 = c2 & t1;
-                        c2 ^= t1;
-                        c3 |= t2;
-                    } else {
-                        c2 |= t1;
-                    }
-                }
+                for (int d = 0; d < Z; ++d) u[d] = sw ^ nw[d] ^ (0u - ((jb >> d) & 1u));
+                csa_count<Z>(u, c0, c1, c2, c3);
 #pragma unroll
                 for (int jj = 0; jj < 16; ++jj) {
                     const int b = 2 * jj;
@@ -619,7 +597,6 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31;
     const int N = P.N, nT = P.nT, nls = S.nls, hs = S.hs;
-    const uint32_t self0 = cl_map(S.base + L.s, S.rank);
     if (threadIdx.x < 32) {
         S.cnt_n[threadIdx.x] = 0;
         S.cnt_d[threadIdx.x] = 0;
@@ -639,13 +616,15 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
         for (int li = hs + threadIdx.x; li < nls; li += blockDim.x) {
             const uint32_t w = sg[li];
             const uint32_t qp = (w ^ (w >> 1)) & 0x55555555u;
+            uint32_t x[Z];                 // a padding entry points at the site itself: x = 0
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                const uint32_t e = S.nb[li * Z + d];
-                if (e == self0 + 4u * (uint32_t)li) continue;      // padding entry
-                const uint32_t wq = cl_ld(e + goff);
-                vadd(pl, (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1);
+                const uint32_t wq = cl_ld(S.nb[li * Z + d] + goff);
+                x[d] = (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1;
             }
+            uint32_t c0, c1, c2, c3;
+            csa_count<Z>(x, c0, c1, c2, c3);
+            vadd4(pl, c0, c1, c2, c3);
         }
         const int v = warp_vsum(pl, lane);   // lane 2k: n of pair k, lane 2k+1: d of pair k
         if (lane < 2 * npair) atomicAdd(((lane & 1) ? S.cnt_d : S.cnt_n) + 16 * g + (lane >> 1), v);

@@ -296,6 +296,67 @@ __device__ __forceinline__ void vadd(uint32_t (&pl)[NPL], uint32_t w)
     }
 }
 
+// Full adder on whole words: per bit lane, a + b + c = s + 2 cy.
+__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy)
+{
+    const uint32_t x = a ^ b;
+    s = x ^ c;
+    cy = (a & b) | (c & x);
+}
+
+// Per bit lane, the number of set bits among x[0..Z-1] (Z = 4, 6 or 8) as
+// bit-planes c0..c3, by a carry-save adder tree (c2 = c3 = 0 where the
+// count cannot reach them).
+template <int Z>
+__device__ __forceinline__ void csa_count(const uint32_t (&x)[Z], uint32_t &c0, uint32_t &c1, uint32_t &c2,
+                                          uint32_t &c3)
+{
+    static_assert(Z == 4 || Z == 6 || Z == 8, "coordination 4, 6 or 8");
+    uint32_t a, ca;
+    full_add(x[0], x[1], x[2], a, ca);
+    if constexpr (Z == 4) {
+        c0 = a ^ x[3];
+        const uint32_t h = a & x[3];
+        c1 = ca ^ h;
+        c2 = ca & h;
+        c3 = 0u;
+    } else if constexpr (Z == 6) {
+        uint32_t b, cb;
+        full_add(x[3], x[4], x[5], b, cb);
+        c0 = a ^ b;
+        full_add(ca, cb, a & b, c1, c2);
+        c3 = 0u;
+    } else {
+        uint32_t b, cb, c, cc, t, e;
+        full_add(x[3], x[4], x[5], b, cb);
+        full_add(a, b, x[6], c, cc);
+        c0 = c ^ x[7];
+        const uint32_t h = c & x[7];             // weight 2: ca, cb, cc, h
+        full_add(ca, cb, cc, t, e);
+        c1 = t ^ h;
+        const uint32_t f = t & h;                // weight 4: e, f
+        c2 = e ^ f;
+        c3 = e & f;
+    }
+}
+
+// Add a number given as four bit-planes to NPL bit-planes of vertical
+// counters (ripple carry over the planes).
+template <int NPL>
+__device__ __forceinline__ void vadd4(uint32_t (&pl)[NPL], uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3)
+{
+    const uint32_t in[4] = {c0, c1, c2, c3};
+    uint32_t cy = 0u;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const uint32_t b = i < 4 ? in[i] : 0u;
+        const uint32_t x = pl[i] ^ b;
+        const uint32_t ncy = (pl[i] & b) | (cy & x);
+        pl[i] = x ^ cy;
+        cy = ncy;
+    }
+}
+
 // Warp totals of vertical counters.  Every lane holds 32 counters as NPL
 // bit-planes (bit b of plane i = binary digit i of counter b).  Five
 // butterfly steps add the lanes' counters plane by plane (a ripple-carry

@@ -240,21 +240,10 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             const uint32_t jb = S.Jb[ICM_IDX(p, N, 3)];
             int q[Z];
             load_nbrs<Z>(S.nbr, p, q);
+            uint32_t u[Z];
 #pragma unroll
-            for (int d = 0; d < Z; ++d) {
-                const uint32_t u = sw0 ^ sg[ICM_IDX(q[d], N, 1)] ^ (0u - ((jb >> d) & 1u));
-                const uint32_t t0 = c0 & u;
-                c0 ^= u;
-                const uint32_t t1 = c1 & t0;
-                c1 ^= t0;
-                if constexpr (Z > 7) {              // u up to 8: a fourth plane
-                    const uint32_t t2 = c2 & t1;
-                    c2 ^= t1;
-                    c3 |= t2;
-                } else {
-                    c2 |= t1;
-                }
-            }
+            for (int d = 0; d < Z; ++d) u[d] = sw0 ^ sg[ICM_IDX(q[d], N, 1)] ^ (0u - ((jb >> d) & 1u));
+            csa_count<Z>(u, c0, c1, c2, c3);
             c0 >>= sh0;
             c1 >>= sh0;
             c2 >>= sh0;
@@ -393,21 +382,10 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
             } else {
                 uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
                 const uint32_t jb = S.Jb[ICM_IDX(p, N, 3)];
+                uint32_t u[Z];
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const uint32_t u = sw ^ sg[ICM_IDX(q[d], N, 6)] ^ (0u - ((jb >> d) & 1u));
-                    const uint32_t t0 = c0 & u;
-                    c0 ^= u;
-                    const uint32_t t1 = c1 & t0;
-                    c1 ^= t0;
-                    if constexpr (Z > 7) {
-                        const uint32_t t2 = c2 & t1;
-                        c2 ^= t1;
-                        c3 |= t2;
-                    } else {
-                        c2 |= t1;
-                    }
-                }
+                for (int d = 0; d < Z; ++d) u[d] = sw ^ sg[ICM_IDX(q[d], N, 6)] ^ (0u - ((jb >> d) & 1u));
+                csa_count<Z>(u, c0, c1, c2, c3);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const int b = 2 * j;
@@ -728,13 +706,15 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
             const uint32_t qp = (w ^ (w >> 1)) & 0x55555555u;
             int qn[Z];
             load_nbrs<Z>(S.nbr, p, qn);
+            uint32_t x[Z];                 // an absent bond points at p itself: x = 0
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                const int q = qn[d];
-                if (q == p) continue;
-                const uint32_t wq = sg[ICM_IDX(q, N, 13)];
-                vadd(pl, (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1);
+                const uint32_t wq = sg[ICM_IDX(qn[d], N, 13)];
+                x[d] = (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1;
             }
+            uint32_t c0, c1, c2, c3;
+            csa_count<Z>(x, c0, c1, c2, c3);
+            vadd4(pl, c0, c1, c2, c3);
         }
         const int v = warp_vsum(pl, lane);   // lane 2k: n of pair k, lane 2k+1: d of pair k
         if (lane < 2 * npair) atomicAdd(((lane & 1) ? S.cnt_d : S.cnt_n) + 16 * g + (lane >> 1), v);
