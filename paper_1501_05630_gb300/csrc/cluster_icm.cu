@@ -324,16 +324,14 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     for (int m = warp; m < NWl; m += nwarps) {
         const int li = 32 * m + lane;
         const uint32_t w0 = S.s[li];
-        const uint32_t q0 = w0 ^ (w0 >> 1);
-        uint32_t q1 = 0u;
+        uint32_t x = (w0 ^ (w0 >> 1)) & 0x55555555u;   // bit 2j: pair j; bit 2j + 1: pair 16 + j
         if (G > 1) {
             const uint32_t w1 = S.s[nls + li];
-            q1 = w1 ^ (w1 >> 1);
+            x |= ((w1 ^ (w1 >> 1)) & 0x55555555u) << 1;
         }
-        for (int k = 0; k < nicm; ++k) {
-            const uint32_t word = __ballot_sync(kFull, ((k < 16 ? q0 : q1) >> (2 * (k & 15))) & 1u);
-            if (lane == (k & 31)) S.mask[k * NWl + m] = word;
-        }
+        const uint32_t col = warp_transpose32(x, lane);
+        const int k = (lane >> 1) + 16 * (lane & 1);
+        if (k < nicm) S.mask[k * NWl + m] = col;
     }
     for (int i = tid; i < nls; i += nth) {
         S.C0[i] = 0u;

@@ -296,6 +296,21 @@ __device__ __forceinline__ void vadd(uint32_t (&pl)[NPL], uint32_t w)
     }
 }
 
+// 32 x 32 bit-matrix transpose across a warp: lane j returns the word whose
+// bit l is bit j of lane l's x.  Five butterfly stages; the one of stride s
+// swaps the off-diagonal s x s blocks between lanes l and l ^ s.
+__device__ __forceinline__ uint32_t warp_transpose32(uint32_t x, int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const uint32_t m = s == 16 ? 0x0000FFFFu : s == 8 ? 0x00FF00FFu : s == 4 ? 0x0F0F0F0Fu
+                         : s == 2 ? 0x33333333u : 0x55555555u;     // bits whose index has bit s clear
+        const uint32_t o = __shfl_xor_sync(kFull, x, s);
+        x = (lane & s) ? ((x & ~m) | ((o >> s) & m)) : ((x & m) | ((o << s) & ~m));
+    }
+    return x;
+}
+
 // Full adder on whole words: per bit lane, a + b + c = s + 2 cy.
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s, uint32_t &cy)
 {

@@ -21,7 +21,7 @@
 //    summed in fp32 from sign-injected couplings, accept via ex2.
 //    The energies of all replicas fall out of the colour-1 half-sweep
 //    (every bond touches exactly one colour-1 site).
-//  * Steps 2a/2b: overlap masks of all ICM pairs by warp ballots; one thread
+//  * Steps 2a/2b: overlap masks of all ICM pairs by a warp bit transpose; one thread
 //    per pair counts, decides the copy-1 reversal and picks the seed by rank;
 //    the clusters of all pairs grow at once, bit-parallel (bit 2k of a site's
 //    cluster word = member of pair k's cluster), until a round adds nothing;
@@ -401,7 +401,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
 
 // ---------------------------------------------------------------------------
 // Steps 2a and 2b at every ICM temperature k < n_icm.
-//  (a) overlap masks of all pairs by warp ballots (bit 2k of s ^ (s >> 1));
+//  (a) overlap masks of all pairs by a warp bit-matrix transpose (bit 2k of s ^ (s >> 1));
 //  (b) one thread per pair: n, the step-2a decision, the seed by rank;
 //  (c) copy-1 reversal of the flagged pairs, then the clusters of all pairs
 //      at once: C_p (bit 2k = site p in pair k's cluster) grows by
@@ -424,19 +424,18 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     // (a) masks; clear the cluster words
     for (int m = warp; m < NW; m += nwarps) {
         const int p = 32 * m + lane;
-        uint32_t q0 = 0, q1 = 0;
+        uint32_t x = 0u;       // bit 2j: q of pair j (first word); bit 2j + 1: q of pair 16 + j
         if (p < N) {
             const uint32_t w0 = S.s[p];
-            q0 = w0 ^ (w0 >> 1);
+            x = (w0 ^ (w0 >> 1)) & 0x55555555u;
             if (G > 1) {
                 const uint32_t w1 = S.s[N + p];
-                q1 = w1 ^ (w1 >> 1);
+                x |= ((w1 ^ (w1 >> 1)) & 0x55555555u) << 1;
             }
         }
-        for (int k = 0; k < nicm; ++k) {
-            const uint32_t word = __ballot_sync(kFull, ((k < 16 ? q0 : q1) >> (2 * (k & 15))) & 1u);
-            if (lane == (k & 31)) S.mask[ICM_IDX(k * NW + m, nicm * NW, 8)] = word;
-        }
+        const uint32_t col = warp_transpose32(x, lane);   // lane l: bit l of the 32 sites' x
+        const int k = (lane >> 1) + 16 * (lane & 1);
+        if (k < nicm) S.mask[ICM_IDX(k * NW + m, nicm * NW, 8)] = col;
     }
     for (int i = tid; i < 2 * N; i += nth) S.C[i] = 0u;
     if (tid < 2) S.flipw[tid] = 0u;
