@@ -477,81 +477,92 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         }
     }
     cl_sync();                                       // flipped words of other CTAs are read below
+    // copy-a energies of the moved pairs (cb = 0); a traced sweep then also
+    // recomputes the copy-b energies (cb = 1) and records E_a + E_b of the two
+    // recomputed energies, so that the trace tests the conservation of E_a + E_b
     ET *part = (ET *)S.Epart;
-    for (int g = 0; g < G; ++g) {
-        const uint32_t act = g ? act1 : act0;
-        if (!act) continue;
-        const uint32_t goff = (uint32_t)(g * nls * 4);
-        const uint32_t *sg = S.s + g * nls;
-        ET acc[16];
+    for (int cb = 0; cb < (trace ? 2 : 1); ++cb) {
+        if (cb) cl_sync();                           // every CTA has read the copy-a shares
+        for (int g = 0; g < G; ++g) {
+            const uint32_t act = g ? act1 : act0;
+            if (!act) continue;
+            const uint32_t goff = (uint32_t)(g * nls * 4);
+            const uint32_t *sg = S.s + g * nls;
+            ET acc[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) acc[j] = ET(0);
-        for (int j = tid; j < hs; j += nth) {
-            const int li = hs + j;                   // colour-1 sites: every bond once
-            const uint32_t sw = sg[li];
-            uint32_t nw[Z];
+            for (int j = 0; j < 16; ++j) acc[j] = ET(0);
+            for (int j = tid; j < hs; j += nth) {
+                const int li = hs + j;               // colour-1 sites: every bond once
+                const uint32_t sw = sg[li] >> cb;
+                uint32_t nw[Z];
 #pragma unroll
-            for (int d = 0; d < Z; ++d) nw[d] = cl_ld(S.nb[li * Z + d] + goff);
-            if constexpr (GAUSS) {
-                float J2[Z];
-                float Jsum = 0.f;
+                for (int d = 0; d < Z; ++d) nw[d] = cl_ld(S.nb[li * Z + d] + goff) >> cb;
+                if constexpr (GAUSS) {
+                    float J2[Z];
+                    float Jsum = 0.f;
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const float J = S.Jd[li * Z + d];
-                    Jsum += J;
-                    J2[d] = 2.f * J;
+                    for (int d = 0; d < Z; ++d) {
+                        const float J = S.Jd[li * Z + d];
+                        Jsum += J;
+                        J2[d] = 2.f * J;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        if (!((act >> (2 * jj)) & 1u)) continue;
+                        const int b = 2 * jj;
+                        float h = Jsum;
+#pragma unroll
+                        for (int d = 0; d < Z; ++d)
+                            if ((nw[d] >> b) & 1u) h -= J2[d];
+                        acc[jj] += ((sw >> b) & 1u) ? h : -h;
+                    }
+                } else {
+                    uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+                    const uint32_t jb = S.Jb[li];
+                    uint32_t u[Z];
+#pragma unroll
+                    for (int d = 0; d < Z; ++d) u[d] = sw ^ nw[d] ^ (0u - ((jb >> d) & 1u));
+                    csa_count<Z>(u, c0, c1, c2, c3);
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int b = 2 * jj;
+                        acc[jj] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2) |
+                                         (((c3 >> b) & 1u) << 3));
+                    }
                 }
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    if (!((act >> (2 * jj)) & 1u)) continue;
-                    const int b = 2 * jj;
-                    float h = Jsum;
-#pragma unroll
-                    for (int d = 0; d < Z; ++d)
-                        if ((nw[d] >> b) & 1u) h -= J2[d];
-                    acc[jj] += ((sw >> b) & 1u) ? h : -h;
-                }
-            } else {
-                uint32_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-                const uint32_t jb = S.Jb[li];
-                uint32_t u[Z];
-#pragma unroll
-                for (int d = 0; d < Z; ++d) u[d] = sw ^ nw[d] ^ (0u - ((jb >> d) & 1u));
-                csa_count<Z>(u, c0, c1, c2, c3);
-#pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int b = 2 * jj;
-                    acc[jj] += (int)(((c0 >> b) & 1u) | (((c1 >> b) & 1u) << 1) | (((c2 >> b) & 1u) << 2) |
-                                     (((c3 >> b) & 1u) << 3));
+            }
+            const ET v = transpose_reduce16(acc, lane);
+            if (!(lane & 1)) part[warp * 32 + 16 * g + (lane >> 1)] = v;
+        }
+        __syncthreads();
+        for (int k = tid; k < nicm; k += nth) {
+            ET e = ET(0);
+            if (S.seed[k])
+                for (int w = 0; w < nwarps; ++w) e += part[w * 32 + k];
+            ((ET *)S.Epair)[k] = e;
+        }
+        cl_sync();
+        for (int k = tid; k < nicm; k += nth) {
+            if (!S.seed[k]) continue;
+            ET e = cl_sum<ET>(S, L.Epair + 4 * k);
+            if constexpr (!GAUSS) e = 2 * e - (P.diluted ? P.nb_inst[slot] : P.Nb);   // E = 2 U - N_b (bonds present)
+            if (cb == 0) {
+                E[2 * k] = e;
+                E[2 * k + 1] = esum[k] - e;
+            }
+            if (trace && S.rank == 0) {
+                const size_t o = (size_t)slot * P.nT + k;
+                if (cb == 0) {
+                    int cs = 0;
+                    for (uint32_t r = 0; r < S.K; ++r) cs += (int)cl_ld(cl_map(S.base + L.csz + 4 * k, r));
+                    P.tr_csize[o] = cs;
+                } else {
+                    P.tr_ea[o] = (float)(E[2 * k] + e);
                 }
             }
         }
-        const ET v = transpose_reduce16(acc, lane);
-        if (!(lane & 1)) part[warp * 32 + 16 * g + (lane >> 1)] = v;
+        __syncthreads();
     }
-    __syncthreads();
-    for (int k = tid; k < nicm; k += nth) {
-        ET e = ET(0);
-        if (S.seed[k])
-            for (int w = 0; w < nwarps; ++w) e += part[w * 32 + k];
-        ((ET *)S.Epair)[k] = e;
-    }
-    cl_sync();
-    for (int k = tid; k < nicm; k += nth) {
-        if (!S.seed[k]) continue;
-        ET ea = cl_sum<ET>(S, L.Epair + 4 * k);
-        if constexpr (!GAUSS) ea = 2 * ea - (P.diluted ? P.nb_inst[slot] : P.Nb);   // E = 2 U - N_b (bonds present)
-        E[2 * k] = ea;
-        E[2 * k + 1] = esum[k] - ea;
-        if (trace && S.rank == 0) {
-            const size_t o = (size_t)slot * P.nT + k;
-            int cs = 0;
-            for (uint32_t r = 0; r < S.K; ++r) cs += (int)cl_ld(cl_map(S.base + L.csz + 4 * k, r));
-            P.tr_csize[o] = cs;
-            P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
-        }
-    }
-    __syncthreads();
 }
 
 // Step 3 (see pt_pass in pt_icm.cu): the same energies and draws in every

@@ -335,12 +335,13 @@ __device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, 
 }
 
 // ---------------------------------------------------------------------------
-// Energies of the copy-a replicas (bit 2k) of the pairs flagged in act0/act1,
-// from the spins: +-J via bit-sliced unsatisfied-bond counts (E = 2U - N_b),
-// Gaussian via per-bit fp32 local fields; summed in a fixed order.  Every
-// thread ends with partial sums in S.Epart[warp][k]; the caller adds warps.
+// Energies of copy cb (bit 2k + cb; cb = 0: copy a) of the pairs flagged in
+// act0/act1 (bit 2k), from the spins: +-J via bit-sliced unsatisfied-bond
+// counts (E = 2U - N_b), Gaussian via per-bit fp32 local fields; summed in a
+// fixed order.  Every thread ends with partial sums in S.Epart[warp][k]; the
+// caller adds warps.
 template <bool GAUSS, int Z, bool WIDE>
-__device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uint32_t act0, uint32_t act1)
+__device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uint32_t act0, uint32_t act1, int cb)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -355,7 +356,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
         for (int j = 0; j < 16; ++j) acc[j] = ET(0);
         for (int i = threadIdx.x; i < half; i += nth) {
             const int p = half + i;              // colour-1 sites: every bond once
-            const uint32_t sw = sg[p];
+            const uint32_t sw = sg[p] >> cb;
             int q[Z];
             load_nbrs<Z>(S.nbr, p, q);
             if constexpr (GAUSS) {
@@ -364,7 +365,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
                 float Jsum = 0.f;
 #pragma unroll
                 for (int d = 0; d < Z; ++d) {
-                    nw[d] = sg[ICM_IDX(q[d], N, 6)];
+                    nw[d] = sg[ICM_IDX(q[d], N, 6)] >> cb;
                     const float J = S.Jd[ICM_IDX(p * Z + d, N * Z, 2)];
                     Jsum += J;
                     J2[d] = 2.f * J;
@@ -384,7 +385,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
                 const uint32_t jb = S.Jb[ICM_IDX(p, N, 3)];
                 uint32_t u[Z];
 #pragma unroll
-                for (int d = 0; d < Z; ++d) u[d] = sw ^ sg[ICM_IDX(q[d], N, 6)] ^ (0u - ((jb >> d) & 1u));
+                for (int d = 0; d < Z; ++d) u[d] = sw ^ (sg[ICM_IDX(q[d], N, 6)] >> cb) ^ (0u - ((jb >> d) & 1u));
                 csa_count<Z>(u, c0, c1, c2, c3);
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -410,6 +411,9 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
 //      of {q = -1};
 //  (d) flip in both copies (bits 2k, 2k+1 of C_p | C_p << 1), then E_a from
 //      the spins and E_b = (E_a + E_b)_before - E_a (the move is isoenergetic).
+//      A traced sweep also recomputes E_b from the spins and records
+//      E_a + E_b of the two recomputed energies, so that the trace tests the
+//      conservation of E_a + E_b instead of restating it.
 template <bool GAUSS, int Z, bool WIDE>
 __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
 {
@@ -623,7 +627,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         }
     }
     __syncthreads();
-    pair_energies<GAUSS, Z, WIDE>(P, S, act0, act1);
+    pair_energies<GAUSS, Z, WIDE>(P, S, act0, act1, 0);
     __syncthreads();
     for (int k = tid; k < nicm; k += nth) {
         if (S.icm_seed[k] < 0) continue;
@@ -632,15 +636,23 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         if constexpr (!GAUSS) ea = 2 * ea - S.nb;            // E = 2 U - N_b (bonds present)
         E[2 * k] = ea;
         E[2 * k + 1] = esum[k] - ea;
-        if (trace) {
-            const size_t o = (size_t)slot * P.nT + k;
-            P.tr_csize[o] = S.cnt_d[k];
-            P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
-        }
+        if (trace) P.tr_csize[(size_t)slot * P.nT + k] = S.cnt_d[k];
     }
     __syncthreads();
-    if (trace)
+    if (trace) {
+        // E_b of the moved pairs on its own, from the flipped spins
+        pair_energies<GAUSS, Z, WIDE>(P, S, act0, act1, 1);
+        __syncthreads();
+        for (int k = tid; k < nicm; k += nth) {
+            if (S.icm_seed[k] < 0) continue;
+            ET eb = ET(0);
+            for (int w = 0; w < nwarps; ++w) eb += ((const ET *)S.Epart)[w * 32 + k];
+            if constexpr (!GAUSS) eb = 2 * eb - S.nb;
+            P.tr_ea[(size_t)slot * P.nT + k] = (float)(E[2 * k] + eb);
+        }
         for (int k = tid; k < 32; k += nth) S.cnt_d[k] = 0;
+        __syncthreads();
+    }
     ICM_SUB(10);
 }
 

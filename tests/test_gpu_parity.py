@@ -3,14 +3,15 @@
 +-J couplings: bit-exact, sweep by sweep (spins, integer energies, n before
 step 2a, step-2a decisions, seed sites, cluster sizes, PT decisions) and for
 the accumulated observables.  Gaussian couplings: statistical agreement
-(energy per spin, link overlap, overlap distribution within 3.5 standard
-errors over instances), energy conservation of every cluster move to 1e-5
-of sum |J| in fp32, and the Eq. 1 identity.
+(energy per spin, link overlap, overlap distribution within three standard
+errors over instances, one Hotelling test per observable: statcheck),
+energy conservation of every cluster move to 1e-5 of sum |J| in fp32 (the
+kernel's own E_a + E_b and float64 energies of the spins), and the Eq. 1
+identity.
 """
-import math
-
 import numpy as np
 import pytest
+import statcheck
 
 from oracle import exact
 from oracle import oracle as O
@@ -181,9 +182,80 @@ def test_mix_invariance(icm):
 
 
 # ----------------------------------------------------------------------------- Gaussian, statistical
+def _e64(J, spins, g):
+    """H = -sum_b J_b s_i s_j of every replica, in float64 ([n][R])."""
+    out = np.empty(spins.shape[:2])
+    for a0 in range(0, spins.shape[0], 64):
+        sl = slice(a0, a0 + 64)
+        out[sl] = -np.einsum("nb,nrb->nr", J[sl].astype(np.float64),
+                             (spins[sl][:, :, g.bi] * spins[sl][:, :, g.bj]).astype(np.float64))
+    return out
+
+
+def _check_icm_only_step(b, g, J, T, T_icm, tol=1e-5):
+    """One step with only steps 2a/2b (no Metropolis sweep, no PT pass) on the
+    batch's current state, checked on the host against the spins:
+      * the spins change exactly on the traced clusters (copy b also by the
+        step-2a reversal), and each cluster is the connected component of its
+        traced seed among the q = -1 sites (the paper's cluster);
+      * E_a + E_b of each pair, recomputed from the spins in float64, is the
+        same before and after the move (the move is isoenergetic);
+      * the device energies after the move equal the float64 energies of the
+        spins, to tol * sum|J| (north_star's 1e-5 in fp32);
+      * the traced E_a + E_b, both recomputed by the kernel from the flipped
+        spins, equals the traced value before the move to tol * sum|J|.
+    Returns the number of moves checked."""
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import connected_components
+    nT = len(T)
+    sched = b.schedule()
+    b.set_schedule(enable_metropolis=0, swap_every=0, t_meas=1 << 40, trace=1)
+    s0 = b.read_spins()
+    b.run(1)
+    s1, E1, tr, cm = b.read_spins(), b.read_energies(), b.read_trace(), b.read_cluster_masks()
+    b.set_schedule(icm_every=sched.icm_every, swap_every=sched.swap_every, enable_2a=sched.enable_2a,
+                   enable_metropolis=sched.enable_metropolis, t_meas=sched.t_meas, trace=sched.trace)
+    scale = np.abs(J).astype(np.float64).sum(1)
+    e0, e1 = _e64(J, s0, g), _e64(J, s1, g)
+    icm_k = np.flatnonzero(T <= T_icm)
+    assert np.all(tr["n_pre"][:, icm_k] >= 0) and np.all(tr["n_pre"][:, len(icm_k):] == -1)
+    # conservation in float64 from the spins, every instance and ICM pair
+    d = (e1[:, 0::2] + e1[:, 1::2]) - (e0[:, 0::2] + e0[:, 1::2])
+    assert np.all(np.abs(d[:, icm_k]) <= 1e-9 * scale[:, None]), np.abs(d).max()
+    # device energies = float64 energies of the spins
+    assert np.all(np.abs(E1 - e1) <= tol * scale[:, None]), np.abs(E1 - e1).max()
+    # traced E_a + E_b: both recomputed by the kernel from the flipped spins
+    err = np.abs(tr["esum_after"] - tr["esum_before"])[:, icm_k]
+    assert np.all(err <= tol * scale[:, None]), err.max()
+    # the moved sets: spins change exactly on the cluster, which is the seed's component
+    moves = 0
+    for a in range(s0.shape[0]):
+        for k in icm_k:
+            sa, sb = s0[a, 2 * k], s0[a, 2 * k + 1].copy()
+            if tr["flip2a"][a, k]:
+                sb = -sb
+            neg = sa * sb == -1
+            comp = cm[a, k].astype(bool)
+            assert np.array_equal(s1[a, 2 * k] != sa, comp) and np.array_equal(s1[a, 2 * k + 1] != sb, comp)
+            assert comp.sum() == tr["csize"][a, k]
+            if not neg.any():
+                assert tr["seed_site"][a, k] == -1 and not comp.any()
+                continue
+            seed = tr["seed_site"][a, k]
+            assert neg[seed] and comp[seed]
+            if a % 50 == 0:                      # connectivity on a sample (scipy per pair)
+                m = neg[g.bi] & neg[g.bj] & (J[a] != 0)      # bonds present (dilution)
+                A = coo_matrix((np.ones(m.sum()), (g.bi[m], g.bj[m])), shape=(g.N, g.N))
+                _, lab = connected_components(A, directed=False)
+                assert np.array_equal(comp, neg & (lab == lab[seed]))
+            moves += 1
+    return moves
+
+
 def test_gauss_energy_conservation_and_consistency(icm):
-    """Every cluster move keeps E_a + E_b to 1e-5 sum|J| (fp32); device energies
-    agree with energies recomputed from the spins."""
+    """Every cluster move keeps E_a + E_b to 1e-5 sum|J| (fp32; the traced sum
+    is of E_a and E_b each recomputed from the flipped spins); device energies
+    agree with energies recomputed from the spins in float64."""
     icmpt, ctx = icm
     T = I.ladder(0.2, 2.0, 24)
     seed = 0x1501056300000002
@@ -200,11 +272,7 @@ def test_gauss_energy_conservation_and_consistency(icm):
         err = np.abs(tr["esum_after"] - tr["esum_before"])[icm_k]
         assert np.all(err <= 1e-5 * np.repeat(scale[:, None], 24, 1)[icm_k])
         spins, E = b.read_spins(), b.read_energies()
-        Jd = J.astype(np.float64)
-        e_ref = -np.einsum("b,rb->r", Jd[0], spins[0][:, g.bi] * spins[0][:, g.bj])
-        for a in range(0, 64, 9):
-            e_ref = -np.einsum("b,rb->r", Jd[a], (spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64))
-            assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a])
+        assert np.all(np.abs(E - _e64(J, spins, g)) <= 1e-5 * scale[:, None])
     assert moves > 100
 
 
@@ -212,8 +280,10 @@ def test_gauss_3d_L8_full_workload_invariants(icm):
     """The 3D L=8 Gaussian workload at its full size and launch shape (1000
     instances, 24 temperatures, ICM at 17, one launch of 256 sweeps, 128
     threads, 7 CTAs per SM): every cluster move of the last sweep keeps
-    E_a + E_b to 1e-5 sum|J|, and every instance's device energies equal the
-    energies recomputed from its spins in fp64 to 2e-5 sum|J|."""
+    E_a + E_b to 1e-5 sum|J|, every instance's device energies equal the
+    energies recomputed from its spins in fp64 to 1e-5 sum|J|; then one step
+    of cluster moves alone on that state, checked move by move against the
+    spins (see _check_icm_only_step)."""
     icmpt, ctx = icm
     T = I.ladder(0.2, 2.0, 24)
     seed = 0x1501056300000002
@@ -231,50 +301,61 @@ def test_gauss_3d_L8_full_workload_invariants(icm):
     err = np.abs(tr["esum_after"] - tr["esum_before"])[icm_k]
     assert np.all(err <= 1e-5 * np.repeat(scale[:, None], 24, 1)[icm_k])
     spins, E = b.read_spins(), b.read_energies()
-    Jd = J.astype(np.float64)
-    for a in range(n):
-        e_ref = -((spins[a][:, g.bi] * spins[a][:, g.bj]).astype(np.float64) @ Jd[a])
-        assert np.allclose(E[a], e_ref, rtol=0, atol=2e-5 * scale[a]), a
+    assert np.all(np.abs(E - _e64(J, spins, g)) <= 1e-5 * scale[:, None])
     assert np.array_equal(b.read_sweeps(), np.full(n, 256))
+    assert _check_icm_only_step(b, g, J, T, 1.0) > 5000
     b.close()
 
 
-def _stats(samples):
-    s = np.asarray(samples, dtype=np.float64)
-    return s.mean(0), s.std(0, ddof=1) / math.sqrt(len(s))
+def _paired(gpu_obs, refs, g):
+    """Per-instance GPU-minus-oracle differences of e, q_l and the coarse
+    symmetrised P(q), each [n][n_T(, bins)]."""
+    m = gpu_obs.n_meas[:, None].astype(np.float64)
+    ge = gpu_obs.accE / (2 * g.N * m)
+    gq = 1 - 2 * gpu_obs.acc_d / (g.Nb * m)
+    gp = statcheck.pq_bins(gpu_obs.hist)
+    oe = np.array([r.observables()["e"] for r in refs])
+    oq = np.array([r.observables()["q_l"] for r in refs])
+    op = statcheck.pq_bins(np.array([r.hist for r in refs]))
+    return dict(e=ge - oe, q_l=gq - oq, P_q=gp - op)
 
 
-def test_gauss_statistical_agreement_with_oracle(icm):
-    """3D L=4 Gaussian, 96 instances: per-temperature energy, link overlap and
-    <q^2> from the GPU agree with the oracle's on the same instances."""
+def _run_oracles(refs, sweeps):
+    """The oracle instances, spread over the host cores (ctypes drops the GIL)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        list(ex.map(lambda r: r.run(sweeps), refs))
+
+
+@pytest.mark.parametrize("L", [4, 6])
+def test_gauss_statistical_agreement_with_oracle(icm, L):
+    """3D L=4 and L=6 Gaussian, 256 instances, 2^14 sweeps (measured over the
+    second half), 24 temperatures in [0.2, 2.0], ICM for T <= 1: the energy per
+    spin, the link overlap and the symmetrised overlap distribution P(q)
+    (coarse bins of |q|) of every temperature agree between the GPU and the
+    oracle, on the same instances, at three standard errors over instances
+    (one Hotelling test per observable, see statcheck)."""
     icmpt, ctx = icm
-    T = I.ladder(0.3, 2.0, 8)
-    seed = 4242
-    n = 96
-    g, J, s0, ids = _setup(O.CUBIC3D, 4, I.GAUSS, n, T, seed)
-    sweeps, t_meas = 4000, 1000
-    b = icmpt.Batch(ctx, O.CUBIC3D, 4, I.GAUSS, J, T, 1.0, seed, spins=s0)
-    b.set_schedule(t_meas=t_meas)
+    T = I.ladder(0.2, 2.0, 24)
+    seed = 0x1501056300000020 + L
+    n, sweeps = 256, 1 << 14
+    g, J, s0, ids = _setup(O.CUBIC3D, L, I.GAUSS, n, T, seed)
+    b = icmpt.Batch(ctx, O.CUBIC3D, L, I.GAUSS, J, T, 1.0, seed, spins=s0)
+    b.set_schedule(t_meas=sweeps // 2)
     b.run(sweeps)
     o = b.read_observables()
-    m = o.n_meas[:, None].astype(np.float64)
-    gpu = dict(e=o.accE / (2 * g.N * m), q_l=1 - 2 * o.acc_d / (g.Nb * m), q2=o.acc_q2 / (g.N ** 2 * m))
-    cpu = {k: [] for k in gpu}
-    for a in range(n):
-        r = _oracle(g, J[a], s0[a], T, 1.0, seed, a, I.GAUSS, t_meas=t_meas)
-        r.run(sweeps)
-        ob = r.observables()
-        for k in cpu:
-            cpu[k].append(ob[k])
-    for k in gpu:
-        d = gpu[k] - np.asarray(cpu[k])          # paired by instance: disorder cancels
-        mu, se = _stats(d)
-        assert np.all(np.abs(mu) <= 3.5 * se + 1e-9), (k, mu, se)
+    refs = [_oracle(g, J[a], s0[a], T, 1.0, seed, a, I.GAUSS, t_meas=sweeps // 2) for a in range(n)]
+    _run_oracles(refs, sweeps)
+    for key, d in _paired(o, refs, g).items():
+        statcheck.agree(d, (L, key))
+    b.close()
 
 
 def test_gauss_matches_exact_enumeration(icm):
     """2D L=4 Gaussian (N = 16): 64 independent chains of one instance agree
-    with exact enumeration (energy, link overlap, symmetrised P(q))."""
+    with exact enumeration (energy, link overlap, symmetrised P(q) at the
+    lowest and highest temperature), three standard errors (statcheck)."""
     icmpt, ctx = icm
     T = I.ladder(0.4, 2.0, 6)
     seed = 5
@@ -292,19 +373,17 @@ def test_gauss_matches_exact_enumeration(icm):
     E = exact.energies(g.bi, g.bj, J1.astype(np.float64), st)
     ex = [exact.thermal(g.bi, g.bj, J1.astype(np.float64), g.N, t, st, E) for t in T]
     for name, vals in (("e", o.accE / (2 * g.N * m)), ("q_l", 1 - 2 * o.acc_d / (g.Nb * m))):
-        mu, se = _stats(vals)
         want = np.array([x[name] for x in ex])
-        assert np.all(np.abs(mu - want) <= 3.5 * se + 1e-4), (name, mu, se, want)
-    P = o.hist / m[:, :, None] if o.hist.ndim == 3 else None
+        statcheck.agree(vals - want[None, :], name)
+    P = o.hist / m[:, :, None]
     for k in (0, len(T) - 1):
-        sym = (P[:, k] + P[:, k, ::-1]) / 2
-        mu, se = _stats(sym)
-        assert np.all(np.abs(mu - ex[k]["P_n"]) <= 3.5 * se + 2e-3)
+        statcheck.agree_distribution((P[:, k] + P[:, k, ::-1]) / 2, ex[k]["P_n"], o.n_meas, (k, "P(q)"))
 
 
 def test_gauss_eq1_identity(icm):
     """Eq. 1: disorder-averaged e = -(N_b/N)(1 - [q_l])/T at equilibrium
-    (3D L=4, 200 instances, well-thermalised moderate temperatures)."""
+    (3D L=4, 200 instances, well-thermalised moderate temperatures), three
+    standard errors over instances (statcheck)."""
     icmpt, ctx = icm
     T = I.ladder(0.6, 2.0, 8)
     seed = 31
@@ -317,9 +396,7 @@ def test_gauss_eq1_identity(icm):
     m = o.n_meas[:, None].astype(np.float64)
     e = o.accE / (2 * g.N * m)
     ql = 1 - 2 * o.acc_d / (g.Nb * m)
-    d = e + (g.Nb / g.N) * (1 - ql) / T[None, :]
-    mu, se = _stats(d)
-    assert np.all(np.abs(mu) <= 3.5 * se + 2e-3), (mu, se)
+    statcheck.agree(e + (g.Nb / g.N) * (1 - ql) / T[None, :], "Eq. 1")
 
 
 # ----------------------------------------------------------------------------- limits and errors
@@ -399,7 +476,8 @@ def test_gauss_3d_L16_conservation_and_consistency(icm, threads):
 
 def test_wide_layout_gauss_statistical_agreement_with_oracle(icm):
     """3D L=4 Gaussian forced into the wide layout: per-temperature energy,
-    link overlap and <q^2> agree with the oracle's on the same instances."""
+    link overlap and P(q) agree with the oracle's on the same instances at
+    three standard errors (statcheck)."""
     icmpt, ctx = icm
     T = I.ladder(0.3, 2.0, 8)
     seed = 4343
@@ -411,18 +489,10 @@ def test_wide_layout_gauss_statistical_agreement_with_oracle(icm):
     b.set_schedule(t_meas=t_meas)
     b.run(sweeps)
     o = b.read_observables()
-    m = o.n_meas[:, None].astype(np.float64)
-    gpu = dict(e=o.accE / (2 * g.N * m), q_l=1 - 2 * o.acc_d / (g.Nb * m), q2=o.acc_q2 / (g.N ** 2 * m))
-    cpu = {k: [] for k in gpu}
-    for a in range(n):
-        r = _oracle(g, J[a], s0[a], T, 1.0, seed, a, I.GAUSS, t_meas=t_meas)
-        r.run(sweeps)
-        ob = r.observables()
-        for k in cpu:
-            cpu[k].append(ob[k])
-    for k in gpu:
-        mu, se = _stats(gpu[k] - np.asarray(cpu[k]))
-        assert np.all(np.abs(mu) <= 3.5 * se + 1e-9), (k, mu, se)
+    refs = [_oracle(g, J[a], s0[a], T, 1.0, seed, a, I.GAUSS, t_meas=t_meas) for a in range(n)]
+    _run_oracles(refs, sweeps)
+    for key, d in _paired(o, refs, g).items():
+        statcheck.agree(d, key)
 
 
 def test_wide_layout_autotune_keeps_state(icm):

@@ -16,6 +16,7 @@ import math
 
 import numpy as np
 import pytest
+import statcheck
 
 from oracle import exact
 from oracle import oracle as O
@@ -139,6 +140,31 @@ def test_exact_overlap_distribution_is_normalised_and_symmetric():
     assert np.allclose(th["P_n"], th["P_n"][::-1], atol=1e-12)   # spin-reversal symmetry
 
 
+@pytest.mark.parametrize("kind,L,T", [(O.CHIMERA, 1, 0.7), (O.CUBIC3D, 2, 1.3)])
+def test_exact_overlap_distribution_equals_direct_double_sum(kind, L, T):
+    """P(n) of two independent replicas, written out as the double sum over
+    state pairs sum_s sum_t p(s) p(t) [popcount(s xor t) = n] (N = 8), equals
+    the transform-based P(n) of exact.thermal, and so do <q^2>, <n>/N and p
+    from it."""
+    g = O.Geometry(kind, L)
+    assert g.N == 8
+    J = I.couplings(g.Nb, I.GAUSS, 17, [0])[0].astype(np.float64)
+    st = exact.all_states(g.N)
+    E = -(st[:, g.bi].astype(np.float64) * st[:, g.bj]) @ J
+    p = np.exp(-(E - E.min()) / T)
+    p /= p.sum()
+    P = np.zeros(g.N + 1)
+    for s in range(1 << g.N):
+        for t in range(1 << g.N):
+            P[bin(s ^ t).count("1")] += p[s] * p[t]
+    th = exact.thermal(g.bi, g.bj, J, g.N, T)
+    assert np.allclose(th["P_n"], P, rtol=0, atol=1e-14)
+    n = np.arange(g.N + 1)
+    assert th["q2"] == pytest.approx(np.sum(P * (1 - 2 * n / g.N) ** 2), abs=1e-14)
+    assert th["n_frac"] == pytest.approx(np.sum(P * n) / g.N, abs=1e-14)
+    assert th["p"] == pytest.approx(np.sum(P * np.minimum(n, g.N - n)) / g.N, abs=1e-14)
+
+
 def test_eq1_identity_for_gaussian_disorder_exact():
     """[<H>]/N = -(N_b/N)(1 - [q_l])/T, averaged over Gaussian disorder (Eq. 1)."""
     g = O.Geometry(O.SQUARE2D, 4)
@@ -150,7 +176,7 @@ def test_eq1_identity_for_gaussian_disorder_exact():
         th = exact.thermal(g.bi, g.bj, J, g.N, T, st)
         d.append(th["e"] + (g.Nb / g.N) * (1.0 - th["q_l"]) / T)
     d = np.array(d)
-    assert abs(d.mean()) < 3.5 * d.std(ddof=1) / math.sqrt(len(d))
+    statcheck.agree(d, "Eq. 1")
     # the identity is a disorder average: single instances do deviate
     assert d.std() > 1e-3
 
@@ -170,10 +196,12 @@ def _chains(kind, L, disorder, T, T_icm, n_chains, sweeps, seed=5, t_meas=None, 
     return g, J, obs
 
 
-def _agree(samples, target, nsig=3.5, floor=1e-9):
-    samples = np.asarray(samples)
-    se = samples.std(ddof=1, axis=0) / math.sqrt(len(samples))
-    return np.all(np.abs(samples.mean(axis=0) - target) <= nsig * se + floor), samples.mean(0), se
+def _agree(samples, target):
+    """Samples agree with target at three standard errors (one Hotelling test
+    over all components, statcheck); returns (ok, sample mean, test figures)."""
+    d = np.asarray(samples, dtype=np.float64) - np.asarray(target, dtype=np.float64)
+    r = statcheck.hotelling(d)
+    return r["p"] >= statcheck.P_3SIGMA, d.mean(0) + target, r
 
 
 @pytest.mark.parametrize("kind,L,disorder", [
@@ -195,8 +223,7 @@ def test_oracle_chain_matches_exact_enumeration(kind, L, disorder):
     # symmetrised, (P(n) + P(N - n))/2, with the (symmetric) exact P(n).
     for k in (0, len(T) - 1):
         sym = [(o["P_n"][k] + o["P_n"][k][::-1]) / 2 for o in obs]
-        ok, mean, se = _agree(sym, ex[k]["P_n"], floor=2e-3)
-        assert ok, (k, mean, se, ex[k]["P_n"])
+        statcheck.agree_distribution(sym, ex[k]["P_n"], [o["n_meas"] for o in obs], (k, "P(n)"))
 
 
 def test_oracle_samples_boltzmann_distribution_chi2():

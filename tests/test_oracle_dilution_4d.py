@@ -18,10 +18,10 @@ lattices (bonds with J = 0 absent from the lattice).
   accepted with probability 1/2, clusters are single sites and every swap is
   accepted.
 """
-import math
 
 import numpy as np
 import pytest
+import statcheck
 
 from oracle import exact
 from oracle import oracle as O
@@ -58,10 +58,12 @@ def test_geometry_4d_smallest_torus_keeps_doubled_bonds():
     assert np.all(d == 8)
 
 
-def _agree(samples, target, nsig=3.5, floor=1e-9):
-    samples = np.asarray(samples)
-    se = samples.std(ddof=1, axis=0) / math.sqrt(len(samples))
-    return np.all(np.abs(samples.mean(axis=0) - target) <= nsig * se + floor), samples.mean(0), se
+def _agree(samples, target):
+    """Samples agree with target at three standard errors (one Hotelling test
+    over all components, statcheck); returns (ok, sample mean, test figures)."""
+    d = np.asarray(samples, dtype=np.float64) - np.asarray(target, dtype=np.float64)
+    r = statcheck.hotelling(d)
+    return r["p"] >= statcheck.P_3SIGMA, d.mean(0) + target, r
 
 
 @pytest.mark.parametrize("disorder", [I.PM_J, I.GAUSS])
