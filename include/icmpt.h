@@ -199,17 +199,31 @@ icm_status icm_batch_load(icm_batch *b, const void *couplings, const int8_t *spi
                           uint32_t t0, uint32_t flags);
 
 /* Replace the temperature ladder (same n_T; ascending, > 0) and T_icm, e.g.
- * between the steps of an annealing schedule ("convergence of simulated
- * annealing ... improved by adding isoenergetic cluster moves at each
- * temperature step").  Takes effect from the next icm_run_sweeps; the
- * configurations, energies and sweep counters are kept.                   */
+ * between the steps of an annealing schedule: the paper's introduction
+ * proposes simulated annealing with cluster moves at every temperature of
+ * its schedule as a ground-state heuristic.  Takes effect from the next
+ * icm_run_sweeps; the configurations, energies and sweep counters are kept. */
 icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, double T_icm);
 
+/* Which steps of the simulation step ("Isoenergetic cluster algorithm":
+ * 1 Metropolis sweep, 2a copy-1 reversal, 2b cluster move, 3 PT pass; the
+ * observables of "Benchmark model and observables") run at each sweep t, see
+ * icm_schedule.  The paper runs every step at every sweep (the default);
+ * other schedules serve its comparisons (plain PT: icm_every = 0; the
+ * Houdayer algorithm: cluster moves at every temperature without 2a) and
+ * tests.  Takes effect from the next icm_run_sweeps.  icm_get_schedule
+ * returns the batch's current schedule.                                  */
 icm_status icm_set_schedule(icm_batch *b, const icm_schedule *s);
 icm_status icm_get_schedule(const icm_batch *b, icm_schedule *s);
 
-/* Enqueue n_sweeps simulation steps of every instance (one kernel launch).
- * Asynchronous. */
+/* Enqueue n_sweeps simulation steps of every instance, in one kernel launch.
+ * One simulation step is the paper's loop of "Isoenergetic cluster
+ * algorithm" (steps 1, 2a, 2b, 3, in that order, as listed at the top of
+ * this file), followed by the measurement of "Benchmark model and
+ * observables" when t >= t_meas; the sweep counter t of each instance
+ * advances by one per step.  Asynchronous: returns once the launch is
+ * enqueued on the context's stream.  ICM_ERR_STATE if the batch holds
+ * refused (invalid) couplings.                                            */
 icm_status icm_run_sweeps(icm_batch *b, uint32_t n_sweeps);
 
 /* ---------------------------------------------------------------- reads
@@ -403,15 +417,18 @@ icm_status icm_batch_delta(icm_batch *b, int32_t k, double *delta_mean, double *
  *               int8 0 counts as +1), Gaussian zeros contribute 0
  *   spins     : device [n_inst][n_rep][N] int8 +-1, 1 <= n_rep <= 64
  *   out       : device [n_inst][n_rep] double, H = -sum_<ij> J_ij s_i s_j
- * Work is enqueued on the context's stream; the call returns after it ends.
- * Scratch is one fixed 8 MiB array in the library's device image, held by
- * every GPU that loads the library until the process exits.  Requests that
- * need more (geometry tables + n_inst instances of packed spins, expanded
- * couplings and energies) fail with ICM_ERR_UNSUPPORTED and a message.  The
- * first call on a device looks up the array's address (do it before any
- * stream capture).  All calls share the array: calls that overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller.  Every scratch byte a call reads is written earlier in that call. */
+ * Work is enqueued on the context's stream, and the call then synchronises
+ * that stream: it returns after the work has ended.  Scratch is one fixed
+ * 8 MiB array in the library's device image, held by every GPU that loads
+ * the library until the process exits.  Requests that need more (geometry
+ * tables + n_inst instances of packed spins, expanded couplings and
+ * energies) fail with ICM_ERR_UNSUPPORTED and a message.  The first call on
+ * a device looks up the array's address (do it before any stream capture);
+ * after a cudaDeviceReset of that device the looked-up address is stale, so
+ * do not call this entry point on a device that was reset.  All calls share
+ * the array: calls that overlap on the GPU (other streams, other host
+ * threads) race and must be serialised by the caller.  Every scratch byte a
+ * call reads is written earlier in that call.                              */
 icm_status icm_energies_static(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t disorder, int32_t n_inst,
                                int32_t n_rep, const void *couplings, const int8_t *spins, double *out);
 

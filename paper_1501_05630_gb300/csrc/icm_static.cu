@@ -11,6 +11,7 @@
 #include "icmpt.h"
 
 #include <cstring>
+#include <mutex>
 #include <string>
 
 #include "icm_internal.h"
@@ -24,7 +25,14 @@ constexpr size_t kStaticScratchBytes = size_t(8) << 20;   // 8 MiB
 static __device__ __align__(256) unsigned char g_icm_static_scratch[kStaticScratchBytes];
 
 constexpr int kMaxDevices = 64;
-void *g_scratch_addr[kMaxDevices];   // device address of the array, per device (set up on first use)
+// Device address of the array, per device, looked up by the first call on
+// that device (with the device current) under g_scratch_mutex, so that host
+// threads calling on different devices at the same time do not race on it.
+// cudaDeviceReset unloads the module that holds the array, so the address
+// looked up before a reset is not valid after it: a process that resets a
+// device must not call this entry point on that device afterwards.
+void *g_scratch_addr[kMaxDevices];
+std::mutex g_scratch_mutex;
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 
@@ -81,14 +89,20 @@ extern "C" icm_status icm_energies_static(icm_ctx *ctx, int32_t lattice, int32_t
         return ICM_ERR_ARG;
     }
     cudaError_t e = cudaSetDevice(dev);
-    if (e == cudaSuccess && !g_scratch_addr[dev])   // first call on this device: look up the array's address
-        e = cudaGetSymbolAddress(&g_scratch_addr[dev], g_icm_static_scratch);
-    if (e != cudaSuccess || !g_scratch_addr[dev]) {
-        g_scratch_addr[dev] = nullptr;
+    void *addr = nullptr;
+    if (e == cudaSuccess) {
+        std::lock_guard<std::mutex> lock(g_scratch_mutex);
+        if (!g_scratch_addr[dev]) {                  // first call on this device: look up the array's address
+            e = cudaGetSymbolAddress(&addr, g_icm_static_scratch);
+            if (e == cudaSuccess) g_scratch_addr[dev] = addr;
+        }
+        addr = g_scratch_addr[dev];
+    }
+    if (e != cudaSuccess || !addr) {
         icm::set_ctx_error(ctx, std::string("icm_energies_static: scratch set-up failed: ") + cudaGetErrorString(e));
         return ICM_ERR_CUDA;
     }
-    unsigned char *base = (unsigned char *)g_scratch_addr[dev];
+    unsigned char *base = (unsigned char *)addr;
     cudaStream_t st = icm::ctx_stream(ctx);
     icm::KParams P{};
     P.N = N; P.Nb = tab.Nb; P.R = n_rep; P.G = G; P.Z = Z; P.n_inst = n_inst; P.half = N / 2;

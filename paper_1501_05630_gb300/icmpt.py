@@ -234,6 +234,7 @@ class Context:
             rc = self._lib.icm_ctx_create(ctypes.byref(h), int(device), st)
         if rc:
             raise IcmError(rc, "icm_ctx_create failed (no CUDA device?)")
+        self.device = int(device)
         self._h = h
         self._batches = weakref.WeakSet()
 
@@ -315,13 +316,43 @@ def therm_update(state: ThermState, crit: ThermCriterion, e: float, q_l: float, 
     return bool(out.value)
 
 
+def _check_static_args(device: int, N: int, Nb: int, disorder: int, couplings, spins, out):
+    """Shapes, dtypes and device of the energies_static tensors: the library
+    reads and writes exactly [n_inst][N_b] couplings (int8 for +-J, float32
+    for Gaussian), [n_inst][n_rep][N] int8 spins and [n_inst][n_rep] float64
+    energies, so any other shape or dtype would be read or written past the
+    caller's buffers on the device.  Returns (n_inst, n_rep)."""
+    names = ("couplings", "spins", "out")
+    for name, a in zip(names, (couplings, spins, out)):
+        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
+            raise ValueError(f"energies_static: {name} must be a contiguous CUDA tensor")
+        dev = getattr(a, "device", None)
+        if getattr(dev, "index", device) not in (None, device):
+            raise ValueError(f"energies_static: {name} is on {dev}, the context is on cuda:{device}")
+    if len(spins.shape) != 3 or int(spins.shape[2]) != N:
+        raise ValueError(f"energies_static: spins must be [n_inst][n_rep][{N}], got {tuple(spins.shape)}")
+    n_inst, n_rep = int(spins.shape[0]), int(spins.shape[1])
+    want_j = "torch.float32" if disorder == GAUSS else "torch.int8"
+    if str(couplings.dtype) != want_j or tuple(couplings.shape) != (n_inst, Nb):
+        raise ValueError(f"energies_static: couplings must be {want_j} [{n_inst}][{Nb}], "
+                         f"got {couplings.dtype} {tuple(couplings.shape)}")
+    if str(spins.dtype) != "torch.int8":
+        raise ValueError(f"energies_static: spins must be torch.int8, got {spins.dtype}")
+    if str(out.dtype) != "torch.float64" or tuple(out.shape) != (n_inst, n_rep):
+        raise ValueError(f"energies_static: out must be torch.float64 [{n_inst}][{n_rep}], "
+                         f"got {out.dtype} {tuple(out.shape)}")
+    return n_inst, n_rep
+
+
 def energies_static(ctx: Context, lattice: int, L: int, disorder: int, couplings, spins, out):
     """Energies [n_inst][n_rep] of device spin arrays, computed on the library's
-    fixed device scratch (no device allocation; see icm_energies_static)."""
-    for a in (couplings, spins, out):
-        if not (hasattr(a, "is_cuda") and a.is_cuda and a.is_contiguous()):
-            raise ValueError("energies_static takes contiguous CUDA tensors")
-    n_inst, n_rep = int(spins.shape[0]), int(spins.shape[1])
+    fixed device scratch (no device allocation; see icm_energies_static).
+    Raises ValueError before any device work when a tensor's shape, dtype or
+    device does not match the lattice, the disorder kind and the context."""
+    if disorder not in (PM_J, GAUSS):
+        raise ValueError("energies_static: disorder must be PM_J or GAUSS")
+    N, Nb = lattice_size(lattice, L)
+    n_inst, n_rep = _check_static_args(ctx.device, N, Nb, disorder, couplings, spins, out)
     ctx.check(ctx._lib.icm_energies_static(ctx._h, int(lattice), int(L), int(disorder), n_inst, n_rep,
                                            couplings.data_ptr(), spins.data_ptr(), out.data_ptr()))
     return out

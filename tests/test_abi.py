@@ -115,3 +115,43 @@ def test_inputs_are_deterministic_and_typed():
     T = I.ladder(0.2, 2.0, 24)
     assert T[0] == 0.2 and abs(T[-1] - 2.0) < 1e-12 and np.all(np.diff(T) > 0)
     assert int(np.sum(T <= 1.0)) == 17
+
+
+class _FakeTensor:
+    """Just the attributes energies_static inspects (no device memory)."""
+
+    def __init__(self, shape, dtype, index=0, cuda=True, contiguous=True):
+        import types
+        self.shape, self.dtype, self.is_cuda = tuple(shape), dtype, cuda
+        self.device = types.SimpleNamespace(index=index)
+        self._contiguous = contiguous
+
+    def is_contiguous(self):
+        return self._contiguous
+
+
+def test_energies_static_checks_shapes_dtypes_and_device():
+    """Wrong dtypes, shapes or devices are refused with ValueError before the
+    library is called (it would read or write past the caller's buffers)."""
+    from paper_1501_05630_gb300.icmpt import _check_static_args
+    N, Nb, n, r = 512, 1536, 3, 48
+    ok = dict(couplings=_FakeTensor((n, Nb), "torch.float32"), spins=_FakeTensor((n, r, N), "torch.int8"),
+              out=_FakeTensor((n, r), "torch.float64"))
+    assert _check_static_args(0, N, Nb, I.GAUSS, **ok) == (n, r)
+    pmj = dict(ok, couplings=_FakeTensor((n, Nb), "torch.int8"))
+    assert _check_static_args(0, N, Nb, I.PM_J, **pmj) == (n, r)
+    bad = [
+        (I.GAUSS, dict(ok, couplings=_FakeTensor((n, Nb), "torch.int8"))),      # +-J couplings passed as Gaussian
+        (I.PM_J, ok),                                                          # float couplings passed as +-J
+        (I.GAUSS, dict(ok, couplings=_FakeTensor((n, Nb - 1), "torch.float32"))),
+        (I.GAUSS, dict(ok, spins=_FakeTensor((n, r, N - 1), "torch.int8"))),
+        (I.GAUSS, dict(ok, spins=_FakeTensor((n, r, N), "torch.float32"))),
+        (I.GAUSS, dict(ok, out=_FakeTensor((n, r), "torch.float32"))),
+        (I.GAUSS, dict(ok, out=_FakeTensor((n, r + 1), "torch.float64"))),
+        (I.GAUSS, dict(ok, out=_FakeTensor((n, r), "torch.float64", index=1))),   # another device
+        (I.GAUSS, dict(ok, spins=_FakeTensor((n, r, N), "torch.int8", cuda=False))),
+        (I.GAUSS, dict(ok, spins=_FakeTensor((n, r, N), "torch.int8", contiguous=False))),
+    ]
+    for dis, kw in bad:
+        with pytest.raises(ValueError):
+            _check_static_args(0, N, Nb, dis, **kw)
