@@ -60,6 +60,72 @@ ALG_OPS = {I.PM_J: lambda z: 24.5 + 12.5,
            I.GAUSS: lambda z: 24.5 + 12.5 + z + 1}
 
 
+
+def icm_ops(N: int, Nb: int, z: int, n_icm: int, pairs: float, moves: float, scans: float) -> float:
+    """Algorithmic operations of the cluster moves (steps 2a/2b), the
+    method's cost model of O(N + N_b) per pair plus the growth iterations:
+      per ICM pair visited (`pairs` = instances x ICM temperatures x sweeps):
+        the overlap q_i (N), the count n (N), step 2a (N);
+      per moved pair (`moves`, n > 0, from the device counter): the seed
+        draw (one Philox4x32-10 call, 98 ops), the rank search (N), the flip
+        of both copies (2N), the energy update over the bonds (N_b);
+      per growth scan (`scans`, from the device counter, summed over the
+        instances): one pass over the site words that hold ICM pairs
+        (ceil(n_icm / 16) per site, two replica bits per pair), each word
+        the OR of its z neighbours' cluster words, one AND with its domain
+        and one OR into its own word (z + 2).
+    One operation per spin (or bond) and pair, as the method is written,
+    except the growth, counted per 32-bit word of the bit-parallel flood fill
+    that stands for one label-propagation pass of every pair."""
+    words = -(-n_icm // 16)
+    return pairs * 3 * N + moves * (98 + 3 * N + Nb) + scans * words * N * (z + 2)
+
+
+def phase_fractions(b, stream, flush, S, n_inst, updates_per_step, ops_per_update, N, Nb, z, n_icm, peak):
+    """Roofline fractions of the two phases, from launches that differ only in
+    the public schedule flags: the sweep alone (no cluster moves, PT pass or
+    measurement) and the cluster moves alone (no Metropolis sweep, PT pass or
+    measurement), each timed over three launches of S sweeps after one
+    untimed launch, with CUDA events on the launching stream and L2 flushed
+    between launches.  The schedule is restored afterwards."""
+    import torch
+    sched = b.schedule()
+    keep = {k: getattr(sched, k) for k in ("icm_every", "swap_every", "enable_2a", "enable_metropolis",
+                                           "t_meas", "trace")}
+
+    def timed(n=3):
+        b.run(S)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(n):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.run(S)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.mean(ts))
+
+    b.set_schedule(icm_every=0, swap_every=0, t_meas=1 << 62, trace=0)
+    t_sweep = timed()
+    b.set_schedule(icm_every=1, swap_every=0, enable_metropolis=0, t_meas=1 << 62, trace=0)
+    b.clear_observables()
+    t_icm = timed()
+    st = b.read_icm_stats().astype(np.float64)
+    b.set_schedule(**keep)
+    moves, scans = st[:, 0].sum() / 4, st[:, 1].sum() / 4        # per launch (4 launches counted)
+    pairs = n_inst * n_icm * S
+    sweep_ach = updates_per_step * ops_per_update / (t_sweep * 1e-3) / 1e12
+    icm_ach = icm_ops(N, Nb, z, n_icm, pairs, moves, scans) / (t_icm * 1e-3) / 1e12
+    return {"sweep_frac": sweep_ach / peak, "sweep_ms": t_sweep,
+            "sweep_updates_per_ns": updates_per_step / (t_sweep * 1e6),
+            "icm_frac": icm_ach / peak, "icm_ms": t_icm, "icm_moved_fraction": moves / pairs,
+            "icm_scans_per_sweep": scans / (n_inst * S),
+            "phase_note": "sweep_frac: Metropolis ops of a sweep-only launch; icm_frac: cluster-move ops "
+                          "(icm_ops) of an ICM-only launch; both over the same issue peak"}
+
+
 # the sources of the fused kernel (its launch shape and arithmetic); host-side
 # files (the API, the request server, other kernels) do not change its traffic
 FUSED_SOURCES = ("pt_icm.cu", "fused_pmj.cu", "fused_gauss.cu", "icm_device.cuh", "icm_internal.h")
@@ -250,7 +316,19 @@ def serving_requests(n, rate, seed, n_T_choices):
     return reqs
 
 
-def run_serving(args):
+def _menu_name(lat, L, dis):
+    return f"{['2D', '3D', 'chimera', '4D'][lat]} L={L} {['pmJ', 'gauss'][dis]}"
+
+
+def serving_measurement(args):
+    """Workload 5 (serving): a Poisson stream of requests over the full menu,
+    run to the per-instance thermalization criterion by the native
+    continuous-batching server; then the plain method one instance at a time
+    (plain PT: T_icm below every temperature, so no step 2a or 2b; a one-slot
+    server, the same criterion and sweep cap) on a sample stratified by menu
+    kind, `alone_sample` requests of each kind taken round-robin over the
+    kinds and started while `alone_seconds` last.  Returns the figures as a
+    dict (rates in instances thermalized per second of wall time)."""
     import torch
     from paper_1501_05630_gb300 import build
     from paper_1501_05630_gb300.serve import Server
@@ -277,47 +355,71 @@ def run_serving(args):
                 continue
             srv.step()
         wall = time.perf_counter() - start
-    res = [srv.poll(t) for t in tickets]
-    lat = np.array([r.latency for r in res])
-    therm = sum(r.status == "thermalized" for r in res)
+    res = {t: srv.poll(t) for t in tickets}
     srv.close()
-    # one instance at a time (the plain form), same criterion, on a sample
-    # stratified like the stream: the first `alone_sample` requests of each
-    # menu kind (the stream draws kinds uniformly)
-    sample, per_kind = [], {}
+    lat = np.array([r.latency for r in res.values()])
+    therm = sum(r.status == "thermalized" for r in res.values())
+    last_arrival = max(r.arrival for r in tickets.values())
+    admits = np.array([r.admitted for r in res.values()])
+    per_class = {}
+    for t, r in tickets.items():
+        c = per_class.setdefault(_menu_name(r.lattice, r.L, r.disorder), {"requests": 0, "thermalized": 0})
+        c["requests"] += 1
+        c["thermalized"] += res[t].status == "thermalized"
+    # the plain method, one instance at a time
+    kinds = {}
     for r in pending:
-        k = (r.lattice, r.L, r.disorder)
-        if per_kind.get(k, 0) < args.alone_sample:
-            per_kind[k] = per_kind.get(k, 0) + 1
-            sample.append(r)
+        kinds.setdefault((r.lattice, r.L, r.disorder), []).append(r)
+    order = [kinds[k][j] for j in range(args.alone_sample) for k in kinds if j < len(kinds[k])]
     a0 = time.perf_counter()
-    alone_therm = 0
-    for r in sample:
+    alone_therm, alone_done, alone_class = 0, 0, {}
+    for r in order:
+        if time.perf_counter() - a0 > args.alone_seconds:
+            break
         one = Server(slots_per_class=1, **kw)
         r2 = dataclasses_replace(r)
+        r2.T_icm = 0.0                                      # plain PT: no cluster temperature
         tk = one.submit(r2)
         one.run_until_idle()
-        alone_therm += one.poll(tk).status == "thermalized"
+        ok = one.poll(tk).status == "thermalized"
         one.close()
+        alone_therm += ok
+        alone_done += 1
+        c = alone_class.setdefault(_menu_name(r.lattice, r.L, r.disorder), {"requests": 0, "thermalized": 0})
+        c["requests"] += 1
+        c["thermalized"] += int(ok)
     alone_s = time.perf_counter() - a0
-    out = {
-        "metric": "instances_thermalized_per_s", "value": therm / wall, "unit": "instances/s", "n_gpus": 1,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "data": "synthetic",
-        "dtype": "u32/f32", "config": {"workload": "serving", "requests": len(res), "rate_per_s": args.rate,
-                                       "menu": [f"{['2D', '3D', 'chimera'][m[0]]} L={m[1]} {['pmJ', 'gauss'][m[2]]}"
-                                                for m in SERVING_MENU], "n_T": n_T, "quantum": args.quantum,
-                                       "max_sweeps": args.max_sweeps, "slots_per_class": args.slots,
-                                       "criterion": "block means of e and q_l at T_min agree (|de|<=0.005, "
-                                                    "|dq_l|<=0.01) on 2 consecutive doubling windows"},
+    return {
+        "instances_thermalized_per_s": therm / wall, "latency_p50_s": float(np.percentile(lat, 50)),
+        "latency_p99_s": float(np.percentile(lat, 99)), "requests": len(res), "offered_per_s": args.rate,
         "thermalized": int(therm), "not_thermalized": int(len(res) - therm), "wall_s": wall,
-        "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
-        "mean_sweeps": float(np.mean([r.sweeps for r in res])),
-        "one_at_a_time": {"requests": len(sample), "sample": f"{args.alone_sample} per menu kind, first arrivals",
-                          "thermalized": int(alone_therm), "wall_s": alone_s,
-                          "value": alone_therm / alone_s, "unit": "instances/s"},
+        "completed_per_s": len(res) / wall,
+        "admitted_per_s": len(res) / max(float(admits.max()) - start, 1e-9),
+        "backlog_at_last_arrival": int(np.sum(admits > last_arrival)),
+        "sustainable": bool(len(res) / wall >= 0.95 * args.rate),
+        "mean_sweeps": float(np.mean([r.sweeps for r in res.values()])),
+        "per_class": per_class,
+        "one_at_a_time_plain_pt": {"value": alone_therm / alone_s, "unit": "instances/s",
+                                   "requests": alone_done, "thermalized": int(alone_therm), "wall_s": alone_s,
+                                   "sample": f"{args.alone_sample} per menu kind, round-robin over the kinds, "
+                                             f"started within {args.alone_seconds:.0f} s",
+                                   "per_class": alone_class},
+        "config": {"menu": [_menu_name(*m[:3]) for m in SERVING_MENU], "n_T": n_T, "quantum": args.quantum,
+                   "max_sweeps": args.max_sweeps, "slots_per_class": args.slots,
+                   "criterion": "block means of e and q_l at T_min agree (|de|<=0.005, |dq_l|<=0.01) on 2 "
+                                "consecutive doubling windows"},
         "clocks": clk.summary(),
     }
-    print(json.dumps(out))
+
+
+def run_serving(args):
+    out = serving_measurement(args)
+    line = {"metric": "instances_thermalized_per_s", "value": out["instances_thermalized_per_s"],
+            "unit": "instances/s", "n_gpus": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "data": "synthetic", "dtype": "u32/f32",
+            "config": dict(out.pop("config"), workload="serving", requests=args.requests, rate_per_s=args.rate)}
+    line.update(out)
+    print(json.dumps(line))
 
 
 def dataclasses_replace(r):
@@ -629,7 +731,11 @@ def main():
     ap.add_argument("--max-sweeps", type=int, default=1 << 14)
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--serving-nT", default="16,24,32")
-    ap.add_argument("--alone-sample", type=int, default=1, help="serving: one-at-a-time requests per menu kind")
+    ap.add_argument("--alone-sample", type=int, default=3, help="serving: one-at-a-time requests per menu kind")
+    ap.add_argument("--alone-seconds", type=float, default=40.0,
+                    help="serving: start one-at-a-time requests while this many seconds last")
+    ap.add_argument("--no-serving", action="store_true", help="default workload: leave out the serving leg")
+    ap.add_argument("--no-phases", action="store_true", help="leave out the sweep-only / ICM-only launches")
     ap.add_argument("--masks", type=int, default=200000)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--log2-max", type=int, default=17)
@@ -721,6 +827,8 @@ def main():
         b.run(S)
     barrier()
     launches0 = b.info()["launches"]
+    b.clear_observables()                                         # cluster-move counters of the timed steps
+    barrier()
     times = []
     with ClockSampler(local) as clk:
         barrier()
@@ -743,7 +851,9 @@ def main():
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     value = updates_per_step * args.steps * world / (ms * 1e6)
-    icm_moves_per_s = n * n_icm * S * args.steps * world / (ms * 1e-3)
+    icm_attempts_per_s = n * n_icm * S * args.steps * world / (ms * 1e-3)
+    stats = b.read_icm_stats().astype(np.float64)
+    icm_moves_per_s = stats[:, 0].sum() * world / (ms * 1e-3)     # pairs with n > 0 (a cluster moved)
 
     # end to end through the C ABI with host buffers
     e2e = None
@@ -775,11 +885,16 @@ def main():
         hb.close()
 
     peaks, peak_src = _peaks()
-    z = 6 if wl["lattice"] != I.SQUARE2D else 4
+    z = {I.SQUARE2D: 4, I.CUBIC3D: 6, I.CHIMERA: 6, I.HYPERCUBIC4D: 8}[wl["lattice"]]
     ops_per_update = ALG_OPS[wl["disorder"]](z)
-    per_launch_ms = ms / max(args.steps, 1) / (world if False else 1)
-    achieved = updates_per_step * ops_per_update / (per_launch_ms * 1e-3) / 1e12     # Tops/s
-    peak = 152 * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12                   # issue limit
+    per_launch_ms = ms / max(args.steps, 1)
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sm * 128 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12                  # issue limit, Tops/s
+    # the whole step: the sweep's algorithmic ops plus the cluster moves' (from
+    # the device counters of the timed steps), over the fused kernel's time
+    icm_ops_step = icm_ops(N, Nb, z, n_icm, n * n_icm * S, stats[:, 0].sum() / args.steps,
+                           stats[:, 1].sum() / args.steps)
+    achieved = (updates_per_step * ops_per_update + icm_ops_step) / (per_launch_ms * 1e-3) / 1e12
     # executed thread-instructions per update (ncu) give the issue utilisation
     # beside the algorithmic fraction
     ipu = None if args.cluster else recorded_counter(args.workload, "instructions_per_update")
@@ -787,10 +902,14 @@ def main():
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak, "traffic": None if args.cluster else recorded_traffic(args.workload),
                 "kernel": "cluster_kernel" if args.cluster else "fused_kernel",
-                "ops_per_update": ops_per_update, "instructions_per_update": ipu, "issue_frac": issue_frac,
-                "peak_note": f"issue limit: 152 SMs x 128 thread-instr/clk x sm_max_mhz ({peak_src}); "
-                             "frac = algorithmic ops, issue_frac = executed instructions (ncu); "
-                             "traffic = DRAM bytes per launch"}
+                "ops_per_update": ops_per_update, "icm_ops_per_step": icm_ops_step,
+                "instructions_per_update": ipu, "issue_frac": issue_frac,
+                "peak_note": f"issue limit: {n_sm} SMs x 128 thread-instr/clk x sm_max_mhz ({peak_src}); "
+                             "frac = algorithmic ops (Metropolis per update + cluster moves from the device "
+                             "counters), issue_frac = executed instructions (ncu); traffic = DRAM bytes per launch"}
+    if not args.no_phases:
+        roofline.update(phase_fractions(b, stream, flush, S, n, updates_per_step, ops_per_update, N, Nb, z,
+                                        n_icm, peak))
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -812,10 +931,17 @@ def main():
                        "sweeps_per_step": S, "n_icm": n_icm, "l2": "flushed between steps (256 MB write)",
                        "threads": info["threads"], "ctas_per_sm": info["ctas_per_sm"], "grid": info["grid"],
                        "smem_bytes": info["smem_bytes"]},
-            "icm_moves_per_s": icm_moves_per_s,
+            "icm_moves_per_s": icm_moves_per_s, "icm_attempts_per_s": icm_attempts_per_s,
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "wall_s": t_wall,
         }
+        if world == 1 and args.workload == "3d_gauss_L8" and not args.no_serving:
+            # the metric's second half: instances thermalized/s and latency of
+            # the served form (workload 5), against the plain method one at a time
+            sv = serving_measurement(args)
+            out.update({k: sv[k] for k in ("instances_thermalized_per_s", "latency_p50_s", "latency_p99_s")})
+            sv.pop("clocks", None)
+            out["serving"] = sv
         print(json.dumps(out))
     b.close()
     ctx.close()

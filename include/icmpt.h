@@ -267,7 +267,21 @@ icm_status icm_read_observables(icm_batch *b, double *accE, int64_t *acc_n, int6
  * flips copy 1 at ICM temperatures, so the sign of q there is folded:
  * compare P(q) symmetrised.                                                */
 icm_status icm_read_overlaps(icm_batch *b, double *q_mean, double *q2_mean, double *ql_mean, int64_t *q_hist);
+/* Clear the accumulated observables and the cluster-move counters below. */
 icm_status icm_clear_observables(icm_batch *b);
+
+/* Counters of the cluster moves (the paper's step 2b) since the last clear,
+ * out [n_inst][2] uint64:
+ *   out[i][0] : moves, i.e. ICM temperatures at which a cluster was grown
+ *               and flipped (n > 0 q = -1 sites after step 2a; a pair with
+ *               n = 0 has no seed and no move);
+ *   out[i][1] : growth scans, the passes over the sites that grew the
+ *               clusters of all pairs (bit-parallel, all pairs of a sweep
+ *               at once), summed over sweeps.
+ * They give the cluster-move rate and the work of the growth.  Not part of
+ * checkpoints.  Host or device buffer (ICM_DEVICE_PTR); waits for the
+ * batch's work.                                                           */
+icm_status icm_read_icm_stats(icm_batch *b, uint64_t *out, uint32_t flags);
 
 /* Decisions of the last sweep of the last icm_run_sweeps (schedule.trace = 1):
  *   n_pre [n_inst][n_T] int32 : n before step 2a (-1: no ICM at k)

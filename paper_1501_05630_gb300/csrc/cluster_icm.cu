@@ -105,6 +105,7 @@ struct CS {
     uint64_t *swap_mask;
     double *accE;
     long long *acc64, *nmeas;
+    unsigned long long *icmst;
     uint32_t base;        // shared-window address of this CTA's dynamic shared memory
     uint32_t rank, K;
     int hs, nls;
@@ -142,6 +143,7 @@ __device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &
     S.accE = (double *)(smem + L.accE);
     S.acc64 = (long long *)(smem + L.acc64);
     S.nmeas = (long long *)(smem + L.nmeas);
+    S.icmst = (unsigned long long *)(smem + L.icmst);
     S.base = (uint32_t)__cvta_generic_to_shared(smem);
     S.rank = cl_rank();
     S.K = (uint32_t)L.K;
@@ -458,7 +460,13 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         if (__any_sync(kFull, grew) && lane == 0)
             for (uint32_t r = 0; r < S.K; ++r) cl_st(cl_map(S.base + L.flags + 4 * (round & 1), r), stamp);
         cl_sync();
-        if ((uint32_t)S.flags[round & 1] != stamp) break;
+        if ((uint32_t)S.flags[round & 1] != stamp) {
+            if (S.rank == 0 && tid == 0) {
+                S.icmst[0] += (unsigned)(__popc(act0) + __popc(act1));
+                S.icmst[1] += (unsigned)(round + 1) * kScansPerRound;   // scans of the own sites
+            }
+            break;
+        }
     }
 
     // (d) flip the own sites; copy-a energies of the moved pairs
@@ -713,7 +721,10 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
                 S.accE[k] = P.accE[(size_t)slot * nT + k];
                 for (int a = 0; a < 4; ++a) S.acc64[a * nT + k] = P.acc64[((size_t)a * P.n_inst + slot) * nT + k];
             }
-            if (tid == 0) S.nmeas[0] = P.n_meas[slot];
+            if (tid == 0) {
+                S.nmeas[0] = P.n_meas[slot];
+                S.icmst[0] = S.icmst[1] = 0ull;
+            }
         }
         // a diluted instance: its own neighbour table (absent bonds point at the
         // site itself) and degrees, and zero-energy proposals accepted with
@@ -773,6 +784,10 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
             if (tid == 0) {
                 P.n_meas[slot] = S.nmeas[0];
                 P.tsweep[slot] = t;
+                if (P.icm_stats) {
+                    P.icm_stats[2 * (size_t)slot] += S.icmst[0];
+                    P.icm_stats[2 * (size_t)slot + 1] += S.icmst[1];
+                }
             }
         }
         cl_sync();
@@ -867,6 +882,7 @@ ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwar
     L.accE = take(nT * 8);
     L.acc64 = take(4 * nT * 8);
     L.nmeas = take(8);
+    L.icmst = take(16);
     L.total = align_up16(o);
     return L;
 }

@@ -465,6 +465,7 @@ icm_status clear_observables(icm_batch *b)
     ICM_CUDA(ctx, cudaMemsetAsync(P.acc64, 0, 4 * nk * sizeof(long long), ctx->stream));
     ICM_CUDA(ctx, cudaMemsetAsync(P.hist, 0, nk * (P.N + 1) * sizeof(unsigned long long), ctx->stream));
     ICM_CUDA(ctx, cudaMemsetAsync(P.n_meas, 0, (size_t)b->n_inst * sizeof(long long), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.icm_stats, 0, 2 * (size_t)b->n_inst * sizeof(unsigned long long), ctx->stream));
     return ICM_OK;
 }
 
@@ -772,7 +773,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     double *d_beta, *d_accE;
     float *d_dbl;
     long long *d_acc64, *d_nmeas;
-    unsigned long long *d_hist;
+    unsigned long long *d_hist, *d_icmst;
     uint8_t *d_trsw;
     uint16_t *d_nbr_inst;
     uint8_t *d_zdeg_inst;
@@ -791,7 +792,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
         (st = dalloc(b, &d_beta, n_T)) || (st = dalloc(b, &d_dbl, n_T - 1)) || (st = dalloc(b, &d_thrs, thr_swap.size())) ||
         (st = dalloc(b, &d_off, n_T - 1)) || (st = dalloc(b, &d_len, n_T - 1)) || (st = dalloc(b, &d_accE, nk)) ||
         (st = dalloc(b, &d_acc64, 4 * nk)) || (st = dalloc(b, &d_hist, nk * (N + 1))) ||
-        (st = dalloc(b, &d_nmeas, n_inst)) || (st = dalloc(b, &d_trn, nk)) || (st = dalloc(b, &d_trf, nk)) ||
+        (st = dalloc(b, &d_nmeas, n_inst)) || (st = dalloc(b, &d_icmst, 2 * (size_t)n_inst)) || (st = dalloc(b, &d_trn, nk)) || (st = dalloc(b, &d_trf, nk)) ||
         (st = dalloc(b, &d_trs, nk)) || (st = dalloc(b, &d_trc, nk)) || (st = dalloc(b, &d_treb, nk)) ||
         (st = dalloc(b, &d_trea, nk)) || (st = dalloc(b, &d_trsw, (size_t)n_inst * 2 * (n_T - 1))) ||
         (st = dalloc(b, (uint8_t **)&b->raw_coup, (size_t)n_inst * g.Nb * (b->gauss ? 4 : 1))) ||
@@ -802,7 +803,7 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     P.nbr = d_nbr; P.pos2site = d_pos2site; P.zdeg = d_zdeg; P.Jb = d_Jb; P.Jd = d_Jd; P.spins = d_spins;
     P.Ef = d_Ef; P.Ei = d_Ei; P.tsweep = d_t; P.inst_id = d_id; P.thr_metro = d_thr; P.b2l = d_b2l;
     P.beta = d_beta; P.dbeta_l2e = d_dbl; P.thr_swap = d_thrs; P.swap_off = d_off; P.swap_len = d_len; P.accE = d_accE;
-    P.acc64 = d_acc64; P.hist = d_hist; P.n_meas = d_nmeas; P.tr_n_pre = d_trn; P.tr_flip2a = d_trf;
+    P.acc64 = d_acc64; P.hist = d_hist; P.n_meas = d_nmeas; P.icm_stats = d_icmst; P.tr_n_pre = d_trn; P.tr_flip2a = d_trf;
     P.tr_seed = d_trs; P.tr_csize = d_trc; P.tr_eb = d_treb; P.tr_ea = d_trea; P.tr_swap = d_trsw;
     P.nbr_inst = d_nbr_inst; P.zdeg_inst = d_zdeg_inst; P.nb_inst = d_nb_inst;
     b->h_nb.assign(n_inst, g.Nb);
@@ -1008,6 +1009,15 @@ icm_status icm_read_overlaps(icm_batch *b, double *q_mean, double *q2_mean, doub
     return ICM_OK;
 }
 
+icm_status icm_read_icm_stats(icm_batch *b, uint64_t *out, uint32_t flags)
+{
+    if (!b || !out) return ICM_ERR_ARG;
+    icm_status st = copy_out(b->ctx, out, b->kp.icm_stats, (size_t)b->n_inst * 16, flags);
+    if (st) return st;
+    ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));
+    return ICM_OK;
+}
+
 icm_status icm_clear_observables(icm_batch *b)
 {
     if (!b) return ICM_ERR_ARG;
@@ -1086,6 +1096,7 @@ static icm_status clear_slot_observables(icm_batch *b, int slot)
     ICM_CUDA(ctx, cudaMemsetAsync(P.hist + slot * nT * (P.N + 1), 0, nT * (P.N + 1) * sizeof(unsigned long long),
                                   ctx->stream));
     ICM_CUDA(ctx, cudaMemsetAsync(P.n_meas + slot, 0, sizeof(long long), ctx->stream));
+    ICM_CUDA(ctx, cudaMemsetAsync(P.icm_stats + 2 * (size_t)slot, 0, 2 * sizeof(unsigned long long), ctx->stream));
     return ICM_OK;
 }
 
@@ -1356,6 +1367,7 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
         {P.acc64, 4 * nk * 8, nullptr},
         {P.hist, nk * (P.N + 1) * 8, nullptr},
         {P.n_meas, (size_t)b->n_inst * 8, nullptr},
+        {P.icm_stats, (size_t)b->n_inst * 16, nullptr},
     };
     icm_status st = ICM_OK;
     for (auto &pc : pieces) {

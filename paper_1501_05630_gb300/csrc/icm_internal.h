@@ -46,6 +46,7 @@ struct SmemLayout {
     int accE;       // double [nT]
     int acc64;      // int64 [4][nT]  n, q2, pmin, d
     int nmeas;      // int64 [1]
+    int icmst;      // uint64 [2]      this instance's cluster moves (pairs with n > 0) and growth scans
     int total;
 };
 
@@ -94,6 +95,9 @@ struct KParams {
     long long *acc64;             // [4][n_inst][nT]: n, (N-2n)^2, min(n,N-n), d
     unsigned long long *hist;     // [n_inst][nT][N+1]
     long long *n_meas;            // [n_inst]
+    // ICM counters, accumulated over launches (cleared with the observables):
+    // [n_inst][2] = pairs moved (n > 0 after step 2a), growth scans (passes over the sites)
+    unsigned long long *icm_stats;
     // trace of the last sweep
     int32_t *tr_n_pre, *tr_flip2a, *tr_seed, *tr_csize;  // [n_inst][nT]
     float *tr_eb, *tr_ea;                                // [n_inst][nT]
@@ -141,6 +145,7 @@ struct ClusterLayout {
     int swap_x, swap_list, swap_n, swap_mask;   // as in SmemLayout
     int cnt_n, cnt_d;   // int32 [32]           this CTA's observable counts (read remotely)
     int accE, acc64, nmeas;                     // observables (rank 0)
+    int icmst;      // uint64 [2]               cluster moves and growth scans of this instance (rank 0)
     int total;
 };
 ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss);

@@ -106,6 +106,7 @@ struct Sm {
     double *accE;
     long long *acc64;
     long long *nmeas;
+    unsigned long long *icmst;
     int tie;         // this instance is diluted: a zero-energy proposal is accepted with probability 1/2
     int nb;          // bonds present in this instance
 };
@@ -139,6 +140,7 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     S.accE = (double *)(base + L.accE);
     S.acc64 = (long long *)(base + L.acc64);
     S.nmeas = (long long *)(base + L.nmeas);
+    S.icmst = (unsigned long long *)(base + L.icmst);
     return S;
 }
 
@@ -613,6 +615,10 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
 #ifdef ICM_PHASE_TIMERS
     if (tid == 0) atomicAdd(&g_icm_phase_cycles[11], (unsigned long long)rounds);
 #endif
+    if (tid == 0) {
+        S.icmst[0] += (unsigned)(__popc(act0) + __popc(act1));
+        S.icmst[1] += (unsigned)rounds;
+    }
     ICM_SUB(9);
     if (!(act0 | act1)) {
         __syncthreads();
@@ -839,7 +845,10 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
             S.accE[k] = P.accE[(size_t)slot * nT + k];
             for (int a = 0; a < 4; ++a) S.acc64[a * nT + k] = P.acc64[((size_t)a * P.n_inst + slot) * nT + k];
         }
-        if (tid == 0) S.nmeas[0] = P.n_meas[slot];
+        if (tid == 0) {
+            S.nmeas[0] = P.n_meas[slot];
+            S.icmst[0] = S.icmst[1] = 0ull;
+        }
         const uint32_t inst = P.inst_id[slot];
         const long long t_meas = P.t_meas_inst ? P.t_meas_inst[slot] : P.t_meas;
         uint32_t t = P.tsweep[slot];
@@ -902,6 +911,10 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
         if (tid == 0) {
             P.n_meas[slot] = S.nmeas[0];
             P.tsweep[slot] = t;
+            if (P.icm_stats) {
+                P.icm_stats[2 * (size_t)slot] += S.icmst[0];
+                P.icm_stats[2 * (size_t)slot + 1] += S.icmst[1];
+            }
         }
         __syncthreads();
         PHASE_MARK(5);
@@ -1144,6 +1157,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.accE = take(nT * 8, 16);
     L.acc64 = take(4 * nT * 8, 16);
     L.nmeas = take(8, 16);
+    L.icmst = take(16, 16);
     L.total = align_up(o, 16);
     return L;
 }

@@ -47,7 +47,7 @@ EXPORTS = [
     "icm_ctx_create", "icm_ctx_create_ex", "icm_ctx_memory", "icm_ctx_destroy", "icm_last_error", "icm_sync", "icm_query", "icm_lattice_size",
     "icm_batch_create",
     "icm_batch_destroy", "icm_batch_load", "icm_set_schedule", "icm_get_schedule", "icm_run_sweeps",
-    "icm_read_couplings", "icm_read_overlaps", "icm_read_cluster_masks", "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables",
+    "icm_read_couplings", "icm_read_overlaps", "icm_read_icm_stats", "icm_read_cluster_masks", "icm_read_spins", "icm_read_energies", "icm_read_sweeps", "icm_read_observables",
     "icm_clear_observables",
     "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
     "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
@@ -118,6 +118,7 @@ def load_library(path: str = LIB_PATH):
         L.icm_read_couplings.argtypes = [vp, vp, u32]
         L.icm_read_cluster_masks.argtypes = [vp, vp]
         L.icm_read_overlaps.argtypes = [vp, vp, vp, vp, vp]
+        L.icm_read_icm_stats.argtypes = [vp, vp, u32]
         L.icm_read_energies.argtypes = [vp, vp, u32]
         L.icm_read_sweeps.argtypes = [vp, vp, u32]
         L.icm_read_observables.argtypes = [vp] + [vp] * 7 + [u32]
@@ -483,6 +484,13 @@ class Batch:
         self.ctx.check(self._lib.icm_read_overlaps(self._h, q.ctypes.data, q2.ctypes.data, ql.ctypes.data,
                                                    None if h is None else h.ctypes.data))
         return q, q2, ql, h
+
+    def read_icm_stats(self) -> np.ndarray:
+        """[n_inst][2] uint64: cluster moves (pairs with n > 0) and growth
+        scans since the last clear (see icm_read_icm_stats)."""
+        out = np.empty((self.n_inst, 2), dtype=np.uint64)
+        self.ctx.check(self._lib.icm_read_icm_stats(self._h, out.ctypes.data, 0))
+        return out
 
     def read_cluster_masks(self) -> np.ndarray:
         """[n_inst][n_T][N] uint8: the clusters moved in the last traced sweep."""

@@ -62,6 +62,7 @@ class Result:
     acc_d: int
     n_meas: int
     slot: int = -1
+    admitted: float = 0.0       # when the request entered a slot (same clock as done)
 
     @property
     def latency(self) -> float:
@@ -129,7 +130,7 @@ class Server:
                   "thermalized" if out.thermalized else "not_thermalized")
         return Result(int(ticket), status, int(out.sweeps),
                       self._arrival.get(int(ticket), out.t_submit), out.t_done, out.e, out.q_l, out.delta,
-                      out.accE, int(out.acc_d), int(out.n_meas), int(out.slot))
+                      out.accE, int(out.acc_d), int(out.n_meas), int(out.slot), out.t_admit)
 
     def cancel(self, ticket: int):
         """Drop a queued request, or release a running one at its class's next collection."""

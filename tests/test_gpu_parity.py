@@ -60,11 +60,14 @@ def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, c
         setup(b)
     b.set_schedule(trace=1, **sched)
     refs = [_oracle(g, J[a], s0[a], T, T_icm, seed, ids[a], I.PM_J, **sched) for a in range(n_inst)]
+    b.clear_observables()
+    moves = np.zeros(n_inst, dtype=np.int64)            # the oracle's cluster moves (seeded pairs)
     done = 0
     while done < sweeps:
         step = min(check_every, sweeps - done)
         b.run(step)
         trs = [r.run(step, trace=True) for r in refs]
+        moves += [int((tr["seed_site"] >= 0).sum()) for tr in trs]
         done += step
         spins, E, tr = b.read_spins(), b.read_energies(), b.read_trace()
         cm = b.read_cluster_masks()
@@ -76,6 +79,10 @@ def _compare_sweeps(icm, kind, L, nT, T_lo, T_hi, T_icm, n_inst, sweeps, seed, c
                 assert np.array_equal(tr[key][a], trs[a][key]), (a, done, key, tr[key][a], trs[a][key])
             if nT > 1:
                 assert np.array_equal(tr["swap_acc"][a], trs[a]["swap_acc"]), (a, done, "swap")
+    if check_every == 1:
+        st = b.read_icm_stats()
+        assert np.array_equal(st[:, 0].astype(np.int64), moves), (st[:, 0], moves)   # cluster moves
+        assert np.all(st[:, 1] >= (st[:, 0] > 0))                                      # growth scans
     o = b.read_observables()
     for a, r in enumerate(refs):
         assert np.array_equal(o.accE[a], r.accE)
