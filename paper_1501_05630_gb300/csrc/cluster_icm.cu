@@ -211,7 +211,7 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.key, x, y);
                     uint32_t f8 = 0u;
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -258,7 +258,7 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.key, x, y);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;
@@ -365,7 +365,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         int seed_pos = -1;
         if (n > 0) {
             uint32_t x[4];
-            philox10((uint32_t)k, t, 0u, (1u << 24) | inst, P.seed_lo, P.seed_hi, x);
+            philox10k((uint32_t)k, t, 0u, (1u << 24) | inst, P.key, x);
             uint32_t rank = (uint32_t)(((uint64_t)x[0] * (uint32_t)n) >> 32);
             for (int c = 0; c < 2 && seed_pos < 0; ++c)
                 for (uint32_t r = 0; r < S.K; ++r) {
@@ -583,7 +583,7 @@ __device__ void cl_pt_pass(const KParams &P, const CS &S, uint32_t t, uint32_t i
     for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
         const int c = i / np, k = i % np;
         uint32_t x[4];
-        philox10((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.seed_lo, P.seed_hi, x);
+        philox10k((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.key, x);
         if constexpr (GAUSS) S.swap_x[c * 32 + k] = pt_word_gauss(x[0]);
         else S.swap_x[c * 32 + k] = pt_word_pmj(x[0], P.thr_swap + P.swap_off[k], P.swap_len[k], P.dbeta_l2e[k]);
     }

@@ -756,6 +756,10 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
     b->uniform_z = P.const_z;
     P.seed_lo = (uint32_t)(seed & 0xffffffffu);
     P.seed_hi = (uint32_t)(seed >> 32);
+    for (int i = 0; i < 10; ++i) {                 // Philox round keys (Weyl sequence of the seed)
+        P.key[2 * i] = P.seed_lo + (uint32_t)i * 0x9E3779B9u;
+        P.key[2 * i + 1] = P.seed_hi + (uint32_t)i * 0xBB67AE85u;
+    }
     {
         icm_status st0 = apply_threads(b, threads);
         if (st0) {

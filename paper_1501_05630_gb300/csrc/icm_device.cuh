@@ -34,43 +34,44 @@ __device__ __forceinline__ int icm_guard(int idx, int bound, int site)
 #endif
 
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): 10 rounds, multipliers
-// 0xD2511F53 / 0xCD9E8D57, Weyl key increments 0x9E3779B9 / 0xBB67AE85.
-__device__ __forceinline__ void philox10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                         uint32_t k1, uint32_t (&o)[4])
+// 0xD2511F53 / 0xCD9E8D57; the round keys are the Weyl sequence of the
+// 64-bit key (increments 0x9E3779B9 / 0xBB67AE85), taken here from a table
+// computed once per batch (key[2i], key[2i+1] = the key of round i, see
+// KParams::key).
+__device__ __forceinline__ void philox10k(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                          const uint32_t (&key)[20], uint32_t (&o)[4])
 {
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
         const uint64_t m0 = (uint64_t)c0 * 0xD2511F53ull;
         const uint64_t m1 = (uint64_t)c2 * 0xCD9E8D57ull;
-        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ k0;
-        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ k1;
+        const uint32_t n0 = (uint32_t)(m1 >> 32) ^ c1 ^ key[2 * i];
+        const uint32_t n2 = (uint32_t)(m0 >> 32) ^ c3 ^ key[2 * i + 1];
         c1 = (uint32_t)m1;
         c3 = (uint32_t)m0;
         c0 = n0;
         c2 = n2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
     o[0] = c0; o[1] = c1; o[2] = c2; o[3] = c3;
 }
 
 // Two Philox4x32-10 blocks with counters {c0, c1, c2, c3} and {c0, c1, c2+1, c3},
-// written as two independent chains so that the scheduler can interleave them.
-__device__ __forceinline__ void philox10x2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, uint32_t k0,
-                                           uint32_t k1, uint32_t (&o)[4], uint32_t (&p)[4])
+// written as two independent chains so that the scheduler can interleave them;
+// round keys from a table as in philox10k.
+__device__ __forceinline__ void philox10x2(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                           const uint32_t (&key)[20], uint32_t (&o)[4], uint32_t (&p)[4])
 {
     uint32_t a0 = c0, a1 = c1, a2 = c2, a3 = c3;
     uint32_t b0 = c0, b1 = c1, b2 = c2 + 1u, b3 = c3;
 #pragma unroll
     for (int i = 0; i < 10; ++i) {
+        const uint32_t k0 = key[2 * i], k1 = key[2 * i + 1];
         const uint64_t ma0 = (uint64_t)a0 * 0xD2511F53ull, ma1 = (uint64_t)a2 * 0xCD9E8D57ull;
         const uint64_t mb0 = (uint64_t)b0 * 0xD2511F53ull, mb1 = (uint64_t)b2 * 0xCD9E8D57ull;
         const uint32_t na0 = (uint32_t)(ma1 >> 32) ^ a1 ^ k0, na2 = (uint32_t)(ma0 >> 32) ^ a3 ^ k1;
         const uint32_t nb0 = (uint32_t)(mb1 >> 32) ^ b1 ^ k0, nb2 = (uint32_t)(mb0 >> 32) ^ b3 ^ k1;
         a1 = (uint32_t)ma1; a3 = (uint32_t)ma0; a0 = na0; a2 = na2;
         b1 = (uint32_t)mb1; b3 = (uint32_t)mb0; b0 = nb0; b2 = nb2;
-        k0 += 0x9E3779B9u;
-        k1 += 0xBB67AE85u;
     }
     o[0] = a0; o[1] = a1; o[2] = a2; o[3] = a3;
     p[0] = b0; p[1] = b1; p[2] = b2; p[3] = b3;
@@ -133,7 +134,7 @@ __device__ __forceinline__ void pt_warp(ET *E, int R, int np, const uint32_t *w,
     const uint32_t *wc = w + 32 * c;
     uint32_t acc = 0u;
     ET ek = E[c];
-#pragma unroll
+#pragma unroll 1
     for (int k = 0; k < 31; ++k) {
         if (k < np) {
             const ET ek1 = E[ICM_IDX(2 * k + 2 + c, R, 11)];

@@ -32,7 +32,7 @@ struct SmemLayout {
     int Epart;      // float or int32 [nwarps][max(R, 32)]
     int rtab;       // uint32 [R][thr_stride(Z)] thresholds (+-J) or float [R] -2 beta log2(e) (Gaussian)
     int icm_mask;   // uint32 [n_icm][NW] overlap masks per ICM pair
-    int icm_C;      // uint2 [N]         cluster bits of both words (bit 2k: site in pair k's cluster)
+    int icm_C;      // uint32 [N]        cluster bits of every pair (bit 2k: pair k, bit 2k + 1: pair 16 + k)
     int swap_x;     // uint32 [2][32]
     int swap_list;  // int32 [2][32]   per run: (source bit << 8) | destination bit
     int swap_n;     // int32 [2]       runs per copy
@@ -90,6 +90,10 @@ struct KParams {
     const long long *t_meas_inst;  // [n_inst] per-instance measurement start, or null (t_meas for all)
     const uint8_t *active;         // [n_inst] 0 = free slot (skipped), or null (all active)
     uint32_t seed_lo, seed_hi;
+    // Philox4x32-10 key schedule of the seed: key[2i] = seed_lo + i 0x9E3779B9,
+    // key[2i+1] = seed_hi + i 0xBB67AE85 (mod 2^32), the round keys i = 0..9;
+    // read from the kernel parameters, so no round recomputes them
+    uint32_t key[20];
     // observables
     double *accE;                 // [n_inst][nT]
     long long *acc64;             // [4][n_inst][nT]: n, (N-2n)^2, min(n,N-n), d

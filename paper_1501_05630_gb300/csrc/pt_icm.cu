@@ -144,6 +144,15 @@ __device__ __forceinline__ Sm make_sm(unsigned char *base, const SmemLayout &L)
     return S;
 }
 
+// A 32-bit word of shared memory by its shared-window address.  Volatile: the
+// cluster growth reads words that other threads rewrite during the same round.
+__device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+    return v;
+}
+
 // Neighbour positions of position p (padding entries repeat p), read as
 // 32-bit pairs from the [N][Z] uint16 table (Z even, so rows are 4-byte aligned).
 template <int Z>
@@ -209,7 +218,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.key, x, y);
                     uint32_t f8 = 0u;                           // this group's accepted bits
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -218,17 +227,20 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 #pragma unroll
                         for (int d = 0; d < Z; ++d)
                             if ((nw[d] >> b) & 1u) h -= J2[d];
-                        // sh = s_i h_i, Delta E = 2 sh; accept iff sh <= 0 or x < 2^32 exp(-2 beta sh)
+                        // sh = s_i h_i, Delta E = 2 sh; accept iff x < 2^32 exp(-2 beta sh),
+                        // compared as rz(x) < 2^(32 + b2l sh) in fp32 (b2l = -2 beta log2 e):
+                        // for sh <= 0 the right side is >= 2^32 > rz(x), so Delta E <= 0 is
+                        // always accepted
                         const float sh = ((sw >> b) & 1u) ? -h : h;
                         const uint32_t xr = i < 4 ? x[i] : y[i - 4];
-                        const uint32_t thr = __float2uint_rz(ex2_approx(fmaf(b2l[b], sh, 32.f)));
+                        const float lim = ex2_approx(fmaf(b2l[b], sh, 32.f));
                         bool a;
                         if constexpr (DIL) {
                             // diluted instance: Delta E = 0 (a site without bonds) is
                             // accepted with probability 1/2
-                            a = (sh < 0.f) || (sh == 0.f ? (!S.tie || xr < 0x80000000u) : (xr < thr));
+                            a = (sh < 0.f) || (sh == 0.f ? (!S.tie || xr < 0x80000000u) : (__uint2float_rz(xr) < lim));
                         } else {
-                            a = (sh <= 0.f) || (xr < thr);
+                            a = __uint2float_rz(xr) < lim;
                         }
                         f8 |= (uint32_t)a << i;
                         acc[b] -= sh;                           // e = -s'h: -sh, or +sh after a flip
@@ -266,7 +278,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.seed_lo, P.seed_hi, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.key, x, y);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;
@@ -407,11 +419,12 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
 //  (a) overlap masks of all pairs by a warp bit-matrix transpose (bit 2k of s ^ (s >> 1));
 //  (b) one thread per pair: n, the step-2a decision, the seed by rank;
 //  (c) copy-1 reversal of the flagged pairs, then the clusters of all pairs
-//      at once: C_p (bit 2k = site p in pair k's cluster) grows by
+//      at once: C_p (bit 2k = site p in pair k's cluster, bit 2k + 1 the same
+//      for pair 16 + k) grows by
 //      C_p |= domain_p & OR(C of the neighbours) in rounds until a round
 //      changes nothing -- the fixed point is each seed's connected component
 //      of {q = -1};
-//  (d) flip in both copies (bits 2k, 2k+1 of C_p | C_p << 1), then E_a from
+//  (d) flip in both copies (bits 2k, 2k + 1 of the spin word of the pair), then E_a from
 //      the spins and E_b = (E_a + E_b)_before - E_a (the move is isoenergetic).
 //      A traced sweep also recomputes E_b from the spins and records
 //      E_a + E_b of the two recomputed energies, so that the trace tests the
@@ -443,7 +456,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         const int k = (lane >> 1) + 16 * (lane & 1);
         if (k < nicm) S.mask[ICM_IDX(k * NW + m, nicm * NW, 8)] = col;
     }
-    for (int i = tid; i < 2 * N; i += nth) S.C[i] = 0u;
+    for (int i = tid; i < N; i += nth) S.C[i] = 0u;
     if (tid < 2) S.flipw[tid] = 0u;
     __syncthreads();
 
@@ -466,7 +479,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         int seed = -1;
         if (n > 0) {
             uint32_t x[4];
-            philox10((uint32_t)k, t, 0u, (1u << 24) | inst, P.seed_lo, P.seed_hi, x);
+            philox10k((uint32_t)k, t, 0u, (1u << 24) | inst, P.key, x);
             uint32_t rank = (uint32_t)(((uint64_t)x[0] * (uint32_t)n) >> 32);
             for (int m = 0; m < NW; ++m) {
                 const uint32_t w = Mk[m];
@@ -477,7 +490,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                 }
                 rank -= c;
             }
-            atomicOr(&S.C[ICM_IDX(2 * seed + (k >> 4), 2 * N, 9)], 1u << (2 * (k & 15)));
+            atomicOr(&S.C[ICM_IDX(seed, N, 9)], 1u << (2 * (k & 15) + (k >> 4)));
         }
         S.icm_seed[k] = seed;
         esum[k] = E[2 * k] + E[2 * k + 1];
@@ -494,34 +507,48 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     __syncthreads();
     ICM_SUB(8);
 
-    // (c) which pairs move, then copy-1 reversal and cluster growth
+    // (c) which pairs move, then copy-1 reversal and cluster growth.  One
+    // cluster word per site holds every pair: bit 2j = pair j, bit 2j + 1 =
+    // pair 16 + j (the bit of pair j's copy a in the first spin word, and the
+    // one below pair 16 + j's copy a in the second), so that the domain word
+    // is q of the first word | q of the second word << 1.
     uint32_t act0 = 0u, act1 = 0u;
     for (int k = 0; k < nicm; ++k)
         if (S.icm_seed[k] >= 0) {
             if (k < 16) act0 |= 1u << (2 * k);
             else act1 |= 1u << (2 * (k - 16));
         }
+    const uint32_t actc = act0 | (act1 << 1);
     const uint32_t f0 = S.flipw[0], f1 = S.flipw[1];
-    // cluster words of both replica words of a site side by side: one 64-bit
-    // load per neighbour serves the pairs of both words
-    uint2 *C2 = (uint2 *)S.C;
+    uint32_t *C = S.C;
     int rounds = 0;
     if (N <= 4 * nth) {
         // each thread owns sites tid + j nth (j < 4) and keeps, across rounds,
         // their neighbour positions, their domain words (the q = -1 bits of
         // the moving pairs, fixed during the growth) and their own cluster
         // words (written only by this thread) in registers
-        uint32_t qn[4][Z / 2];                 // neighbour positions, two per register
-        uint32_t dm0[4], dm1[4], cw0[4], cw1[4];
+        // shared-memory layout: the neighbours' cluster words by their
+        // shared-window addresses (one load each); wide layout: by position
+        uint32_t qa[4][WIDE ? Z / 2 : Z];
+        uint32_t dm[4], cw[4];
         uint32_t todo = 0u;                    // bit j: site j not yet absorbed
+        [[maybe_unused]] const uint32_t cbase = WIDE ? 0u : (uint32_t)__cvta_generic_to_shared(C);
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int p = tid + j * nth;
             const bool ok = p < N;
             const uint32_t *row = (const uint32_t *)(S.nbr + (ok ? p : 0) * Z);
 #pragma unroll
-            for (int i = 0; i < Z / 2; ++i) qn[j][i] = row[i];
-            dm0[j] = dm1[j] = cw0[j] = cw1[j] = 0u;
+            for (int i = 0; i < Z / 2; ++i) {
+                const uint32_t v = row[i];
+                if constexpr (WIDE) {
+                    qa[j][i] = v;
+                } else {
+                    qa[j][2 * i] = cbase + 4u * ICM_IDX(v & 0xffffu, N, 10);
+                    qa[j][2 * i + 1] = cbase + 4u * ICM_IDX(v >> 16, N, 10);
+                }
+            }
+            dm[j] = cw[j] = 0u;
             if (ok) {
                 const uint32_t w0 = S.s[p] ^ f0;             // step 2a
                 S.s[p] = w0;
@@ -530,46 +557,45 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                     w1 = S.s[N + p] ^ f1;
                     S.s[N + p] = w1;
                 }
-                const uint2 c = C2[p];
-                dm0[j] = (w0 ^ (w0 >> 1)) & act0;
-                dm1[j] = (w1 ^ (w1 >> 1)) & act1;
-                cw0[j] = c.x;
-                cw1[j] = c.y;
-                if (dm0[j] != c.x || dm1[j] != c.y) todo |= 1u << j;
+                dm[j] = (((w0 ^ (w0 >> 1)) & 0x55555555u) | (((w1 ^ (w1 >> 1)) & 0x55555555u) << 1)) & actc;
+                cw[j] = C[p];
+                if (dm[j] != cw[j]) todo |= 1u << j;
             }
         }
-        if (act0 | act1) {
+        if (actc) {
             int grew;
             do {
                 grew = 0;
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (!((todo >> j) & 1u)) continue;
-                    uint32_t nb0 = 0u, nb1 = 0u;
+                    uint32_t nb = 0u;
+                    if constexpr (WIDE) {
 #pragma unroll
-                    for (int i = 0; i < Z / 2; ++i) {
-                        const uint2 a = C2[ICM_IDX(qn[j][i] & 0xffffu, N, 10)], b = C2[ICM_IDX(qn[j][i] >> 16, N, 10)];
-                        nb0 |= a.x | b.x;
-                        nb1 |= a.y | b.y;
+                        for (int i = 0; i < Z / 2; ++i)
+                            nb |= C[ICM_IDX(qa[j][i] & 0xffffu, N, 10)] | C[ICM_IDX(qa[j][i] >> 16, N, 10)];
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < Z; ++i) nb |= lds_u32(qa[j][i]);
                     }
-                    const uint32_t n0 = cw0[j] | (dm0[j] & nb0), n1 = cw1[j] | (dm1[j] & nb1);
-                    if (n0 != cw0[j] || n1 != cw1[j]) {
-                        C2[tid + j * nth] = make_uint2(n0, n1);
-                        cw0[j] = n0;
-                        cw1[j] = n1;
+                    const uint32_t nw = cw[j] | (dm[j] & nb);
+                    if (nw != cw[j]) {
+                        C[tid + j * nth] = nw;
+                        cw[j] = nw;
                         grew = 1;
-                        if (n0 == dm0[j] && n1 == dm1[j]) todo &= ~(1u << j);
+                        if (nw == dm[j]) todo &= ~(1u << j);
                     }
                 }
                 ++rounds;
             } while (__syncthreads_or(grew));
-            // (d) flip the owned sites
+            // (d) flip the owned sites in both copies of every moving pair
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
                 const int p = tid + j * nth;
-                if (p < N) {
-                    if (cw0[j]) S.s[p] ^= cw0[j] | (cw0[j] << 1);
-                    if (cw1[j]) S.s[N + p] ^= cw1[j] | (cw1[j] << 1);
+                if (p < N && cw[j]) {
+                    const uint32_t e0 = cw[j] & 0x55555555u, e1 = (cw[j] >> 1) & 0x55555555u;
+                    S.s[p] ^= e0 | (e0 << 1);
+                    if (G > 1) S.s[N + p] ^= e1 | (e1 << 1);
                 }
             }
         }
@@ -579,36 +605,35 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             if (G > 1) S.s[N + p] ^= f1;
         }
         __syncthreads();
-        if (act0 | act1) {
+        if (actc) {
             int grew;
             do {
                 grew = 0;
                 for (int p = tid; p < N; p += nth) {
                     const uint32_t w0 = S.s[p], w1 = G > 1 ? S.s[N + p] : 0u;
-                    const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
-                    const uint2 c = C2[p];
-                    if (d0 == c.x && d1 == c.y) continue;
+                    const uint32_t d = (((w0 ^ (w0 >> 1)) & 0x55555555u) | (((w1 ^ (w1 >> 1)) & 0x55555555u) << 1)) & actc;
+                    const uint32_t c = C[p];
+                    if (d == c) continue;
                     int q[Z];
                     load_nbrs<Z>(S.nbr, p, q);
-                    uint32_t nb0 = 0u, nb1 = 0u;
+                    uint32_t nb = 0u;
 #pragma unroll
-                    for (int d = 0; d < Z; ++d) {
-                        const uint2 a = C2[ICM_IDX(q[d], N, 10)];
-                        nb0 |= a.x;
-                        nb1 |= a.y;
-                    }
-                    const uint32_t n0 = c.x | (d0 & nb0), n1 = c.y | (d1 & nb1);
-                    if (n0 != c.x || n1 != c.y) {
-                        C2[p] = make_uint2(n0, n1);
+                    for (int dd = 0; dd < Z; ++dd) nb |= C[ICM_IDX(q[dd], N, 10)];
+                    const uint32_t nw = c | (d & nb);
+                    if (nw != c) {
+                        C[p] = nw;
                         grew = 1;
                     }
                 }
                 ++rounds;
             } while (__syncthreads_or(grew));
             for (int p = tid; p < N; p += nth) {
-                const uint2 c = C2[p];
-                if (c.x) S.s[p] ^= c.x | (c.x << 1);
-                if (c.y) S.s[N + p] ^= c.y | (c.y << 1);
+                const uint32_t c = C[p];
+                if (c) {
+                    const uint32_t e0 = c & 0x55555555u, e1 = (c >> 1) & 0x55555555u;
+                    S.s[p] ^= e0 | (e0 << 1);
+                    if (G > 1) S.s[N + p] ^= e1 | (e1 << 1);
+                }
             }
         }
     }
@@ -616,20 +641,27 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     if (tid == 0) atomicAdd(&g_icm_phase_cycles[11], (unsigned long long)rounds);
 #endif
     if (tid == 0) {
-        S.icmst[0] += (unsigned)(__popc(act0) + __popc(act1));
+        S.icmst[0] += (unsigned)__popc(actc);
         S.icmst[1] += (unsigned)rounds;
     }
     ICM_SUB(9);
-    if (!(act0 | act1)) {
+    if (!actc) {
         __syncthreads();
         return;
     }
     if (trace) {
-        // cluster sizes: counted once per cluster site; the cluster words themselves
-        for (int i = tid; i < 2 * N; i += nth) {
-            const uint32_t c = S.C[i];   // word i & 1 of site i >> 1
-            for (uint32_t b = c; b; b &= b - 1u) atomicAdd(&S.cnt_d[16 * (i & 1) + ((__ffs(b) - 1) >> 1)], 1);
-            if (P.tr_cmask) P.tr_cmask[(size_t)slot * 2 * N + i] = c;
+        // cluster sizes: counted once per cluster site; the cluster words as
+        // [N][2] words, bit 2(k & 15) of word k >> 4 = site in pair k's cluster
+        for (int p = tid; p < N; p += nth) {
+            const uint32_t c = S.C[p];
+            for (uint32_t b = c; b; b &= b - 1u) {
+                const int bit = __ffs(b) - 1;
+                atomicAdd(&S.cnt_d[(bit >> 1) + 16 * (bit & 1)], 1);
+            }
+            if (P.tr_cmask) {
+                P.tr_cmask[(size_t)slot * 2 * N + 2 * p] = c & 0x55555555u;
+                P.tr_cmask[(size_t)slot * 2 * N + 2 * p + 1] = (c >> 1) & 0x55555555u;
+            }
         }
     }
     __syncthreads();
@@ -673,7 +705,7 @@ __device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst
     for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
         const int c = i / np, k = i % np;
         uint32_t x[4];
-        philox10((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.seed_lo, P.seed_hi, x);
+        philox10k((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.key, x);
         if constexpr (GAUSS) S.swap_x[c * 32 + k] = pt_word_gauss(x[0]);
         else S.swap_x[c * 32 + k] = pt_word_pmj(x[0], P.thr_swap + S.sw_off[k], S.sw_len[k], P.dbeta_l2e[k]);
     }
@@ -1143,7 +1175,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
     L.Epart = take(nwarps * (R > 32 ? R : 32) * 4, 16);
     L.rtab = take(gauss ? G * 32 * 4 : G * 32 * thr_stride(Z) * 4, 16);   // every bit of the G words
     L.icm_mask = take(in_smem * n_icm * NW * 4, 16);
-    L.icm_C = take(in_smem * 2 * N * 4, 16);
+    L.icm_C = take(in_smem * N * 4, 16);
     L.swap_x = take(2 * 32 * 4, 16);
     L.swap_list = take(2 * 32 * 4, 16);
     L.swap_n = take(2 * 4, 16);

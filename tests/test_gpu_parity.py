@@ -170,6 +170,48 @@ def test_pmj_chimera_C8_full_batch_sampled(icm):
         assert np.array_equal(e, E[a].astype(np.int64))
 
 
+def test_pmj_chimera_C8_planned_scale(icm):
+    """The chimera C_8 workload at its planned parity scale: 10^4 instances,
+    30 temperatures, in the launch shape of the bench; 64 instances sampled
+    across the batch are bit-exact with the oracle (spins, integer energies,
+    P(q) histograms, accumulated link disagreements) after 2^12 sweeps, and 4
+    of them after the full 2^16 sweeps.  The oracle runs on the host cores
+    while the GPU runs."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    icmpt, ctx = icm
+    seed = 0x1501056300000003
+    T = I.ladder(0.2, 3.0, 30)
+    n = 10000
+    g = O.Geometry(O.CHIMERA, 8)
+    J = I.couplings(g.Nb, I.PM_J, seed, range(n))
+    s0 = I.initial_spins(g.N, 60, seed, range(n))
+    sample = np.linspace(0, n - 1, 64).astype(int)
+    full = sample[[0, 21, 42, 63]]
+    refs = {a: _oracle(g, J[a], s0[a], T, 1.5, seed, a, I.PM_J) for a in sample}
+    b = icmpt.Batch(ctx, O.CHIMERA, 8, I.PM_J, J, T, 1.5, seed, spins=s0)
+    with ThreadPoolExecutor(os.cpu_count() or 1) as ex:
+        fut = {a: ex.submit(refs[a].run, 1 << 12) for a in sample}
+        b.run(1 << 12)
+        spins, E, o = b.read_spins(), b.read_energies(), b.read_observables()
+        for a in sample:
+            fut[a].result()
+            r = refs[a]
+            assert np.array_equal(spins[a], r.s), a
+            assert np.array_equal(E[a], r.E), a
+            assert np.array_equal(o.hist[a], r.hist) and np.array_equal(o.acc_d[a], r.acc_d), a
+        del spins, o
+        fut = {a: ex.submit(refs[a].run, (1 << 16) - (1 << 12)) for a in full}
+        b.run((1 << 16) - (1 << 12))
+        spins, E = b.read_spins(), b.read_energies()
+        for a in full:
+            fut[a].result()
+            assert np.array_equal(spins[a], refs[a].s), a
+            assert np.array_equal(E[a], refs[a].E), a
+    assert np.all(b.read_sweeps() == 1 << 16)
+    b.close()
+
+
 def test_mix_invariance(icm):
     """An instance gives the same result alone and inside a larger batch."""
     icmpt, ctx = icm
