@@ -430,11 +430,14 @@ def dataclasses_replace(r):
 MIXED = dict(sizes=(4, 6, 8, 10, 12), counts=(4096, 2048, 1024, 512, 256), T=(0.2, 2.0, 24), T_icm=1.0,
              seed=0x1501056300000004,
              desc="3D EA Gaussian, L in {4,6,8,10,12} x {4096,2048,1024,512,256} instances, 24 T geometric "
-                  "[0.2,2.0], ICM T<=1.0, one CUDA graph per step (one kernel per size on forked streams), "
-                  "CTA width autotuned per size")
+                  "[0.2,2.0], ICM T<=1.0, one seed (instance ids distinct across sizes)")
 
 
 def run_mixed(args):
+    """Workload 4: uneven sizes in one captured launch.  shared (default): the
+    instances of all sizes share one persistent kernel (icm_group_create_shared),
+    threads per instance tuned by timing (icmpt.tune_shared_widths); graph: one
+    kernel per size on forked streams, CTA width autotuned per size."""
     import torch
     from paper_1501_05630_gb300 import build, icmpt
     torch.cuda.set_device(0)
@@ -443,18 +446,31 @@ def run_mixed(args):
     ctx = icmpt.Context(0, stream.cuda_stream)
     T = I.ladder(*MIXED["T"])
     batches, updates, tuned = [], 0, {}
+    first = 0
     for L, n in zip(MIXED["sizes"], MIXED["counts"]):
         N, Nb = icmpt.lattice_size(I.CUBIC3D, L)
-        ids = np.arange(n, dtype=np.uint32)
-        J = torch.from_numpy(I.couplings(Nb, I.GAUSS, MIXED["seed"] + L, ids)).cuda()
-        s0 = torch.from_numpy(I.initial_spins(N, 2 * len(T), MIXED["seed"] + L, ids)).cuda()
-        b = icmpt.Batch(ctx, I.CUBIC3D, L, I.GAUSS, J, T, MIXED["T_icm"], MIXED["seed"] + L, spins=s0)
-        th, ms = b.autotune(sweeps=8)
-        tuned[f"L{L}"] = {"threads": th, "ctas_per_sm": b.info()["ctas_per_sm"]}
+        ids = np.arange(first, first + n, dtype=np.uint32)
+        first += n
+        J = torch.from_numpy(I.couplings(Nb, I.GAUSS, MIXED["seed"], ids)).cuda()
+        s0 = torch.from_numpy(I.initial_spins(N, 2 * len(T), MIXED["seed"], ids)).cuda()
+        b = icmpt.Batch(ctx, I.CUBIC3D, L, I.GAUSS, J, T, MIXED["T_icm"], MIXED["seed"], spins=s0, instance_ids=ids)
+        if args.mixed_mode == "graph":
+            th, ms = b.autotune(sweeps=8)
+            tuned[f"L{L}"] = {"threads": th, "ctas_per_sm": b.info()["ctas_per_sm"]}
         batches.append(b)
         updates += n * 2 * len(T) * N
     S = args.sweeps_per_step
-    g = icmpt.Group(ctx, batches, S)
+    if args.mixed_mode == "shared":
+        widths, table = icmpt.tune_shared_widths(ctx, batches, sweeps=8)
+        g = icmpt.Group(ctx, batches, S, shared=True, team_threads=widths)
+        info = g.info()
+        for L, w, k in zip(MIXED["sizes"], info["team_threads"], info["tile"]):
+            tuned[f"L{L}"] = {"threads_per_instance": w, "instances_per_tile": k,
+                              "tried_ms": {str(x): round(y, 3) for x, y in table[MIXED["sizes"].index(L)].items()}}
+        tuned["kernel"] = {"grid": info["grid"], "smem_bytes": info["smem_bytes"], "tiles": info["n_items"],
+                           "threads": 896}
+    else:
+        g = icmpt.Group(ctx, batches, S)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     for _ in range(args.warmup):
         g.run(1)
@@ -472,13 +488,18 @@ def run_mixed(args):
             times.append(e0.elapsed_time(e1))
     ms = float(np.sum(times))
     value = updates * S * args.steps / (ms * 1e6)
+    desc = MIXED["desc"] + (", all sizes in one persistent kernel launch (CUDA graph), threads per instance tuned"
+                            if args.mixed_mode == "shared" else
+                            ", one CUDA graph per step (one kernel per size on forked streams), CTA width "
+                            "autotuned per size")
     print(json.dumps({
         "metric": "spin_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3d_gauss_mixed", "desc": MIXED["desc"], "sweeps_per_step": S, "tuned": tuned,
-                   "l2": "flushed between steps (256 MB write)"},
-        "gpu_launches": args.steps, "clocks": clk.summary()}))
+        "config": {"workload": "3d_gauss_mixed", "mode": args.mixed_mode, "desc": desc, "sweeps_per_step": S,
+                   "tuned": tuned, "l2": "flushed between steps (256 MB write)"},
+        "gpu_launches": args.steps if args.mixed_mode == "shared" else args.steps * len(batches),
+        "clocks": clk.summary()}))
     g.close()
 
 
@@ -532,6 +553,41 @@ FIG3 = [
     dict(name="chimera", lattice=I.CHIMERA, Ls=(4, 6, 8), T=(0.2120, 1.6325, 30), n_c=19),
     dict(name="3D", lattice=I.CUBIC3D, Ls=(4, 6, 8), T=(0.4200, 1.8000, 26), n_c=13),
 ]
+
+
+def run_icm_frequency(args):
+    """The frequency of the cluster moves judged on time to the criterion
+    (experiments.icm_frequency) for the Table I systems of the thermalization
+    workload: cluster moves every 1, 2, 4 or 8 sweeps."""
+    import torch
+    from paper_1501_05630_gb300 import build, icmpt
+    from paper_1501_05630_gb300.experiments import icm_frequency
+    torch.cuda.set_device(0)
+    build.build()
+    ctx = icmpt.Context(0)
+    out = {"metric": "icm_frequency_time_to_criterion", "unit": "ms to the criterion", "higher_is_better": False,
+           "n_gpus": 1, "data": "synthetic",
+           "config": {"workload": "icm_frequency", "instances": args.instances, "log2_sweeps": [4, args.log2_max],
+                      "candidates": [1, 2, 4, 8], "criterion": "|Delta| of Eq. 2 within 2 s.e. from a window on"},
+           "systems": {}}
+    t0 = time.perf_counter()
+    for sysd in THERMO:
+        T = I.ladder(*sysd["T"])
+        T_icm = float(T[sysd["n_c"] - 1]) + 1e-9
+        N, Nb = icmpt.lattice_size(sysd["lattice"], sysd["L"])
+        seed = 0x1501056300000006 + sysd["L"]
+        J = I.couplings(Nb, I.GAUSS, seed, range(args.instances))
+        s0 = I.initial_spins(N, 2 * len(T), seed, range(args.instances))
+        best, rows = icm_frequency(ctx, sysd["lattice"], sysd["L"], I.GAUSS, J, s0, T, T_icm, seed,
+                                   candidates=(1, 2, 4, 8), log2_max=args.log2_max)
+        out["systems"][sysd["name"]] = {"best_icm_every": best,
+                                       "rows": [dict(icm_every=r.icm_every, t_therm=r.t_therm,
+                                                     ms_per_sweep=round(r.ms_per_sweep, 5),
+                                                     cost_ms=None if r.cost_ms is None else round(r.cost_ms, 2))
+                                                for r in rows]}
+    out["wall_s"] = time.perf_counter() - t0
+    out["value"] = None
+    print(json.dumps(out))
 
 
 def run_fig3(args):
@@ -724,7 +780,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="3d_gauss_L8", choices=sorted(WORKLOADS) + ["serving", "3d_gauss_mixed", "percolation", "thermalization",
-                                                                   "annealing", "fig1", "fig3"])
+                                                                   "annealing", "fig1", "fig3", "icm_frequency"])
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--rate", type=float, default=200.0)
     ap.add_argument("--quantum", type=int, default=64)
@@ -736,6 +792,8 @@ def main():
                     help="serving: start one-at-a-time requests while this many seconds last")
     ap.add_argument("--no-serving", action="store_true", help="default workload: leave out the serving leg")
     ap.add_argument("--no-phases", action="store_true", help="leave out the sweep-only / ICM-only launches")
+    ap.add_argument("--mixed-mode", default="shared", choices=["shared", "graph"],
+                    help="3d_gauss_mixed: one shared persistent kernel, or one kernel per size in a graph")
     ap.add_argument("--masks", type=int, default=200000)
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--log2-max", type=int, default=17)
@@ -756,6 +814,10 @@ def main():
     if args.workload == "thermalization":
         if int(os.environ.get("RANK", "0")) == 0:
             run_thermalization(args)
+        return
+    if args.workload == "icm_frequency":
+        if int(os.environ.get("RANK", "0")) == 0:
+            run_icm_frequency(args)
         return
     if args.workload == "fig3":
         if int(os.environ.get("RANK", "0")) == 0:

@@ -492,6 +492,34 @@ icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, 
 icm_status icm_group_run(icm_group *g, uint32_t n_launches);
 icm_status icm_group_destroy(icm_group *g);
 
+/* The shared form of a group: the instances of every batch -- uneven sizes
+ * of one disorder kind and one lattice degree, e.g. 3D L = 4..12 -- share
+ * one persistent kernel, the fused simulation step of icm_run_sweeps (the
+ * paper's "Isoenergetic cluster algorithm", steps 1, 2a, 2b, 3, and the
+ * observables), captured as one launch in the group's graph.  One CTA of
+ * 896 threads per SM takes the next tile of instances whenever it is free,
+ * largest tiles first: a tile of batch c is up to 896 / team_threads[c] instances side by side,
+ * each run by its own team of team_threads[c] threads (threads per
+ * instance, a divisor of 896 that is a multiple of 32) with its own shared
+ * memory and barrier, as many as the SM's shared memory holds.
+ *   team_threads : [n] or NULL; an entry <= 0 (or NULL) picks the width that
+ *                  keeps the most threads of the CTA busy (the narrower on a
+ *                  tie).
+ * Every batch must have the same disorder kind, lattice degree and seed
+ * (instance ids tell the instances apart), no dilution and no cluster
+ * layout; at most 8 batches (ICM_ERR_UNSUPPORTED otherwise).  Arithmetic and
+ * random keys are those of icm_run_sweeps, so a +-J instance follows the same
+ * chain either way.  Each batch's schedule and slot flags are taken at
+ * creation.  The tile list is device memory of the context (its budget).  */
+icm_status icm_group_create_shared(icm_ctx *ctx, icm_batch *const *batches, int32_t n, uint32_t sweeps_per_launch,
+                                   const int32_t *team_threads, icm_group **out);
+/* The launch shape of a group, per batch: threads per instance and
+ * instances per tile (the batch's CTA width and 1 for a graph of separate
+ * launches); grid, dynamic shared memory per CTA and tiles of the shared
+ * kernel (0 for separate launches).  Any pointer may be NULL.             */
+icm_status icm_group_info(const icm_group *g, int32_t *team_threads, int32_t *tile, int32_t *grid, int32_t *smem,
+                          int32_t *n_items);
+
 /* ---------------------------------------------------------------- checkpoint / resume
  * The state of a batch -- spins, energies, sweep counters, instance ids,
  * observables, slot flags, ladder and schedule -- as one versioned blob.

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <memory>
 #include <set>
 #include <string>
 #include <vector>
@@ -1449,6 +1450,12 @@ struct icm_group {
     cudaGraphExec_t exec = nullptr;
     uint32_t sweeps = 0;
     int64_t launches = 0;
+    // shared form: one launch of the team kernel over every batch's instances
+    bool shared = false;
+    void *d_items = nullptr;               // icm::TeamItem [n_items] (device)
+    size_t items_bytes = 0;
+    std::vector<int> team_threads, tile;   // per batch: threads per instance, instances per tile
+    int grid = 0, smem = 0, n_items = 0;
 };
 
 static void destroy_group(icm_group *g)
@@ -1458,7 +1465,30 @@ static void destroy_group(icm_group *g)
     if (g->graph) cudaGraphDestroy(g->graph);
     for (auto e : g->events) cudaEventDestroy(e);
     for (auto s : g->streams) cudaStreamDestroy(s);
+    if (g->d_items) ctx_free(g->ctx, g->d_items, g->items_bytes);
     delete g;
+}
+
+// Instances per tile of a batch in the shared group kernel at `w` threads per
+// instance (0 if it does not fit), and the batch's parameters laid out for
+// that width.
+static int team_fit(const icm_batch *b, int w, int max_smem, icm::KParams &P)
+{
+    const icm::KParams &B = b->kp;
+    if (w < 32 || w % 32 || icm::kTeamThreads % w) return 0;
+    const int half = B.N / 2;
+    if (((half + w - 1) / w) * B.Z >= 256 || (B.N + w - 1) / w >= 256) return 0;   // observable counters
+    const icm::SmemLayout sm = icm::smem_layout(B.N, B.Z, B.R, B.G, B.nT, b->n_icm, w / 32, b->gauss, false);
+    int k = icm::kTeamThreads / w;
+    if (k * sm.total > max_smem) k = max_smem / sm.total;
+    if (k < 1) return 0;
+    P = B;
+    P.sm = sm;
+    P.wide = 0;
+    P.scratch = nullptr;
+    P.scratch_words = 0;
+    P.small_counts = (((half + w - 1) / w) * B.Z < 16 && (B.N + w - 1) / w < 16) ? 1 : 0;
+    return k;
 }
 
 extern "C" {
@@ -1520,6 +1550,149 @@ icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, 
         return cuda_fail(ctx, e, "group capture");
     }
     *out = g;
+    return ICM_OK;
+}
+
+icm_status icm_group_create_shared(icm_ctx *ctx, icm_batch *const *batches, int32_t n, uint32_t sweeps_per_launch,
+                                   const int32_t *team_threads, icm_group **out)
+{
+    if (!ctx || !batches || n < 1 || !out || sweeps_per_launch == 0) return ICM_ERR_ARG;
+    *out = nullptr;
+    if (n > icm::kTeamClasses)
+        return fail(ctx, ICM_ERR_UNSUPPORTED, "a shared group takes at most " + std::to_string(icm::kTeamClasses) +
+                                                  " batches");
+    for (int i = 0; i < n; ++i) {
+        const icm_batch *b = batches[i];
+        if (!b || b->ctx != ctx) return fail(ctx, ICM_ERR_ARG, "batches must belong to the context");
+        if (b->gauss != batches[0]->gauss || b->kp.Z != batches[0]->kp.Z)
+            return fail(ctx, ICM_ERR_UNSUPPORTED, "a shared group takes one disorder kind and one lattice degree");
+        if (b->seed != batches[0]->seed)
+            return fail(ctx, ICM_ERR_UNSUPPORTED, "a shared group takes batches of one seed (instance ids tell them apart)");
+        if (b->cluster_k || b->kp.diluted)
+            return fail(ctx, ICM_ERR_UNSUPPORTED, "a shared group takes undiluted batches outside the cluster layout");
+    }
+    icm_group *g = new (std::nothrow) icm_group();
+    if (!g) return ICM_ERR_OOM;
+    std::unique_ptr<icm::TeamParams> TP(new (std::nothrow) icm::TeamParams());
+    if (!TP) {
+        delete g;
+        return ICM_ERR_OOM;
+    }
+    g->ctx = ctx;
+    g->batches.assign(batches, batches + n);
+    g->sweeps = sweeps_per_launch;
+    g->shared = true;
+    for (int i = 0; i < 20; ++i) TP->key[i] = batches[0]->kp.key[i];
+    // per batch: threads per instance (given, or the width that keeps most
+    // threads of the CTA busy, the narrower on a tie) and instances per tile
+    static const int kWidths[] = {32, 64, 128, 224, 448, 896};
+    std::vector<icm::TeamItem> items;
+    std::vector<double> work;
+    for (int c = 0; c < n; ++c) {
+        icm_batch *b = batches[c];
+        int best_w = 0, best_k = 0;
+        icm::KParams best{}, P{};
+        if (team_threads && team_threads[c] > 0) {
+            best_k = team_fit(b, team_threads[c], ctx->max_smem_optin, best);
+            best_w = team_threads[c];
+        } else {
+            for (int w : kWidths) {
+                const int k = team_fit(b, w, ctx->max_smem_optin, P);
+                if (k > 0 && k * w > best_k * best_w) {
+                    best_w = w;
+                    best_k = k;
+                    best = P;
+                }
+            }
+        }
+        if (best_k < 1) {
+            destroy_group(g);
+            return fail(ctx, ICM_ERR_UNSUPPORTED, "batch " + std::to_string(c) +
+                                                      ": no team width (a divisor of " +
+                                                      std::to_string(icm::kTeamThreads) +
+                                                      ") fits the shared memory and the counters");
+        }
+        best.icm_every = b->sched.icm_every;
+        best.swap_every = b->sched.swap_every;
+        best.enable_2a = b->sched.enable_2a;
+        best.enable_metropolis = b->sched.enable_metropolis;
+        best.trace = b->sched.trace;
+        best.t_meas = b->sched.t_meas;
+        best.active = b->d_active;
+        best.t_meas_inst = b->d_tmeas;
+        TP->cls[c] = best;
+        TP->team_threads[c] = best_w;
+        g->team_threads.push_back(best_w);
+        g->tile.push_back(best_k);
+        g->smem = std::max(g->smem, best_k * best.sm.total);
+        for (int s0 = 0; s0 < b->n_inst; s0 += best_k) {
+            items.push_back({c, s0, std::min(best_k, b->n_inst - s0)});
+            work.push_back((double)items.back().count * best.N * best.R);
+        }
+    }
+    // the tiles in descending order of work (spin updates per sweep): the
+    // CTAs take the next one whenever they are free, largest first
+    std::vector<size_t> order(items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work[a] > work[b]; });
+    std::vector<icm::TeamItem> sorted(items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+    g->n_items = (int)sorted.size();
+    // tile list, then the two work counters (16-byte aligned after it)
+    const size_t list_bytes = (sorted.size() * sizeof(icm::TeamItem) + 15) / 16 * 16;
+    g->items_bytes = list_bytes + 16;
+    icm_status st = ctx_alloc(ctx, &g->d_items, g->items_bytes);
+    if (st) {
+        g->d_items = nullptr;
+        destroy_group(g);
+        return st;
+    }
+    cudaError_t e = cudaMemcpy(g->d_items, sorted.data(), sorted.size() * sizeof(icm::TeamItem),
+                               cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset((char *)g->d_items + list_bytes, 0, 16);
+    TP->items = (const icm::TeamItem *)g->d_items;
+    TP->n_items = g->n_items;
+    TP->counters = (int *)((char *)g->d_items + list_bytes);
+    int ctas = 0;
+    if (e == cudaSuccess) e = icm::team_occupancy(batches[0]->gauss, batches[0]->kp.Z, g->smem, &ctas);
+    if (e == cudaSuccess && ctas < 1) {
+        destroy_group(g);
+        return fail(ctx, ICM_ERR_UNSUPPORTED, "the shared group kernel does not fit an SM");
+    }
+    g->grid = std::min(g->n_items, ctx->num_sms * ctas);
+    // capture the one launch
+    cudaStream_t origin = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        e = icm::launch_team(*TP, batches[0]->gauss, batches[0]->kp.Z, g->grid, g->smem, sweeps_per_launch, origin);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ec = cudaStreamEndCapture(origin, &graph);
+        if (e == cudaSuccess) e = ec;
+        g->graph = graph;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, g->graph, 0);
+    if (origin) cudaStreamDestroy(origin);
+    if (e != cudaSuccess) {
+        destroy_group(g);
+        return cuda_fail(ctx, e, "shared group capture");
+    }
+    *out = g;
+    return ICM_OK;
+}
+
+icm_status icm_group_info(const icm_group *g, int32_t *team_threads, int32_t *tile, int32_t *grid, int32_t *smem,
+                          int32_t *n_items)
+{
+    if (!g) return ICM_ERR_ARG;
+    for (size_t c = 0; c < g->batches.size(); ++c) {
+        if (team_threads) team_threads[c] = g->shared ? g->team_threads[c] : g->batches[c]->threads;
+        if (tile) tile[c] = g->shared ? g->tile[c] : 1;
+    }
+    if (grid) *grid = g->shared ? g->grid : 0;
+    if (smem) *smem = g->shared ? g->smem : 0;
+    if (n_items) *n_items = g->shared ? g->n_items : 0;
     return ICM_OK;
 }
 

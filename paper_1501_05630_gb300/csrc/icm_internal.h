@@ -110,6 +110,26 @@ struct KParams {
     SmemLayout sm;
 };
 
+// The shared group kernel (pt_icm.cu): one persistent CTA of kTeamThreads
+// threads per SM runs tiles of instances of several batches (sizes) of one
+// disorder kind and degree; a tile of batch c is `count` instances side by
+// side, one team of team_threads[c] threads each (a divisor of
+// kTeamThreads), each team with its own shared memory (KParams::sm of its
+// batch, laid out for the team's width) and its own barrier.
+constexpr int kTeamThreads = 896;   // 7 x 128: the threads of seven fused-kernel CTAs
+constexpr int kTeamClasses = 8;     // batches per shared group
+struct TeamItem {
+    int cls, slot0, count;
+};
+struct TeamParams {
+    KParams cls[kTeamClasses];
+    int team_threads[kTeamClasses];
+    const TeamItem *items;         // [n_items], in the order the CTAs take them
+    int n_items;
+    int *counters;                 // [2]: next item, CTAs done; zero between launches
+    uint32_t key[20];              // Philox round keys of the common seed
+};
+
 // Host-built position tables of one lattice (see host_tables in icm_api.cpp).
 struct HostTables {
     int N = 0, Nb = 0, Z = 0;
@@ -180,6 +200,11 @@ cudaError_t launch_expand_dilution(const void *bond_J, bool gauss, const int32_t
                                    int n_inst, int N, int Z, int Nb, uint16_t *nbr_inst, uint8_t *zdeg_inst,
                                    int32_t *nb_inst, int32_t *bad, cudaStream_t st);
 cudaError_t launch_init_energies(const KParams &P, bool gauss, cudaStream_t st);
+// The shared group kernel: grid persistent CTAs of kTeamThreads threads with
+// `smem` bytes of dynamic shared memory each.
+cudaError_t launch_team(const TeamParams &TP, bool gauss, int Z, int grid, int smem, uint32_t n_sweeps,
+                        cudaStream_t st);
+cudaError_t team_occupancy(bool gauss, int Z, int smem, int *ctas_per_sm);
 cudaError_t launch_energies_to_double(const KParams &P, bool gauss, double *out, cudaStream_t st);
 
 }  // namespace icm

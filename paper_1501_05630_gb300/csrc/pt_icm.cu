@@ -49,6 +49,10 @@
 namespace icm {
 cudaError_t launch_fused_pmj(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st);
 cudaError_t launch_fused_gauss(const KParams &P, int threads, int grid, uint32_t n_sweeps, cudaStream_t st);
+cudaError_t launch_team_pmj(const TeamParams &TP, int Z, int grid, int smem, uint32_t n_sweeps, cudaStream_t st);
+cudaError_t launch_team_gauss(const TeamParams &TP, int Z, int grid, int smem, uint32_t n_sweeps, cudaStream_t st);
+cudaError_t team_occupancy_pmj(int Z, int smem, int *ctas);
+cudaError_t team_occupancy_gauss(int Z, int smem, int *ctas);
 cudaError_t fused_occupancy_pmj(int Z, bool wide, int threads, int smem, int *ctas);
 cudaError_t fused_occupancy_gauss(int Z, bool wide, int threads, int smem, int *ctas);
 int debug_phase_cycles_pmj(unsigned long long *out, int reset);
@@ -153,6 +157,39 @@ __device__ __forceinline__ uint32_t lds_u32(uint32_t addr)
     return v;
 }
 
+// The threads that run one instance: the whole CTA (the fused kernels), or
+// one of several teams of a persistent CTA that runs instances of several
+// sizes side by side (the shared group kernel).  A team is whole warps; its
+// barrier is the CTA barrier (bar 0), a named barrier of its own (bar 1..15)
+// or, for a one-warp team, a warp barrier (bar -1).
+struct Team {
+    int tid;   // thread index in the team
+    int nth;   // threads of the team, a multiple of 32
+    int bar;
+};
+
+__device__ __forceinline__ void team_sync(const Team &T)
+{
+    if (T.bar == 0) __syncthreads();
+    else if (T.bar < 0) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(T.bar), "r"(T.nth) : "memory");
+}
+
+// Barrier of the team that returns whether pred was set in any of its threads.
+__device__ __forceinline__ int team_sync_or(const Team &T, int pred)
+{
+    if (T.bar == 0) return __syncthreads_or(pred);
+    if (T.bar < 0) {
+        __syncwarp();
+        return __any_sync(kFull, pred);
+    }
+    int r;
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.s32 p, %1, 0;\n\tbar.red.or.pred q, %2, %3, p;\n\t"
+                 "selp.s32 %0, 1, 0, q;\n\t}"
+                 : "=r"(r) : "r"(pred), "r"(T.bar), "r"(T.nth) : "memory");
+    return r;
+}
+
 // Neighbour positions of position p (padding entries repeat p), read as
 // 32-bit pairs from the [N][Z] uint16 table (Z even, so rows are 4-byte aligned).
 template <int Z>
@@ -178,13 +215,13 @@ __device__ __forceinline__ void load_nbrs(const uint16_t *nbr, int p, int (&q)[Z
 // the same time (tiny instances), the flips go in by atomic XOR (each pass
 // owns its 16 bits, so the result does not depend on the order).
 template <bool GAUSS, int Z, bool WIDE, bool DIL, bool SHARED>
-__device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int g, int COLOR,
-                                           int H, int j0, int jstride)
+__device__ __forceinline__ void sweep_pass(const KParams &P, const uint32_t (&key)[20], const Sm &S, const Team &T,
+                                           uint32_t t, uint32_t inst, int g, int COLOR, int H, int j0, int jstride)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = T.tid >> 5;
     const int N = P.N, half = P.half;
-    [[maybe_unused]] const int nth = blockDim.x;   // the bound of a checked index
+    [[maybe_unused]] const int nth = T.nth;   // the bound of a checked index
     const int rbase = 32 * g + 16 * H;
     const int sh0 = 16 * H;                       // first bit of this pass inside the word
     const int npairs8 = (P.R - rbase + 7) >> 3;   // 8-bit groups holding at least one live replica (1 or 2)
@@ -218,7 +255,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.key, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, key, x, y);
                     uint32_t f8 = 0u;                           // this group's accepted bits
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
@@ -278,7 +315,7 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
             for (int qq = 0; qq < 2; ++qq) {
                 if (qq < npairs8) {
                     uint32_t x[4], y[4];
-                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, P.key, x, y);
+                    philox10x2(site, t, (uint32_t)(rbase >> 2) + 2 * qq, inst, key, x, y);
 #pragma unroll
                     for (int i = 0; i < 8; ++i) {
                         const int b = 8 * qq + i;
@@ -308,22 +345,23 @@ __device__ __forceinline__ void sweep_pass(const KParams &P, const Sm &S, uint32
 // same time; every warp writes its energy slots, the ones of passes it did not
 // run as 0.
 template <bool GAUSS, int Z, bool WIDE, bool DIL>
-__device__ __forceinline__ void metropolis_sweep_concurrent(const KParams &P, const Sm &S, uint32_t t, uint32_t inst,
-                                                         int npass, int gthr, int conc)
+__device__ __forceinline__ void metropolis_sweep_concurrent(const KParams &P, const uint32_t (&key)[20], const Sm &S,
+                                                         const Team &T, uint32_t t, uint32_t inst, int npass, int gthr,
+                                                         int conc)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
-    const int group = (int)threadIdx.x / gthr;
-    const int nslot = (int)(blockDim.x >> 5) * P.R;
-    for (int i = threadIdx.x; i < nslot; i += blockDim.x) ((ET *)S.Epart)[i] = ET(0);
-    __syncthreads();
+    const int group = T.tid / gthr;
+    const int nslot = (T.nth >> 5) * P.R;
+    for (int i = T.tid; i < nslot; i += T.nth) ((ET *)S.Epart)[i] = ET(0);
+    team_sync(T);
     for (int color = 0; color < 2; ++color) {
         for (int p0 = 0; p0 < npass; p0 += conc) {
             const int pass = p0 + group;
             if (group < conc && pass < npass)    // whole warps: gthr is a multiple of 32
-                sweep_pass<GAUSS, Z, WIDE, DIL, true>(P, S, t, inst, pass >> 1, color, pass & 1,
-                                                      (int)threadIdx.x - group * gthr, gthr);
+                sweep_pass<GAUSS, Z, WIDE, DIL, true>(P, key, S, T, t, inst, pass >> 1, color, pass & 1,
+                                                      T.tid - group * gthr, gthr);
         }
-        __syncthreads();
+        team_sync(T);
     }
 }
 
@@ -331,20 +369,21 @@ __device__ __forceinline__ void metropolis_sweep_concurrent(const KParams &P, co
 // the site words.  One call site, so the pass body exists once in the kernel
 // (the instruction cache is shared by all CTAs of the SM).
 template <bool GAUSS, int Z, bool WIDE, bool DIL>
-__device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, uint32_t t, uint32_t inst)
+__device__ __forceinline__ void metropolis_sweep(const KParams &P, const uint32_t (&key)[20], const Sm &S, const Team &T,
+                                                 uint32_t t, uint32_t inst)
 {
     const int npass = (P.R + 15) >> 4;          // 16-bit passes per colour
     const int gthr = (P.half + 31) & ~31;        // threads of one pass
-    const int conc = min((int)blockDim.x / gthr, npass);   // passes at a time
+    const int conc = min(T.nth / gthr, npass);   // passes at a time
     if (conc >= 2) {
-        metropolis_sweep_concurrent<GAUSS, Z, WIDE, DIL>(P, S, t, inst, npass, gthr, conc);
+        metropolis_sweep_concurrent<GAUSS, Z, WIDE, DIL>(P, key, S, T, t, inst, npass, gthr, conc);
         return;
     }
     for (int it = 0; it < 2 * npass; ++it) {
         const int color = it >= npass;
         const int pass = it - color * npass;
-        sweep_pass<GAUSS, Z, WIDE, DIL, false>(P, S, t, inst, pass >> 1, color, pass & 1, threadIdx.x, blockDim.x);
-        if (pass == npass - 1) __syncthreads();
+        sweep_pass<GAUSS, Z, WIDE, DIL, false>(P, key, S, T, t, inst, pass >> 1, color, pass & 1, T.tid, T.nth);
+        if (pass == npass - 1) team_sync(T);
     }
 }
 
@@ -355,11 +394,12 @@ __device__ __forceinline__ void metropolis_sweep(const KParams &P, const Sm &S, 
 // fixed order.  Every thread ends with partial sums in S.Epart[warp][k]; the
 // caller adds warps.
 template <bool GAUSS, int Z, bool WIDE>
-__device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uint32_t act0, uint32_t act1, int cb)
+__device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, const Team &T, uint32_t act0, uint32_t act1,
+                                              int cb)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int N = P.N, half = P.half, nth = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = T.tid >> 5;
+    const int N = P.N, half = P.half, nth = T.nth;
     ET *part = (ET *)S.Epart;
     for (int g = 0; g < P.G; ++g) {
         const uint32_t act = g ? act1 : act0;
@@ -368,7 +408,7 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
         ET acc[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[j] = ET(0);
-        for (int i = threadIdx.x; i < half; i += nth) {
+        for (int i = T.tid; i < half; i += nth) {
             const int p = half + i;              // colour-1 sites: every bond once
             const uint32_t sw = sg[p] >> cb;
             int q[Z];
@@ -430,11 +470,12 @@ __device__ __forceinline__ void pair_energies(const KParams &P, const Sm &S, uin
 //      E_a + E_b of the two recomputed energies, so that the trace tests the
 //      conservation of E_a + E_b instead of restating it.
 template <bool GAUSS, int Z, bool WIDE>
-__device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
+__device__ void cluster_moves(const KParams &P, const uint32_t (&key)[20], const Sm &S, const Team &T, uint32_t t,
+                              uint32_t inst, int slot, bool trace)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane = threadIdx.x & 31, warp = T.tid >> 5, nwarps = T.nth >> 5;
+    const int tid = T.tid, nth = T.nth;
     const int N = P.N, NW = P.NW, nicm = P.n_icm, G = P.G;
     ET *E = (ET *)S.E;
     ET *esum = (ET *)S.icm_esum_raw;
@@ -458,7 +499,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     }
     for (int i = tid; i < N; i += nth) S.C[i] = 0u;
     if (tid < 2) S.flipw[tid] = 0u;
-    __syncthreads();
+    team_sync(T);
 
     // (b) per pair: n, step 2a, seed (planted into C)
     for (int k = tid; k < nicm; k += nth) {
@@ -479,7 +520,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         int seed = -1;
         if (n > 0) {
             uint32_t x[4];
-            philox10k((uint32_t)k, t, 0u, (1u << 24) | inst, P.key, x);
+            philox10k((uint32_t)k, t, 0u, (1u << 24) | inst, key, x);
             uint32_t rank = (uint32_t)(((uint64_t)x[0] * (uint32_t)n) >> 32);
             for (int m = 0; m < NW; ++m) {
                 const uint32_t w = Mk[m];
@@ -504,7 +545,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             P.tr_ea[o] = (float)(E[2 * k] + E[2 * k + 1]);
         }
     }
-    __syncthreads();
+    team_sync(T);
     ICM_SUB(8);
 
     // (c) which pairs move, then copy-1 reversal and cluster growth.  One
@@ -587,7 +628,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                     }
                 }
                 ++rounds;
-            } while (__syncthreads_or(grew));
+            } while (team_sync_or(T, grew));
             // (d) flip the owned sites in both copies of every moving pair
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
@@ -604,7 +645,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             S.s[p] ^= f0;
             if (G > 1) S.s[N + p] ^= f1;
         }
-        __syncthreads();
+        team_sync(T);
         if (actc) {
             int grew;
             do {
@@ -626,7 +667,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
                     }
                 }
                 ++rounds;
-            } while (__syncthreads_or(grew));
+            } while (team_sync_or(T, grew));
             for (int p = tid; p < N; p += nth) {
                 const uint32_t c = C[p];
                 if (c) {
@@ -646,7 +687,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
     }
     ICM_SUB(9);
     if (!actc) {
-        __syncthreads();
+        team_sync(T);
         return;
     }
     if (trace) {
@@ -664,9 +705,9 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             }
         }
     }
-    __syncthreads();
-    pair_energies<GAUSS, Z, WIDE>(P, S, act0, act1, 0);
-    __syncthreads();
+    team_sync(T);
+    pair_energies<GAUSS, Z, WIDE>(P, S, T, act0, act1, 0);
+    team_sync(T);
     for (int k = tid; k < nicm; k += nth) {
         if (S.icm_seed[k] < 0) continue;
         ET ea = ET(0);
@@ -676,11 +717,11 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
         E[2 * k + 1] = esum[k] - ea;
         if (trace) P.tr_csize[(size_t)slot * P.nT + k] = S.cnt_d[k];
     }
-    __syncthreads();
+    team_sync(T);
     if (trace) {
         // E_b of the moved pairs on its own, from the flipped spins
-        pair_energies<GAUSS, Z, WIDE>(P, S, act0, act1, 1);
-        __syncthreads();
+        pair_energies<GAUSS, Z, WIDE>(P, S, T, act0, act1, 1);
+        team_sync(T);
         for (int k = tid; k < nicm; k += nth) {
             if (S.icm_seed[k] < 0) continue;
             ET eb = ET(0);
@@ -689,7 +730,7 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
             P.tr_ea[(size_t)slot * P.nT + k] = (float)(E[2 * k] + eb);
         }
         for (int k = tid; k < 32; k += nth) S.cnt_d[k] = 0;
-        __syncthreads();
+        team_sync(T);
     }
     ICM_SUB(10);
 }
@@ -697,45 +738,46 @@ __device__ void cluster_moves(const KParams &P, const Sm &S, uint32_t t, uint32_
 // ---------------------------------------------------------------------------
 // Step 3: the PT pass of each copy (see pt_warp), then the configuration swaps.
 template <bool GAUSS, bool WIDE>
-__device__ void pt_pass(const KParams &P, const Sm &S, uint32_t t, uint32_t inst, int slot, bool trace)
+__device__ void pt_pass(const KParams &P, const uint32_t (&key)[20], const Sm &S, const Team &T, uint32_t t,
+                        uint32_t inst, int slot, bool trace)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int nT = P.nT, np = nT - 1, N = P.N;
     // draws of all (copy, pair) in parallel, in the form of their test
-    for (int i = threadIdx.x; i < 2 * np; i += blockDim.x) {
+    for (int i = T.tid; i < 2 * np; i += T.nth) {
         const int c = i / np, k = i % np;
         uint32_t x[4];
-        philox10k((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, P.key, x);
+        philox10k((uint32_t)k, t, (uint32_t)c, (2u << 24) | inst, key, x);
         if constexpr (GAUSS) S.swap_x[c * 32 + k] = pt_word_gauss(x[0]);
         else S.swap_x[c * 32 + k] = pt_word_pmj(x[0], P.thr_swap + S.sw_off[k], S.sw_len[k], P.dbeta_l2e[k]);
     }
-    __syncthreads();
+    team_sync(T);
     // warp 0 runs both copies (a half-warp each).  Accepted swaps (k,k+1), ...,
     // (m,m+1) in a row form a run: the configuration at k bubbles up to m+1
     // and those at k+1..m+1 move down one slot; the words are permuted below
     // from the runs and the mask of bits that move down.
-    if (threadIdx.x < 32)
+    if (T.tid < 32)
         pt_warp<GAUSS, ET>((ET *)S.E, P.R, np, S.swap_x, S.sw_dbl, S.swap_list, S.swap_n, S.swap_mask,
                            trace ? P.tr_swap + (size_t)slot * 2 * np : nullptr);
-    __syncthreads();
+    team_sync(T);
     const int n0 = S.swap_n[0], n1 = S.swap_n[1];
     if (n0 + n1 > 0) {
         const SwapMasks m = swap_masks(S.swap_list, n0, n1, S.swap_mask);
         const bool two = P.G > 1;
-        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        for (int p = T.tid; p < N; p += T.nth) {
             const uint64_t x = (uint64_t)S.s[p] | (two ? (uint64_t)S.s[N + p] << 32 : 0ull);
             const uint64_t y = swap_apply(m, x);
             S.s[p] = (uint32_t)y;
             if (two) S.s[N + p] = (uint32_t)(y >> 32);
         }
     }
-    __syncthreads();
+    team_sync(T);
 }
 
 // ---------------------------------------------------------------------------
 // Observables: per pair k, n = #{q_i = -1} and d = #{bonds, q_i q_j = -1}.
 template <bool GAUSS, int Z, int NPL, bool WIDE>
-__device__ void measure(const KParams &P, const Sm &S, int slot)
+__device__ void measure(const KParams &P, const Sm &S, const Team &T, int slot)
 {
     using ET = typename std::conditional<GAUSS, float, int>::type;
     const int lane = threadIdx.x & 31;
@@ -746,11 +788,11 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
         uint32_t pl[NPL];   // even bit 2k: q = -1 sites of pair k; odd bit 2k+1: its q_i q_j = -1 bonds
 #pragma unroll
         for (int i = 0; i < NPL; ++i) pl[i] = 0u;
-        for (int p = threadIdx.x; p < N; p += blockDim.x) {
+        for (int p = T.tid; p < N; p += T.nth) {
             const uint32_t w = sg[p];
             vadd(pl, (w ^ (w >> 1)) & 0x55555555u);
         }
-        for (int p = half + threadIdx.x; p < N; p += blockDim.x) {
+        for (int p = half + T.tid; p < N; p += T.nth) {
             const uint32_t w = sg[p];
             const uint32_t qp = (w ^ (w >> 1)) & 0x55555555u;
             int qn[Z];
@@ -768,8 +810,8 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
         const int v = warp_vsum(pl, lane);   // lane 2k: n of pair k, lane 2k+1: d of pair k
         if (lane < 2 * npair) atomicAdd(((lane & 1) ? S.cnt_d : S.cnt_n) + 16 * g + (lane >> 1), v);
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < nT; k += blockDim.x) {
+    team_sync(T);
+    for (int k = T.tid; k < nT; k += T.nth) {
         const long long n = S.cnt_n[k], d = S.cnt_d[k];
         S.cnt_n[k] = 0;
         S.cnt_d[k] = 0;
@@ -781,36 +823,20 @@ __device__ void measure(const KParams &P, const Sm &S, int slot)
         S.acc64[3 * nT + k] += d;
         atomicAdd(&P.hist[((size_t)slot * nT + k) * (N + 1) + ICM_IDX(n, N + 1, 14)], 1ull);
     }
-    if (threadIdx.x == 0) S.nmeas[0] += 1;
-    __syncthreads();
+    if (T.tid == 0) S.nmeas[0] += 1;
+    team_sync(T);
 }
 
 // ---------------------------------------------------------------------------
-// The fused step loop.  WIDE = false: the whole instance lives in shared
-// memory for the launch.  WIDE = true (instances too large for one CTA's
-// shared memory): spins and couplings are updated in place in global memory,
-// the neighbour table is read from global memory, and the cluster words and
-// overlap masks use a per-CTA global scratch; the arithmetic is the same.
-// DIL = true (some instance of the batch has absent bonds): the neighbour
-// table and degrees are per instance (absent bonds point at the site itself,
-// like padding) and a diluted instance takes the probability-1/2 rule for
-// zero-energy proposals.
+// The per-batch tables of a team's shared memory: the neighbour table (the
+// shared-memory layout of an undiluted batch), degrees, temperature and swap
+// tables, cleared counters.
 template <bool GAUSS, int Z, bool WIDE, bool DIL>
-__device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
+__device__ __forceinline__ void load_tables(const KParams &P, Sm &S, const Team &T)
 {
-    using ET = typename std::conditional<GAUSS, float, int>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
-    Sm S = make_sm(smem, P.sm);
-    PHASE_INIT();
-    const int tid = threadIdx.x, nth = blockDim.x, nwarps = nth >> 5;
+    const int tid = T.tid, nth = T.nth;
     const int N = P.N, R = P.R, nT = P.nT, G = P.G;
-
-    if constexpr (WIDE) {
-        S.nbr = const_cast<uint16_t *>(P.nbr);
-        S.zdeg = const_cast<uint8_t *>(P.zdeg);
-        S.C = P.scratch + (size_t)blockIdx.x * P.scratch_words;
-        S.mask = S.C + 2 * N;
-    } else if constexpr (!DIL) {
+    if constexpr (!WIDE && !DIL) {
         for (int i = tid; i < N * Z; i += nth) S.nbr[i] = P.nbr[i];
         if (!GAUSS && !P.const_z)
             for (int i = tid; i < N; i += nth) S.zdeg[i] = P.zdeg[i];
@@ -835,123 +861,161 @@ __device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
         S.cnt_n[tid] = 0;
         S.cnt_d[tid] = 0;
     }
+}
 
+// n_sweeps simulation steps of the instance in slot `slot`, run by team T:
+// load its state into the team's shared memory (the spins and couplings stay
+// in global memory in the wide layout), run the steps, store the state back.
+template <bool GAUSS, int Z, bool WIDE, bool DIL>
+__device__ __forceinline__ void run_instance(const KParams &P, const uint32_t (&key)[20], Sm &S, const Team &T,
+                                             int slot, uint32_t n_sweeps)
+{
+    using ET = typename std::conditional<GAUSS, float, int>::type;
+    PHASE_INIT();
+    const int tid = T.tid, nth = T.nth, nwarps = nth >> 5;
+    const int N = P.N, R = P.R, nT = P.nT, G = P.G;
+    if constexpr (DIL) {
+        const uint16_t *nb_src = P.nbr_inst + (size_t)slot * N * Z;
+        const uint8_t *zd_src = P.zdeg_inst + (size_t)slot * N;
+        if constexpr (WIDE) {
+            S.nbr = const_cast<uint16_t *>(nb_src);
+            S.zdeg = const_cast<uint8_t *>(zd_src);
+        } else {
+            const uint32_t *src = (const uint32_t *)nb_src;     // N Z even: whole 32-bit pairs
+            uint32_t *dst = (uint32_t *)S.nbr;
+            for (int i = tid; i < (N * Z) / 2; i += nth) dst[i] = src[i];
+            for (int i = tid; i < N; i += nth) S.zdeg[i] = zd_src[i];
+        }
+        S.nb = P.nb_inst[slot];
+        S.tie = S.nb < P.Nb;
+    }
+    if constexpr (WIDE) {
+        S.s = P.spins + (size_t)slot * G * N;
+        S.Jd = const_cast<float *>(P.Jd) + (size_t)slot * N * Z;
+        S.Jb = const_cast<uint8_t *>(P.Jb) + (size_t)slot * N;
+    } else {
+        const uint32_t *gs = P.spins + (size_t)slot * G * N;
+        for (int i = tid; i < G * N; i += nth) S.s[i] = gs[i];
+        if constexpr (GAUSS) {
+            const float4 *src = (const float4 *)(P.Jd + (size_t)slot * N * Z);
+            float4 *dst = (float4 *)S.Jd;
+            for (int i = tid; i < (N * Z) / 4; i += nth) dst[i] = src[i];
+        } else {
+            for (int i = tid; i < N; i += nth) S.Jb[i] = P.Jb[(size_t)slot * N + i];
+        }
+    }
+    if constexpr (GAUSS) {
+        for (int r = tid; r < R; r += nth) ((float *)S.E)[r] = P.Ef[(size_t)slot * R + r];
+    } else {
+        for (int r = tid; r < R; r += nth) ((int *)S.E)[r] = P.Ei[(size_t)slot * R + r];
+    }
+    for (int k = tid; k < nT; k += nth) {
+        S.accE[k] = P.accE[(size_t)slot * nT + k];
+        for (int a = 0; a < 4; ++a) S.acc64[a * nT + k] = P.acc64[((size_t)a * P.n_inst + slot) * nT + k];
+    }
+    if (tid == 0) {
+        S.nmeas[0] = P.n_meas[slot];
+        S.icmst[0] = S.icmst[1] = 0ull;
+    }
+    const uint32_t inst = P.inst_id[slot];
+    const long long t_meas = P.t_meas_inst ? P.t_meas_inst[slot] : P.t_meas;
+    uint32_t t = P.tsweep[slot];
+    team_sync(T);
+
+    PHASE_MARK(5);
+    for (uint32_t step = 0; step < n_sweeps; ++step, ++t) {
+        const bool trace = P.trace && step + 1 == n_sweeps;
+        if (trace) {
+            for (int k = tid; k < nT; k += nth) {
+                const size_t o = (size_t)slot * nT + k;
+                P.tr_n_pre[o] = -1;
+                P.tr_flip2a[o] = 0;
+                P.tr_seed[o] = -1;
+                P.tr_csize[o] = 0;
+                P.tr_eb[o] = 0.f;
+                P.tr_ea[o] = 0.f;
+            }
+            for (int i = tid; i < 2 * (nT - 1); i += nth) P.tr_swap[(size_t)slot * 2 * (nT - 1) + i] = 0;
+            if (P.tr_cmask)
+                for (int i = tid; i < 2 * N; i += nth) P.tr_cmask[(size_t)slot * 2 * N + i] = 0u;
+            team_sync(T);
+        }
+        if (P.enable_metropolis) {  // step 1
+            metropolis_sweep<GAUSS, Z, WIDE, DIL>(P, key, S, T, t, inst);
+            for (int r = tid; r < R; r += nth) {
+                ET e = ET(0);
+                for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + r];
+                ((ET *)S.E)[r] = e;
+            }
+            team_sync(T);
+        }
+        PHASE_MARK(0);
+        if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)  // steps 2a, 2b
+            cluster_moves<GAUSS, Z, WIDE>(P, key, S, T, t, inst, slot, trace);
+        PHASE_MARK(1);
+        if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1)  // step 3
+            pt_pass<GAUSS, WIDE>(P, key, S, T, t, inst, slot, trace);
+        PHASE_MARK(2);
+        if ((long long)t >= t_meas) {
+            if (P.small_counts) measure<GAUSS, Z, 4, WIDE>(P, S, T, slot);   // every per-thread count < 16
+            else measure<GAUSS, Z, kPlanes, WIDE>(P, S, T, slot);
+        }
+        PHASE_MARK(3);
+    }
+
+    PHASE_MARK(4);
+    if constexpr (!WIDE) {
+        uint32_t *gd = P.spins + (size_t)slot * G * N;
+        for (int i = tid; i < G * N; i += nth) gd[i] = S.s[i];
+    }
+    for (int r = tid; r < R; r += nth) {
+        if constexpr (GAUSS) P.Ef[(size_t)slot * R + r] = ((float *)S.E)[r];
+        else P.Ei[(size_t)slot * R + r] = ((int *)S.E)[r];
+    }
+    for (int k = tid; k < nT; k += nth) {
+        P.accE[(size_t)slot * nT + k] = S.accE[k];
+        for (int a = 0; a < 4; ++a) P.acc64[((size_t)a * P.n_inst + slot) * nT + k] = S.acc64[a * nT + k];
+    }
+    if (tid == 0) {
+        P.n_meas[slot] = S.nmeas[0];
+        P.tsweep[slot] = t;
+        if (P.icm_stats) {
+            P.icm_stats[2 * (size_t)slot] += S.icmst[0];
+            P.icm_stats[2 * (size_t)slot + 1] += S.icmst[1];
+        }
+    }
+    team_sync(T);
+    PHASE_MARK(5);
+    PHASE_FLUSH();
+}
+
+// The fused step loop.  WIDE = false: the whole instance lives in shared
+// memory for the launch.  WIDE = true (instances too large for one CTA's
+// shared memory): spins and couplings are updated in place in global memory,
+// the neighbour table is read from global memory, and the cluster words and
+// overlap masks use a per-CTA global scratch; the arithmetic is the same.
+// DIL = true (some instance of the batch has absent bonds): the neighbour
+// table and degrees are per instance (absent bonds point at the site itself,
+// like padding) and a diluted instance takes the probability-1/2 rule for
+// zero-energy proposals.  One CTA runs the instances blockIdx.x,
+// blockIdx.x + gridDim.x, ... in turn.
+template <bool GAUSS, int Z, bool WIDE, bool DIL>
+__device__ __forceinline__ void fused_body(const KParams &P, uint32_t n_sweeps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    Sm S = make_sm(smem, P.sm);
+    const Team T{(int)threadIdx.x, (int)blockDim.x, 0};
+    if constexpr (WIDE) {
+        S.nbr = const_cast<uint16_t *>(P.nbr);
+        S.zdeg = const_cast<uint8_t *>(P.zdeg);
+        S.C = P.scratch + (size_t)blockIdx.x * P.scratch_words;
+        S.mask = S.C + 2 * P.N;
+    }
+    load_tables<GAUSS, Z, WIDE, DIL>(P, S, T);
     for (int slot = blockIdx.x; slot < P.n_inst; slot += gridDim.x) {
         if (P.active && !P.active[slot]) continue;   // free slot of a serving batch
-        if constexpr (DIL) {
-            const uint16_t *nb_src = P.nbr_inst + (size_t)slot * N * Z;
-            const uint8_t *zd_src = P.zdeg_inst + (size_t)slot * N;
-            if constexpr (WIDE) {
-                S.nbr = const_cast<uint16_t *>(nb_src);
-                S.zdeg = const_cast<uint8_t *>(zd_src);
-            } else {
-                const uint32_t *src = (const uint32_t *)nb_src;     // N Z even: whole 32-bit pairs
-                uint32_t *dst = (uint32_t *)S.nbr;
-                for (int i = tid; i < (N * Z) / 2; i += nth) dst[i] = src[i];
-                for (int i = tid; i < N; i += nth) S.zdeg[i] = zd_src[i];
-            }
-            S.nb = P.nb_inst[slot];
-            S.tie = S.nb < P.Nb;
-        }
-        if constexpr (WIDE) {
-            S.s = P.spins + (size_t)slot * G * N;
-            S.Jd = const_cast<float *>(P.Jd) + (size_t)slot * N * Z;
-            S.Jb = const_cast<uint8_t *>(P.Jb) + (size_t)slot * N;
-        } else {
-            const uint32_t *gs = P.spins + (size_t)slot * G * N;
-            for (int i = tid; i < G * N; i += nth) S.s[i] = gs[i];
-            if constexpr (GAUSS) {
-                const float4 *src = (const float4 *)(P.Jd + (size_t)slot * N * Z);
-                float4 *dst = (float4 *)S.Jd;
-                for (int i = tid; i < (N * Z) / 4; i += nth) dst[i] = src[i];
-            } else {
-                for (int i = tid; i < N; i += nth) S.Jb[i] = P.Jb[(size_t)slot * N + i];
-            }
-        }
-        if constexpr (GAUSS) {
-            for (int r = tid; r < R; r += nth) ((float *)S.E)[r] = P.Ef[(size_t)slot * R + r];
-        } else {
-            for (int r = tid; r < R; r += nth) ((int *)S.E)[r] = P.Ei[(size_t)slot * R + r];
-        }
-        for (int k = tid; k < nT; k += nth) {
-            S.accE[k] = P.accE[(size_t)slot * nT + k];
-            for (int a = 0; a < 4; ++a) S.acc64[a * nT + k] = P.acc64[((size_t)a * P.n_inst + slot) * nT + k];
-        }
-        if (tid == 0) {
-            S.nmeas[0] = P.n_meas[slot];
-            S.icmst[0] = S.icmst[1] = 0ull;
-        }
-        const uint32_t inst = P.inst_id[slot];
-        const long long t_meas = P.t_meas_inst ? P.t_meas_inst[slot] : P.t_meas;
-        uint32_t t = P.tsweep[slot];
-        __syncthreads();
-
-        PHASE_MARK(5);
-        for (uint32_t step = 0; step < n_sweeps; ++step, ++t) {
-            const bool trace = P.trace && step + 1 == n_sweeps;
-            if (trace) {
-                for (int k = tid; k < nT; k += nth) {
-                    const size_t o = (size_t)slot * nT + k;
-                    P.tr_n_pre[o] = -1;
-                    P.tr_flip2a[o] = 0;
-                    P.tr_seed[o] = -1;
-                    P.tr_csize[o] = 0;
-                    P.tr_eb[o] = 0.f;
-                    P.tr_ea[o] = 0.f;
-                }
-                for (int i = tid; i < 2 * (nT - 1); i += nth) P.tr_swap[(size_t)slot * 2 * (nT - 1) + i] = 0;
-                if (P.tr_cmask)
-                    for (int i = tid; i < 2 * N; i += nth) P.tr_cmask[(size_t)slot * 2 * N + i] = 0u;
-                __syncthreads();
-            }
-            if (P.enable_metropolis) {  // step 1
-                metropolis_sweep<GAUSS, Z, WIDE, DIL>(P, S, t, inst);
-                for (int r = tid; r < R; r += nth) {
-                    ET e = ET(0);
-                    for (int w = 0; w < nwarps; ++w) e += ((const ET *)S.Epart)[w * R + r];
-                    ((ET *)S.E)[r] = e;
-                }
-                __syncthreads();
-            }
-            PHASE_MARK(0);
-            if (P.icm_every > 0 && t % (uint32_t)P.icm_every == 0 && P.n_icm > 0)  // steps 2a, 2b
-                cluster_moves<GAUSS, Z, WIDE>(P, S, t, inst, slot, trace);
-            PHASE_MARK(1);
-            if (P.swap_every > 0 && t % (uint32_t)P.swap_every == 0 && nT > 1)  // step 3
-                pt_pass<GAUSS, WIDE>(P, S, t, inst, slot, trace);
-            PHASE_MARK(2);
-            if ((long long)t >= t_meas) {
-                if (P.small_counts) measure<GAUSS, Z, 4, WIDE>(P, S, slot);   // every per-thread count < 16
-                else measure<GAUSS, Z, kPlanes, WIDE>(P, S, slot);
-            }
-            PHASE_MARK(3);
-        }
-
-        PHASE_MARK(4);
-        if constexpr (!WIDE) {
-            uint32_t *gd = P.spins + (size_t)slot * G * N;
-            for (int i = tid; i < G * N; i += nth) gd[i] = S.s[i];
-        }
-        for (int r = tid; r < R; r += nth) {
-            if constexpr (GAUSS) P.Ef[(size_t)slot * R + r] = ((float *)S.E)[r];
-            else P.Ei[(size_t)slot * R + r] = ((int *)S.E)[r];
-        }
-        for (int k = tid; k < nT; k += nth) {
-            P.accE[(size_t)slot * nT + k] = S.accE[k];
-            for (int a = 0; a < 4; ++a) P.acc64[((size_t)a * P.n_inst + slot) * nT + k] = S.acc64[a * nT + k];
-        }
-        if (tid == 0) {
-            P.n_meas[slot] = S.nmeas[0];
-            P.tsweep[slot] = t;
-            if (P.icm_stats) {
-                P.icm_stats[2 * (size_t)slot] += S.icmst[0];
-                P.icm_stats[2 * (size_t)slot + 1] += S.icmst[1];
-            }
-        }
-        __syncthreads();
-        PHASE_MARK(5);
+        run_instance<GAUSS, Z, WIDE, DIL>(P, P.key, S, T, slot, n_sweeps);
     }
-    PHASE_FLUSH();
 }
 
 template <bool GAUSS, int Z, bool DIL>
@@ -964,6 +1028,48 @@ template <bool GAUSS, int Z, bool DIL>
 __global__ void __launch_bounds__(kMaxThreadsWide, 1) fused_wide_kernel(const KParams P, uint32_t n_sweeps)
 {
     fused_body<GAUSS, Z, true, DIL>(P, n_sweeps);
+}
+
+// The shared group kernel (see TeamParams): each persistent CTA takes the
+// next work item (a global counter) whenever it is free, so the tiles, in
+// descending order of work, balance over the CTAs; a tile's teams run their
+// instances side by side, and the CTA barrier after each item frees the
+// shared memory for the next.  The last CTA to finish resets the counters
+// for the next launch (launches on one stream run in order).  Which CTA runs
+// an instance does not change its result: same arithmetic and random keys as
+// the fused kernel, so a +-J instance follows the same chain in either.
+template <bool GAUSS, int Z>
+__global__ void __launch_bounds__(kTeamThreads, 1) team_kernel(const __grid_constant__ TeamParams TP, uint32_t n_sweeps)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int next_item;
+    for (;;) {
+        if (threadIdx.x == 0) next_item = atomicAdd(&TP.counters[0], 1);
+        __syncthreads();
+        const int it = next_item;
+        if (it >= TP.n_items) break;           // the same value in every thread
+        const TeamItem w = TP.items[it];
+        const KParams &P = TP.cls[w.cls];
+        const int tw = TP.team_threads[w.cls];
+        const int team = (int)threadIdx.x / tw;
+        if (team < w.count) {
+            const int slot = w.slot0 + team;
+            if (!P.active || P.active[slot]) {
+                const Team T{(int)threadIdx.x - team * tw, tw, tw == 32 ? -1 : team + 1};
+                Sm S = make_sm(smem + (size_t)team * P.sm.total, P.sm);
+                load_tables<GAUSS, Z, false, false>(P, S, T);
+                run_instance<GAUSS, Z, false, false>(P, TP.key, S, T, slot, n_sweeps);
+            }
+        }
+        __syncthreads();                       // also: every thread has read next_item
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&TP.counters[1], 1) == (int)gridDim.x - 1) {   // every CTA has taken its last item
+            TP.counters[0] = 0;
+            TP.counters[1] = 0;
+        }
+    }
 }
 
 #if ICM_PART == 0
@@ -1228,6 +1334,17 @@ cudaError_t launch_fused(const KParams &P, bool gauss, int threads, int grid, ui
     return gauss ? launch_fused_gauss(P, threads, grid, n_sweeps, st) : launch_fused_pmj(P, threads, grid, n_sweeps, st);
 }
 
+cudaError_t launch_team(const TeamParams &TP, bool gauss, int Z, int grid, int smem, uint32_t n_sweeps,
+                        cudaStream_t st)
+{
+    return gauss ? launch_team_gauss(TP, Z, grid, smem, n_sweeps, st) : launch_team_pmj(TP, Z, grid, smem, n_sweeps, st);
+}
+
+cudaError_t team_occupancy(bool gauss, int Z, int smem, int *ctas)
+{
+    return gauss ? team_occupancy_gauss(Z, smem, ctas) : team_occupancy_pmj(Z, smem, ctas);
+}
+
 cudaError_t launch_pack_spins(const int8_t *src, uint32_t *dst, const uint16_t *pos2site, int n_inst, int R, int G,
                               int N, cudaStream_t st)
 {
@@ -1311,6 +1428,45 @@ cudaError_t launch_part(const KParams &P, int threads, int grid, uint32_t n_swee
                      : launch_fused_z<false>(P, threads, grid, n_sweeps, st);
 }
 
+template <int Z>
+cudaError_t launch_team_t(const TeamParams &TP, int grid, int smem, uint32_t n_sweeps, cudaStream_t st)
+{
+    auto kern = team_kernel<kPartGauss, Z>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kTeamThreads, smem, st>>>(TP, n_sweeps);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_team_part(const TeamParams &TP, int Z, int grid, int smem, uint32_t n_sweeps, cudaStream_t st)
+{
+    switch (Z) {
+    case 4: return launch_team_t<4>(TP, grid, smem, n_sweeps, st);
+    case 6: return launch_team_t<6>(TP, grid, smem, n_sweeps, st);
+    case 8: return launch_team_t<8>(TP, grid, smem, n_sweeps, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int Z>
+cudaError_t team_occupancy_t(int smem, int *ctas)
+{
+    auto kern = team_kernel<kPartGauss, Z>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, kern, kTeamThreads, smem);
+}
+
+cudaError_t team_occupancy_part(int Z, int smem, int *ctas)
+{
+    switch (Z) {
+    case 4: return team_occupancy_t<4>(smem, ctas);
+    case 6: return team_occupancy_t<6>(smem, ctas);
+    case 8: return team_occupancy_t<8>(smem, ctas);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 cudaError_t occupancy_part(int Z, bool wide, int threads, int smem, int *ctas)
 {
     switch (Z) {
@@ -1363,6 +1519,11 @@ cudaError_t fused_occupancy_pmj(int Z, bool wide, int threads, int smem, int *ct
 {
     return occupancy_part(Z, wide, threads, smem, ctas);
 }
+cudaError_t launch_team_pmj(const TeamParams &TP, int Z, int grid, int smem, uint32_t n_sweeps, cudaStream_t st)
+{
+    return launch_team_part(TP, Z, grid, smem, n_sweeps, st);
+}
+cudaError_t team_occupancy_pmj(int Z, int smem, int *ctas) { return team_occupancy_part(Z, smem, ctas); }
 int debug_phase_cycles_pmj(unsigned long long *out, int reset) { return phase_cycles_part(out, reset); }
 int debug_check_pmj(unsigned int *out, int reset) { return check_part(out, reset); }
 #else
@@ -1374,6 +1535,11 @@ cudaError_t fused_occupancy_gauss(int Z, bool wide, int threads, int smem, int *
 {
     return occupancy_part(Z, wide, threads, smem, ctas);
 }
+cudaError_t launch_team_gauss(const TeamParams &TP, int Z, int grid, int smem, uint32_t n_sweeps, cudaStream_t st)
+{
+    return launch_team_part(TP, Z, grid, smem, n_sweeps, st);
+}
+cudaError_t team_occupancy_gauss(int Z, int smem, int *ctas) { return team_occupancy_part(Z, smem, ctas); }
 int debug_phase_cycles_gauss(unsigned long long *out, int reset) { return phase_cycles_part(out, reset); }
 int debug_check_gauss(unsigned int *out, int reset) { return check_part(out, reset); }
 #endif

@@ -8,7 +8,7 @@ the measured sweeps and then over disorder instances.  Clusters of the
 isoenergetic move percolate once p exceeds the site-percolation threshold
 p_c of the lattice; `crossing_temperature` locates where p(T) reaches p_c.
 
-Thermalization:
+Thermalization (and the frequency of the cluster moves judged on it):
 
 For one method -- plain parallel tempering (no cluster moves), PT with the
 isoenergetic cluster moves (ICM at T_k <= T_icm, with step 2a), or the
@@ -51,8 +51,10 @@ def method_schedule(method: str, T_icm: float):
 
 
 def delta_curve(ctx, lattice: int, L: int, disorder: int, couplings, spins, T, T_icm: float, seed: int,
-                method: str, log2_min: int, log2_max: int, instance_ids=None) -> DeltaCurve:
+                method: str, log2_min: int, log2_max: int, instance_ids=None, icm_every=None) -> DeltaCurve:
     ticm, every, two_a = method_schedule(method, T_icm)
+    if icm_every is not None and every:
+        every = int(icm_every)                 # cluster moves every n-th sweep instead of every sweep
     b = icmpt.Batch(ctx, lattice, L, disorder, couplings, T, min(ticm, 1e300), seed, spins=spins,
                     instance_ids=instance_ids)
     b.set_schedule(icm_every=every, enable_2a=two_a, t_meas=1 << 62)
@@ -86,6 +88,49 @@ def thermalization_time(curve: DeltaCurve, nsig: float = 2.0, floor: float = 0.0
     while i > 0 and ok[i - 1]:
         i -= 1
     return int(curve.t[i])
+
+
+@dataclass
+class FrequencyRow:
+    icm_every: int
+    t_therm: int | None      # thermalization time in sweeps (None: not within the run)
+    ms_per_sweep: float      # time of one simulation step of the batch at this frequency
+    cost_ms: float | None    # t_therm x ms_per_sweep: time to the criterion
+
+
+def icm_frequency(ctx, lattice: int, L: int, disorder: int, couplings, spins, T, T_icm: float, seed: int,
+                  candidates=(1, 2, 4, 8), log2_min: int = 4, log2_max: int = 16, nsig: float = 2.0,
+                  timing_sweeps: int = 256, instance_ids=None):
+    """The frequency of the cluster moves, judged on time to the
+    thermalization criterion -- the figure of merit of the isoenergetic
+    cluster algorithm -- and not on spin updates per second: cluster moves
+    every n-th sweep cost less per sweep but may need more sweeps.  For each
+    candidate n: the thermalization time t_n (sweeps) from Delta(t) of Eq. 2
+    at the lowest temperature over doubling windows (delta_curve,
+    thermalization_time), and the time per sweep s_n of the batch at that
+    frequency (a timed run of `timing_sweeps` steps); the cost is t_n s_n.
+    Returns (the n of least cost, or None when no candidate thermalized, and
+    the rows)."""
+    import time
+    rows = []
+    for n in candidates:
+        c = delta_curve(ctx, lattice, L, disorder, couplings, spins, T, T_icm, seed, "icm", log2_min, log2_max,
+                        instance_ids=instance_ids, icm_every=n)
+        t_th = thermalization_time(c, nsig=nsig)
+        b = icmpt.Batch(ctx, lattice, L, disorder, couplings, T, T_icm, seed, spins=spins,
+                        instance_ids=instance_ids)
+        b.set_schedule(icm_every=int(n))
+        b.run(16)
+        ctx.sync()
+        t0 = time.perf_counter()
+        b.run(timing_sweeps)
+        ctx.sync()
+        s_n = (time.perf_counter() - t0) * 1e3 / timing_sweeps
+        b.close()
+        rows.append(FrequencyRow(int(n), t_th, s_n, None if t_th is None else t_th * s_n))
+    done = [r for r in rows if r.cost_ms is not None]
+    best = min(done, key=lambda r: r.cost_ms).icm_every if done else None
+    return best, rows
 
 
 def anneal(ctx, lattice: int, L: int, disorder: int, couplings, spins, T_hi: float, T_lo: float, steps: int,

@@ -54,7 +54,8 @@ EXPORTS = [
     "icm_server_clock", "icm_server_cancel", "icm_batch_set_cluster", "icm_batch_cluster",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
-    "icm_batch_autotune", "icm_group_create", "icm_group_run", "icm_group_destroy", "icm_percolation",
+    "icm_batch_autotune", "icm_group_create", "icm_group_create_shared", "icm_group_info", "icm_group_run",
+    "icm_group_destroy", "icm_percolation",
     "icm_percolation_random", "icm_set_temperatures", "icm_save", "icm_load",
 ]
 
@@ -149,6 +150,8 @@ def load_library(path: str = LIB_PATH):
         L.icm_batch_set_threads.argtypes = [vp, i32]
         L.icm_batch_autotune.argtypes = [vp, u32, vp, vp]
         L.icm_group_create.argtypes = [vp, vp, i32, u32, ctypes.POINTER(vp)]
+        L.icm_group_create_shared.argtypes = [vp, vp, i32, u32, vp, ctypes.POINTER(vp)]
+        L.icm_group_info.argtypes = [vp, vp, vp, vp, vp, vp]
         L.icm_group_run.argtypes = [vp, u32]
         L.icm_group_destroy.argtypes = [vp]
         L.icm_percolation.argtypes = [vp, i32, i32, i32, vp, vp, u32]
@@ -582,17 +585,77 @@ class Batch:
             pass
 
 
-class Group:
-    """Several batches replayed as one CUDA graph (one forked stream per batch)."""
+SHARED_WIDTHS = (32, 64, 128, 224, 448, 896)   # threads per instance of the shared group kernel (divisors of 896)
 
-    def __init__(self, ctx: Context, batches, sweeps_per_launch: int):
+
+def tune_shared_widths(ctx: Context, batches, sweeps: int = 16, widths=SHARED_WIDTHS):
+    """Threads per instance (and with them the instances per tile) of each
+    batch for the shared group kernel, by timing: each batch alone in a
+    shared group at every width that fits, one untimed and one timed launch
+    of `sweeps` sweeps; the fastest width per spin update wins.  Every
+    batch's state is restored from a checkpoint afterwards, so tuning does
+    not advance the chains.  Returns (widths, {batch index: {width: ms}})."""
+    import time
+    best, table = [], {}
+    for c, b in enumerate(batches):
+        blob = b.checkpoint()
+        times = {}
+        for w in widths:
+            try:
+                g = Group(ctx, [b], sweeps, shared=True, team_threads=[w])
+            except IcmError:
+                continue
+            g.run(1)
+            ctx.sync()
+            t0 = time.perf_counter()
+            g.run(1)
+            ctx.sync()
+            times[w] = (time.perf_counter() - t0) * 1e3
+            g.close()
+        b.restore(blob)
+        if not times:
+            raise IcmError(-7, f"batch {c}: no width fits the shared group kernel")
+        table[c] = times
+        best.append(min(times, key=times.get))
+    return best, table
+
+
+class Group:
+    """Several batches replayed as one CUDA graph.  shared=False: one kernel
+    per batch on forked streams (icm_group_create); shared=True: the
+    instances of every batch share one persistent kernel launch, each run by
+    a team of team_threads[c] threads (icm_group_create_shared; None picks
+    the widths)."""
+
+    def __init__(self, ctx: Context, batches, sweeps_per_launch: int, shared: bool = False, team_threads=None):
         self.ctx, self._lib, self.batches = ctx, ctx._lib, list(batches)
         arr = (ctypes.c_void_p * len(self.batches))(*[b._h for b in self.batches])
         h = ctypes.c_void_p()
-        ctx.check(self._lib.icm_group_create(ctx._h, arr, len(self.batches), int(sweeps_per_launch),
-                                             ctypes.byref(h)))
+        if shared:
+            tt = None
+            if team_threads is not None:
+                tt = np.ascontiguousarray(team_threads, dtype=np.int32)
+                if tt.shape != (len(self.batches),):
+                    raise ValueError("team_threads: one entry per batch")
+            ctx.check(self._lib.icm_group_create_shared(ctx._h, arr, len(self.batches), int(sweeps_per_launch),
+                                                        None if tt is None else tt.ctypes.data, ctypes.byref(h)))
+        else:
+            ctx.check(self._lib.icm_group_create(ctx._h, arr, len(self.batches), int(sweeps_per_launch),
+                                                 ctypes.byref(h)))
         self._h = h
+        self.shared = bool(shared)
         self.sweeps = int(sweeps_per_launch)
+
+    def info(self) -> dict:
+        """Threads per instance and instances per tile of each batch; grid,
+        shared memory per CTA and tiles of the shared kernel."""
+        n = len(self.batches)
+        tt, tile = np.zeros(n, np.int32), np.zeros(n, np.int32)
+        g, sm, it = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        self.ctx.check(self._lib.icm_group_info(self._h, tt.ctypes.data, tile.ctypes.data, ctypes.byref(g),
+                                                ctypes.byref(sm), ctypes.byref(it)))
+        return dict(team_threads=tt.tolist(), tile=tile.tolist(), grid=g.value, smem_bytes=sm.value,
+                    n_items=it.value)
 
     def run(self, n_launches: int = 1):
         self.ctx.check(self._lib.icm_group_run(self._h, int(n_launches)))
