@@ -358,6 +358,7 @@ def serving_measurement(args):
     res = {t: srv.poll(t) for t in tickets}
     srv.close()
     lat = np.array([r.latency for r in res.values()])
+    lat_th = np.array([r.latency for r in res.values() if r.status == "thermalized"])
     therm = sum(r.status == "thermalized" for r in res.values())
     last_arrival = max(r.arrival for r in tickets.values())
     admits = np.array([r.admitted for r in res.values()])
@@ -391,7 +392,10 @@ def serving_measurement(args):
     alone_s = time.perf_counter() - a0
     return {
         "instances_thermalized_per_s": therm / wall, "latency_p50_s": float(np.percentile(lat, 50)),
-        "latency_p99_s": float(np.percentile(lat, 99)), "requests": len(res), "offered_per_s": args.rate,
+        "latency_p99_s": float(np.percentile(lat, 99)),
+        "latency_thermalized_p50_s": float(np.percentile(lat_th, 50)) if len(lat_th) else None,
+        "latency_thermalized_p99_s": float(np.percentile(lat_th, 99)) if len(lat_th) else None,
+        "requests": len(res), "offered_per_s": args.rate,
         "thermalized": int(therm), "not_thermalized": int(len(res) - therm), "wall_s": wall,
         "completed_per_s": len(res) / wall,
         "admitted_per_s": len(res) / max(float(admits.max()) - start, 1e-9),
