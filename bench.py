@@ -465,7 +465,11 @@ def run_mixed(args):
         updates += n * 2 * len(T) * N
     S = args.sweeps_per_step
     if args.mixed_mode == "shared":
-        widths, table = icmpt.tune_shared_widths(ctx, batches, sweeps=8)
+        if args.team_threads:
+            widths = [int(x) for x in args.team_threads.split(",")]
+            table = {c: {} for c in range(len(batches))}
+        else:
+            widths, table = icmpt.tune_shared_widths(ctx, batches, sweeps=8)
         g = icmpt.Group(ctx, batches, S, shared=True, team_threads=widths)
         info = g.info()
         for L, w, k in zip(MIXED["sizes"], info["team_threads"], info["tile"]):
@@ -796,6 +800,8 @@ def main():
                     help="serving: start one-at-a-time requests while this many seconds last")
     ap.add_argument("--no-serving", action="store_true", help="default workload: leave out the serving leg")
     ap.add_argument("--no-phases", action="store_true", help="leave out the sweep-only / ICM-only launches")
+    ap.add_argument("--team-threads", default="",
+                    help="3d_gauss_mixed shared: threads per instance of each size (comma list) instead of tuning")
     ap.add_argument("--mixed-mode", default="shared", choices=["shared", "graph"],
                     help="3d_gauss_mixed: one shared persistent kernel, or one kernel per size in a graph")
     ap.add_argument("--masks", type=int, default=200000)

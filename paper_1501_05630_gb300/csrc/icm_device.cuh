@@ -134,7 +134,7 @@ __device__ __forceinline__ void pt_warp(ET *E, int R, int np, const uint32_t *w,
     const uint32_t *wc = w + 32 * c;
     uint32_t acc = 0u;
     ET ek = E[c];
-#pragma unroll 1
+#pragma unroll 4
     for (int k = 0; k < 31; ++k) {
         if (k < np) {
             const ET ek1 = E[ICM_IDX(2 * k + 2 + c, R, 11)];
