@@ -190,6 +190,9 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
                             int32_t n_inst, const void *couplings, const int8_t *spins,
                             const uint32_t *instance_ids, const double *T, int32_t n_T,
                             double T_icm, uint64_t seed, uint32_t flags, icm_batch **out);
+/* Free a batch.  ICM_ERR_STATE while a group (icm_group_create*) holds it:
+ * the group's captured launches point at the batch's memory, so destroy
+ * the group first.                                                       */
 icm_status icm_batch_destroy(icm_batch *b);
 
 /* Replace the couplings and/or spins of every instance (either may be NULL
@@ -485,7 +488,9 @@ icm_status icm_batch_autotune(icm_batch *b, uint32_t sweeps, int32_t *best_threa
  * joined back into the context stream.  The graph is captured at creation
  * with the batches' current schedules and launch shapes and `sweeps_per_launch`;
  * icm_group_run replays it.  Create a group after the batches are set up
- * and re-create it after changing a schedule or the threads of a batch.   */
+ * and re-create it after changing a schedule or the threads of a batch.
+ * A group holds its batches: icm_batch_destroy refuses a batch of a live
+ * group (destroy the group first).                                        */
 typedef struct icm_group icm_group;
 icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, uint32_t sweeps_per_launch,
                             icm_group **out);

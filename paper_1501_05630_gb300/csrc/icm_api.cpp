@@ -298,6 +298,7 @@ struct icm_batch {
     long long *d_tmeas = nullptr;     // [n_inst]
     std::vector<uint8_t> h_active;
     std::vector<long long> h_tmeas;
+    int groups = 0;                   // live groups whose graphs launch this batch's kernels
 };
 
 extern "C" {
@@ -867,6 +868,8 @@ icm_status icm_batch_create(icm_ctx *ctx, int32_t lattice, int32_t L, int32_t di
 icm_status icm_batch_destroy(icm_batch *b)
 {
     if (!b) return ICM_ERR_ARG;
+    if (b->groups > 0)   // their captured launches still point at this batch's memory
+        return fail(b->ctx, ICM_ERR_STATE, "the batch belongs to a group: destroy the group first");
     destroy_batch(b);
     return ICM_OK;
 }
@@ -1456,11 +1459,14 @@ struct icm_group {
     size_t items_bytes = 0;
     std::vector<int> team_threads, tile;   // per batch: threads per instance, instances per tile
     int grid = 0, smem = 0, n_items = 0;
+    bool counted = false;                  // the batches count this group (icm_batch::groups)
 };
 
 static void destroy_group(icm_group *g)
 {
     if (!g) return;
+    if (g->counted)
+        for (auto *b : g->batches) --b->groups;
     if (g->exec) cudaGraphExecDestroy(g->exec);
     if (g->graph) cudaGraphDestroy(g->graph);
     for (auto e : g->events) cudaEventDestroy(e);
@@ -1549,6 +1555,8 @@ icm_status icm_group_create(icm_ctx *ctx, icm_batch *const *batches, int32_t n, 
         destroy_group(g);
         return cuda_fail(ctx, e, "group capture");
     }
+    for (auto *b : g->batches) ++b->groups;
+    g->counted = true;
     *out = g;
     return ICM_OK;
 }
@@ -1678,6 +1686,8 @@ icm_status icm_group_create_shared(icm_ctx *ctx, icm_batch *const *batches, int3
         destroy_group(g);
         return cuda_fail(ctx, e, "shared group capture");
     }
+    for (auto *b : g->batches) ++b->groups;
+    g->counted = true;
     *out = g;
     return ICM_OK;
 }

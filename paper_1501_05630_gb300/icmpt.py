@@ -572,8 +572,9 @@ class Batch:
         return dict(threads=t.value, ctas_per_sm=c.value, grid=g.value, smem_bytes=s.value, launches=la.value)
 
     def close(self):
+        """Free the batch (refused while a Group holds it: close the group first)."""
         if getattr(self, "_h", None) and getattr(self.ctx, "_h", None):
-            self._lib.icm_batch_destroy(self._h)
+            self.ctx.check(self._lib.icm_batch_destroy(self._h))
         self._h = None
 
     def __del__(self):

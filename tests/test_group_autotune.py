@@ -169,3 +169,19 @@ def test_shared_group_refuses_mixed_kinds(env):
         icmpt.Group(ctx, [a, c], 4, shared=True)                 # two seeds
     with pytest.raises(icmpt.IcmError):
         icmpt.Group(ctx, [a], 4, shared=True, team_threads=[96])  # not a divisor of 896
+
+
+def test_group_holds_its_batches(env):
+    """A batch of a live group cannot be destroyed (the captured launches
+    point at its memory); after the group is closed it can."""
+    icmpt, ctx = env
+    a = _batch(icmpt, ctx, 4, 2, 5)
+    b = _batch(icmpt, ctx, 6, 2, 5)
+    for shared in (False, True):
+        g = icmpt.Group(ctx, [a, b], 4, shared=shared)
+        with pytest.raises(icmpt.IcmError):
+            a.close()
+        g.run(1)
+        g.close()
+    a.close()
+    b.close()
