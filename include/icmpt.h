@@ -291,7 +291,11 @@ icm_status icm_read_icm_stats(icm_batch *b, uint64_t *out, uint32_t flags);
  *   flip2a [n_inst][n_T] int32: step 2a reversed copy 1
  *   seed_site [n_inst][n_T] int32 : seed site (-1: none)
  *   csize [n_inst][n_T] int32 : cluster size
- *   esum_before / esum_after [n_inst][n_T] double : E_a + E_b around 2a/2b
+ *   esum_before / esum_after [n_inst][n_T] double : E_a + E_b around 2a/2b;
+ *               esum_after is the sum of E_a and E_b each recomputed from
+ *               the spins after the move (not the E_b the kernel carries on,
+ *               (E_a + E_b)_before - E_a), so it tests that the move is
+ *               isoenergetic (exactly for +-J, to fp32 rounding for Gaussian)
  *   swap_acc [n_inst][2][n_T - 1] uint8 : PT decisions per copy
  * Any output pointer may be NULL.                                          */
 icm_status icm_read_trace(icm_batch *b, int32_t *n_pre, int32_t *flip2a, int32_t *seed_site,

@@ -595,7 +595,9 @@ def tune_shared_widths(ctx: Context, batches, sweeps: int = 16, widths=SHARED_WI
     shared group at every width that fits, one untimed and one timed launch
     of `sweeps` sweeps; the fastest width per spin update wins.  Every
     batch's state is restored from a checkpoint afterwards, so tuning does
-    not advance the chains.  Returns (widths, {batch index: {width: ms}})."""
+    not advance the chains (the cluster-move counters of icm_read_icm_stats
+    are not part of a checkpoint: they keep the tuning launches' counts).
+    Returns (widths, {batch index: {width: ms}})."""
     import time
     best, table = [], {}
     for c, b in enumerate(batches):
