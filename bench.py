@@ -61,7 +61,8 @@ ALG_OPS = {I.PM_J: lambda z: 24.5 + 12.5,
 
 
 
-def icm_ops(N: int, Nb: int, z: int, n_icm: int, pairs: float, moves: float, scans: float) -> float:
+def icm_ops(N: int, Nb: int, z: int, n_icm: int, pairs: float, moves: float, scans: float,
+            union_find: bool = False) -> float:
     """Algorithmic operations of the cluster moves (steps 2a/2b), the
     method's cost model of O(N + N_b) per pair plus the growth iterations:
       per ICM pair visited (`pairs` = instances x ICM temperatures x sweeps):
@@ -76,9 +77,13 @@ def icm_ops(N: int, Nb: int, z: int, n_icm: int, pairs: float, moves: float, sca
         and one OR into its own word (z + 2).
     One operation per spin (or bond) and pair, as the method is written,
     except the growth, counted per 32-bit word of the bit-parallel flood fill
-    that stands for one label-propagation pass of every pair."""
+    that stands for one label-propagation pass of every pair.  Union-find
+    growth (thread-block-cluster layout on request) counts instead, per moved
+    pair, one label reset per site, one union per bond and one root lookup
+    per site (2N + N_b); its scan counter is not used."""
     words = -(-n_icm // 16)
-    return pairs * 3 * N + moves * (98 + 3 * N + Nb) + scans * words * N * (z + 2)
+    growth = moves * (2 * N + Nb) if union_find else scans * words * N * (z + 2)
+    return pairs * 3 * N + moves * (98 + 3 * N + Nb) + growth
 
 
 def phase_fractions(b, stream, flush, S, n_inst, updates_per_step, ops_per_update, N, Nb, z, n_icm, peak):
@@ -117,7 +122,7 @@ def phase_fractions(b, stream, flush, S, n_inst, updates_per_step, ops_per_updat
     moves, scans = st[:, 0].sum() / 4, st[:, 1].sum() / 4        # per launch (4 launches counted)
     pairs = n_inst * n_icm * S
     sweep_ach = updates_per_step * ops_per_update / (t_sweep * 1e-3) / 1e12
-    icm_ach = icm_ops(N, Nb, z, n_icm, pairs, moves, scans) / (t_icm * 1e-3) / 1e12
+    icm_ach = icm_ops(N, Nb, z, n_icm, pairs, moves, scans, b.cluster_growth() > 0) / (t_icm * 1e-3) / 1e12
     return {"sweep_frac": sweep_ach / peak, "sweep_ms": t_sweep,
             "sweep_updates_per_ns": updates_per_step / (t_sweep * 1e6),
             "icm_frac": icm_ach / peak, "icm_ms": t_icm, "icm_moved_fraction": moves / pairs,
@@ -812,6 +817,8 @@ def main():
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--cluster", type=int, default=0, help="run each instance on a thread-block cluster of K CTAs")
     ap.add_argument("--cluster-threads", type=int, default=512)
+    ap.add_argument("--cluster-growth", type=int, default=-1,
+                    help="cluster layout's growth: 1 union-find, 0 label propagation, -1 the library's choice")
     ap.add_argument("--ref-sweeps", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -883,6 +890,7 @@ def main():
     b = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], J_dev, T, wl["T_icm"], wl["seed"],
                     spins=s_dev, instance_ids=ids)
     if args.cluster:
+        b.set_cluster_growth(args.cluster_growth)
         b.set_cluster(args.cluster, args.cluster_threads)     # one instance per thread-block cluster
     info = b.info()
     S = args.sweeps_per_step
@@ -933,6 +941,7 @@ def main():
         hb = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], J_pin.numpy(), T, wl["T_icm"], wl["seed"],
                          spins=s_pin.numpy(), instance_ids=ids)
         if args.cluster:
+            hb.set_cluster_growth(args.cluster_growth)
             hb.set_cluster(args.cluster, args.cluster_threads)
         for _ in range(2):
             hb.load(J_pin.numpy(), s_pin.numpy())
@@ -965,7 +974,7 @@ def main():
     # the whole step: the sweep's algorithmic ops plus the cluster moves' (from
     # the device counters of the timed steps), over the fused kernel's time
     icm_ops_step = icm_ops(N, Nb, z, n_icm, n * n_icm * S, stats[:, 0].sum() / args.steps,
-                           stats[:, 1].sum() / args.steps)
+                           stats[:, 1].sum() / args.steps, b.cluster_growth() > 0)
     achieved = (updates_per_step * ops_per_update + icm_ops_step) / (per_launch_ms * 1e-3) / 1e12
     # executed thread-instructions per update (ncu) give the issue utilisation
     # beside the algorithmic fraction
@@ -1002,7 +1011,9 @@ def main():
             "config": {"workload": args.workload, "desc": wl["desc"], "instances_per_gpu": n,
                        "sweeps_per_step": S, "n_icm": n_icm, "l2": "flushed between steps (256 MB write)",
                        "threads": info["threads"], "ctas_per_sm": info["ctas_per_sm"], "grid": info["grid"],
-                       "smem_bytes": info["smem_bytes"]},
+                       "smem_bytes": info["smem_bytes"],
+                       "cluster": {"K": args.cluster, "clusters": info["grid"] // args.cluster,
+                                   "union_find_pairs_per_group": b.cluster_growth()} if args.cluster else None},
             "icm_moves_per_s": icm_moves_per_s, "icm_attempts_per_s": icm_attempts_per_s,
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "cpu_baseline": cpu,
             "clocks": clk.summary(), "wall_s": t_wall,

@@ -540,8 +540,6 @@ icm_status icm_group_info(const icm_group *g, int32_t *team_threads, int32_t *ti
 icm_status icm_save(icm_batch *b, void *buf, size_t *len);
 icm_status icm_load(icm_batch *b, const void *buf, size_t len);
 
-/* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
- * dynamic shared memory bytes per CTA and kernel launches issued so far. */
 /* Thread-block-cluster layout: each instance runs on a cluster of K CTAs
  * (K = 2, 4 or 8; K SMs), each holding 1/K of the sites of each colour in
  * its shared memory and reading its neighbours' words through the cluster's
@@ -554,6 +552,26 @@ icm_status icm_load(icm_batch *b, const void *buf, size_t len);
  * couplings with absent bonds are loaded (its kernels change).            */
 icm_status icm_batch_set_cluster(icm_batch *b, int32_t K, int32_t threads);
 icm_status icm_batch_cluster(const icm_batch *b, int32_t *K);
+
+/* How the thread-block-cluster layout finds the clusters of step 2b (the
+ * connected component of q = -1 sites that holds the seed, "Reminder:
+ * Houdayer cluster algorithm" and step 2b of the isoenergetic cluster
+ * move).  mode 1: union-find labelling of the q = -1 sites over the
+ * cluster's shared memory, a few pairs at a time (lock-free hooking of
+ * roots by compare-and-swap, path halving); mode 0: label propagation, all
+ * pairs at once, one bit per pair and site, in rounds of in-place scans
+ * until nothing grows; mode -1 (default): the library's choice, label
+ * propagation (faster on every size measured: its word operations serve
+ * all pairs at once, where union-find works pair by pair).  Both give the
+ * same clusters, so the chain is the same bit for bit.
+ * Takes effect now on a clustered batch, else at icm_batch_set_cluster.
+ * icm_batch_cluster_growth gives the pairs per union-find group (0 = label
+ * propagation, or not clustered).  ICM_ERR_ARG for another mode.          */
+icm_status icm_batch_set_cluster_growth(icm_batch *b, int32_t mode);
+icm_status icm_batch_cluster_growth(const icm_batch *b, int32_t *pairs_per_group);
+
+/* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
+ * dynamic shared memory bytes per CTA and kernel launches issued so far. */
 
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,
                           int32_t *grid, int32_t *smem_bytes, int64_t *launches);

@@ -76,9 +76,34 @@ __device__ __forceinline__ uint32_t cl_ld(uint32_t addr)
 }
 
 
+// A word of this CTA's shared memory by its shared-window address.
+__device__ __forceinline__ uint32_t sh_ld(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void cl_st(uint32_t addr, uint32_t v)
 {
     asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Relaxed cluster-scope accesses of the union-find labels, which other
+// threads of the cluster change while they are read.
+__device__ __forceinline__ uint32_t cl_ld_rlx(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.cluster.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t cl_cas(uint32_t addr, uint32_t cmp, uint32_t v)
+{
+    uint32_t old;
+    asm volatile("atom.relaxed.cluster.shared::cluster.cas.b32 %0, [%1], %2, %3;"
+                 : "=r"(old) : "r"(addr), "r"(cmp), "r"(v) : "memory");
+    return old;
 }
 
 template <typename T>
@@ -97,7 +122,7 @@ struct CS {
     void *E, *Epart, *Esw, *Epair, *esum;
     uint32_t *thr;
     float *b2l;
-    uint32_t *mask;
+    uint32_t *mask, *lab, *sadr, *sroot;
     int *cntloc, *flags, *seed, *csz, *cnt_n, *cnt_d;
     uint32_t *flipw;
     uint32_t *swap_x;
@@ -129,6 +154,9 @@ __device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &
     S.thr = (uint32_t *)(smem + L.rtab);
     S.b2l = (float *)(smem + L.rtab);
     S.mask = (uint32_t *)(smem + L.mask);
+    S.lab = (uint32_t *)(smem + L.lab);
+    S.sadr = (uint32_t *)(smem + L.sadr);
+    S.sroot = (uint32_t *)(smem + L.sroot);
     S.cntloc = (int *)(smem + L.cntloc);
     S.flags = (int *)(smem + L.flags);
     S.seed = (int *)(smem + L.seed);
@@ -310,6 +338,293 @@ __device__ __forceinline__ void cl_metropolis(const KParams &P, const ClusterLay
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// Union-find over the cluster's shared memory.  A label word holds the
+// cluster-window address of its parent's label word; a root holds its own
+// address.  Roots are linked by a fixed random priority of their addresses
+// (a bijective hash): a root is hooked, by compare-and-swap on the root, only
+// under a root of higher priority, so priorities increase strictly along
+// every path (no cycle forms, a walk ends within N steps) and the trees stay
+// shallow, where linking by address would chain the sites of a row.  Words
+// of this CTA are reached through its own shared window, which is faster
+// than the cluster window.  In the phase where only this CTA's threads touch
+// its words (LOCAL) the accesses are plain; otherwise they are relaxed at
+// cluster scope, so that compare-and-swaps from every CTA are atomic with
+// one another.
+struct Uf {
+    uint32_t lab;     // cluster-window address of this CTA's first label word
+    uint32_t loc;     // its shared-window address
+    uint32_t span;    // bytes of this CTA's label words in use
+    int limit;        // N + 1
+};
+
+__device__ __forceinline__ uint32_t uf_prio(uint32_t x)
+{
+    x *= 0x9E3779B1u;
+    x ^= x >> 15;
+    x *= 0x85EBCA77u;
+    return x ^ (x >> 13);
+}
+
+template <bool LOCAL>
+__device__ __forceinline__ uint32_t uf_ld(const Uf &U, uint32_t a)
+{
+    const uint32_t o = a - U.lab;
+    uint32_t v;
+    if (LOCAL) v = sh_ld(U.loc + o);
+    else if (o < U.span)
+        asm volatile("ld.relaxed.cluster.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(U.loc + o) : "memory");
+    else v = cl_ld_rlx(a);
+    return v;
+}
+
+template <bool LOCAL>
+__device__ __forceinline__ uint32_t uf_cas(const Uf &U, uint32_t a, uint32_t cmp, uint32_t v)
+{
+    const uint32_t o = a - U.lab;
+    uint32_t old;
+    if (LOCAL)
+        asm volatile("atom.shared.cas.b32 %0, [%1], %2, %3;" : "=r"(old) : "r"(U.loc + o), "r"(cmp), "r"(v) : "memory");
+    else if (o < U.span)
+        asm volatile("atom.relaxed.cluster.shared::cta.cas.b32 %0, [%1], %2, %3;"
+                     : "=r"(old) : "r"(U.loc + o), "r"(cmp), "r"(v) : "memory");
+    else old = cl_cas(a, cmp, v);
+    return old;
+}
+
+// The root of x (after the unions: nothing changes the labels any more).
+__device__ __forceinline__ uint32_t uf_root(const Uf &U, uint32_t x)
+{
+    for (int i = 0; i < U.limit; ++i) {
+        const uint32_t p = uf_ld<false>(U, x);
+        if (p == x) return x;
+        x = p;
+    }
+    (void)ICM_IDX(U.limit, U.limit, 23);
+    return x;
+}
+
+// Union over the bonds of this CTA's colour-1 sites whose two ends have
+// q = -1 in a group pair, each bond once: those inside this CTA (REMOTE
+// false) or those to other CTAs (REMOTE true).  The lanes of a warp run in
+// lockstep: each iteration, every lane with a union in hand reads the
+// parents of both ends and climbs one level, or, at two distinct roots,
+// hooks the lower-priority root under the other (a failed swap goes on from
+// the root's new parent); a lane without one first takes its next bond.
+// Every iteration ends in a warp vote, so the lanes' loads issue together
+// (lanes that ran their own loops fell apart and waited for their loads one
+// by one).  `it` is bounded (never reached: each union ends within N climbs
+// and N failed swaps).
+template <int Z, bool REMOTE>
+__device__ __forceinline__ void uf_unions(const Uf &U, const CS &S, uint32_t gm0, uint32_t gm1, int n0, uint32_t mys,
+                                          uint32_t dlab, uint32_t qstride)
+{
+    const int nls = S.nls, hs = S.hs, nth = blockDim.x;
+    int j = (int)threadIdx.x - nth, li = 0, d = Z;
+    uint32_t x0 = 0u, x1 = 0u, y0 = 0u, y1 = 0u, ea = 0u, eb = 0u, a = 0u, b = 0u;
+    bool more = true, busy = false;
+    // iterations a lane can need: its bonds x pairs x (N climbs + N failed swaps + 1)
+    const long long cap = (long long)(hs / nth + 1) * Z * 32 * (2ll * U.limit + 1);
+    for (long long it = 0;; ++it) {
+        if (!busy && more) {
+            while (!(y0 | y1)) {                     // the next bond with a pair to link
+                if (d == Z) {
+                    j += nth;
+                    if (j >= hs) {
+                        more = false;
+                        break;
+                    }
+                    li = hs + j;
+                    const uint32_t w0 = S.s[li];
+                    x0 = (w0 ^ (w0 >> 1)) & gm0;
+                    x1 = 0u;
+                    if (gm1) {
+                        const uint32_t w1 = S.s[nls + li];
+                        x1 = (w1 ^ (w1 >> 1)) & gm1;
+                    }
+                    d = (x0 | x1) ? 0 : Z;
+                    ea = U.lab + 4u * (uint32_t)li;
+                    continue;
+                }
+                const uint32_t e = S.nb[li * Z + d];
+                ++d;
+                const uint32_t o = e - mys;
+                if ((o >= qstride) != REMOTE) continue;
+                if (x0) {
+                    const uint32_t v = REMOTE ? cl_ld(e) : S.s[o >> 2];
+                    y0 = x0 & (v ^ (v >> 1));
+                }
+                if (x1) {
+                    const uint32_t v = REMOTE ? cl_ld(e + qstride) : S.s[nls + (o >> 2)];
+                    y1 = x1 & (v ^ (v >> 1));
+                }
+                eb = e + dlab;
+            }
+            if (y0 | y1) {
+                uint32_t q;
+                if (y0) {
+                    q = (uint32_t)__popc(gm0 & ((y0 & (0u - y0)) - 1u));
+                    y0 &= y0 - 1u;
+                } else {
+                    q = (uint32_t)(n0 + __popc(gm1 & ((y1 & (0u - y1)) - 1u)));
+                    y1 &= y1 - 1u;
+                }
+                a = ea + q * qstride;
+                b = eb + q * qstride;
+                busy = true;
+            }
+        }
+        if (!__any_sync(kFull, busy)) break;
+        if (it >= cap) {
+            (void)ICM_IDX(U.limit, U.limit, 23);
+            break;
+        }
+        if (busy) {
+            const uint32_t pa = uf_ld<!REMOTE>(U, a), pb = uf_ld<!REMOTE>(U, b);
+            if (pa != a || pb != b) {
+                a = pa;
+                b = pb;
+            } else if (a == b) {
+                busy = false;
+            } else {
+                if (uf_prio(a) < uf_prio(b)) {
+                    const uint32_t x = a;
+                    a = b;
+                    b = x;
+                }
+                const uint32_t old = uf_cas<!REMOTE>(U, b, b, a);   // hook the lower-priority root under the other
+                if (old == b) busy = false;
+                else b = old;
+            }
+        }
+    }
+}
+
+// The own sites in the seed's component of each group pair: their cluster
+// bits are set.  Lockstep as above: each iteration a lane climbs one level
+// from its site's label toward the root.
+__device__ __forceinline__ void uf_mark(const Uf &U, const CS &S, uint32_t gm0, uint32_t gm1, int n0)
+{
+    const int nls = S.nls, nth = blockDim.x;
+    int li = (int)threadIdx.x - nth, q = 0;
+    uint32_t x0 = 0u, x1 = 0u, bit = 0u, c = 0u, c0 = 0u, c1 = 0u;
+    bool word1 = false, more = true, busy = false;
+    const long long cap = (long long)(nls / nth + 1) * 32 * (U.limit + 1);   // sites x pairs x (N climbs + 1)
+    for (long long it = 0;; ++it) {
+        if (!busy && more) {
+            while (!(x0 | x1)) {
+                if (li >= 0 && (c0 | c1)) {          // the last site's bits are complete
+                    if (c0) S.C0[li] |= c0;
+                    if (c1) S.C1[li] |= c1;
+                    c0 = c1 = 0u;
+                }
+                li += nth;
+                if (li >= nls) {
+                    more = false;
+                    break;
+                }
+                const uint32_t w0 = S.s[li];
+                x0 = (w0 ^ (w0 >> 1)) & gm0;
+                if (gm1) {
+                    const uint32_t w1 = S.s[nls + li];
+                    x1 = (w1 ^ (w1 >> 1)) & gm1;
+                }
+            }
+            if (x0 | x1) {
+                word1 = !x0;
+                uint32_t &x = word1 ? x1 : x0;
+                bit = x & (0u - x);
+                x &= x - 1u;
+                q = word1 ? n0 + __popc(gm1 & (bit - 1u)) : __popc(gm0 & (bit - 1u));
+                c = U.lab + 4u * (uint32_t)(q * nls + li);
+                busy = true;
+            }
+        }
+        if (!__any_sync(kFull, busy)) break;
+        if (it >= cap) {
+            (void)ICM_IDX(U.limit, U.limit, 23);
+            break;
+        }
+        if (busy) {
+            const uint32_t p = uf_ld<false>(U, c);
+            if (p != c) {
+                c = p;
+            } else {
+                if (c == S.sroot[q]) (word1 ? c1 : c0) |= bit;
+                busy = false;
+            }
+        }
+    }
+    if (li < nls && (c0 | c1)) {
+        if (c0) S.C0[li] |= c0;
+        if (c1) S.C1[li] |= c1;
+    }
+}
+
+// Step 2b(c) by union-find: the seed's component of q = -1 sites of every
+// moving pair, set in the cluster words C0 / C1 of the own sites (the seed's
+// bit is already set).  Pairs go in groups of L.ufg (act0 / act1: pair j of
+// word w at bit 2j of act_w).  Per group: labels reset (every site its own
+// root); union over the bonds inside this CTA, where every walk stays in this
+// CTA; cluster barrier; union over the bonds to other CTAs; cluster barrier;
+// every own site compares its root with the seed's.  The components are those
+// of the propagation in the other branch, so the cluster words are the same,
+// bit for bit.
+template <int Z>
+__device__ __forceinline__ void cl_grow_uf(const KParams &P, const ClusterLayout &L, const CS &S, uint32_t act0,
+                                           uint32_t act1)
+{
+    const int tid = threadIdx.x, nth = blockDim.x;
+    const int nls = S.nls, g = L.ufg;
+    Uf U;
+    U.lab = cl_map(S.base + L.lab, S.rank);
+    U.loc = S.base + (uint32_t)L.lab;
+    U.limit = P.N + 1;
+    const uint32_t mys = cl_map(S.base + L.s, S.rank);      // this CTA's spin words in the cluster window
+    const uint32_t dlab = (uint32_t)(L.lab - L.s);          // a site's spin word 0 -> its first label word
+    const uint32_t qstride = 4u * (uint32_t)nls;            // label arrays of consecutive group pairs; word 0 -> 1
+    uint32_t rest0 = act0, rest1 = act1;
+    int groups = 0;
+    while (rest0 | rest1) {
+        uint32_t gm0 = 0u, gm1 = 0u;                 // the next (up to) g pairs, in pair order
+        for (int q = 0; q < g && (rest0 | rest1); ++q) {
+            if (rest0) {
+                gm0 |= rest0 & (0u - rest0);
+                rest0 &= rest0 - 1u;
+            } else {
+                gm1 |= rest1 & (0u - rest1);
+                rest1 &= rest1 - 1u;
+            }
+        }
+        const int n0 = __popc(gm0), ng = n0 + __popc(gm1);
+        U.span = (uint32_t)ng * qstride;
+        ++groups;
+        for (int i = tid; i < ng * nls; i += nth) S.lab[i] = U.lab + 4u * (uint32_t)i;
+        __syncthreads();
+        uf_unions<Z, false>(U, S, gm0, gm1, n0, mys, dlab, qstride);
+        cl_sync();                                   // every CTA's own unions are done
+        uf_unions<Z, true>(U, S, gm0, gm1, n0, mys, dlab, qstride);
+        cl_sync();
+        if (tid < ng) {                              // the root of the tid-th group pair's seed
+            uint32_t m0 = gm0, m1 = gm1;
+            for (int q = 0; q < tid; ++q) {
+                if (m0) m0 &= m0 - 1u;
+                else m1 &= m1 - 1u;
+            }
+            const int k = m0 ? (__ffs(m0) - 1) >> 1 : 16 + ((__ffs(m1) - 1) >> 1);
+            S.sroot[tid] = uf_root(U, S.sadr[k] + (uint32_t)L.lab + (uint32_t)tid * qstride);
+        }
+        __syncthreads();
+        uf_mark(U, S, gm0, gm1, n0);
+        if (rest0 | rest1) cl_sync();                // walks through these labels end before the reset
+    }
+    __syncthreads();
+    if (S.rank == 0 && tid == 0) {
+        S.icmst[0] += (unsigned)(__popc(act0) + __popc(act1));
+        S.icmst[1] += 4u * (unsigned)groups;         // passes over the own sites
+    }
+}
+
 // Steps 2a and 2b (see cluster_moves in pt_icm.cu).
 template <bool GAUSS, int Z>
 __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const CS &S, uint32_t t, uint32_t inst,
@@ -380,6 +695,10 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                                 if (rank < pc) {
                                     const int li = 32 * m + nth_set_bit(w, rank);
                                     atomicOr((k < 16 ? S.C0 : S.C1) + ICM_IDX(li, nls, 21), 1u << (2 * (k & 15)));
+                                    if (L.ufg) {       // the seed's site address, for the union-find roots
+                                        const uint32_t sa = cl_map(S.base, S.rank) + 4u * (uint32_t)li;
+                                        for (uint32_t r2 = 0; r2 < S.K; ++r2) cl_st(cl_map(S.base + L.sadr + 4 * k, r2), sa);
+                                    }
                                     if (trace) P.tr_seed[(size_t)slot * P.nT + k] = (int)__ldg(P.pos2site + pos_of(P, S, li));
                                     break;
                                 }
@@ -434,7 +753,8 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     // words need no reset; a stale equal value could only add one empty round.
     constexpr int kScansPerRound = 4;
     const uint32_t dC0 = (uint32_t)(L.C0 - L.s), dC1 = (uint32_t)(L.C1 - L.s);
-    for (int round = 0;; ++round) {
+    if (L.ufg) cl_grow_uf<Z>(P, L, S, act0, act1);
+    else for (int round = 0;; ++round) {
         int grew = 0;
         for (int scan = 0; scan < kScansPerRound; ++scan)
             for (int li = tid; li < nls; li += nth) {
@@ -840,10 +1160,11 @@ int align_up16(int v) { return (v + 15) / 16 * 16; }
 
 }  // namespace
 
-ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss)
+ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss, int ufg)
 {
     ClusterLayout L{};
     L.K = K;
+    L.ufg = ufg;
     L.hs = (N / 2) / K;
     L.nls = 2 * L.hs;
     L.NWl = L.nls / 32;
@@ -866,7 +1187,12 @@ ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwar
     L.Esw = take(R * 4);
     L.Epair = take(32 * 4);
     L.rtab = take(gauss ? G * 32 * 4 : G * 32 * thr_stride(Z) * 4);
-    L.mask = take(32 * L.NWl * 4);
+    // the overlap masks are dead once the seeds are planted: the union-find
+    // labels take their place (one pair's labels are as large as the masks)
+    L.lab = take((ufg > 1 ? ufg : 1) * nls * 4);
+    L.mask = L.lab;
+    L.sadr = take(32 * 4);
+    L.sroot = take(kMaxUfGroup * 4);
     L.cntloc = take(2 * 32 * 4);
     L.flags = take(2 * 4);
     L.seed = take(32 * 4);

@@ -288,6 +288,7 @@ struct icm_batch {
     std::vector<int32_t> h_bad;
     // cluster layout: one instance per thread-block cluster of cluster_k CTAs
     int cluster_k = 0;
+    int cl_growth = -1;               // cluster growth: -1 = by the library (scans), 0 = scans, 1 = union-find
     icm::ClusterLayout cl{};
     int n_clusters = 0;
     // wide (global-resident) layout: per-CTA scratch, grown on demand (in allocs)
@@ -1324,12 +1325,26 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     const int hs = half / K;
     if (((hs + threads - 1) / threads) * P.Z >= 256 || (2 * hs + threads - 1) / threads >= 256)
         return fail(b->ctx, ICM_ERR_UNSUPPORTED, "too many sites per thread for the observable counters");
-    const icm::ClusterLayout L = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss);
+    // union-find growth (on request) takes one pair's labels in the place of
+    // the overlap masks, so one pair per group costs no shared memory; a
+    // group takes the most pairs (up to kMaxUfGroup) that keep as many
+    // clusters resident
+    const int ufg1 = b->cl_growth == 1 ? 1 : 0;
+    icm::ClusterLayout L = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss, ufg1);
     if (L.total > b->ctx->max_smem_optin) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster slice exceeds shared memory");
     int clusters = 0;
     cudaError_t e = icm::cluster_occupancy(b->gauss, P.Z, P.diluted != 0, K, threads, L.total, &clusters);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "cluster occupancy");
     if (clusters < 1) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster does not fit");
+    for (int g = 2; ufg1 && g <= icm::kMaxUfGroup && g <= (P.n_icm > 1 ? P.n_icm : 1); ++g) {
+        const icm::ClusterLayout Lg = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss, g);
+        int cg = 0;
+        if (Lg.total > b->ctx->max_smem_optin ||
+            icm::cluster_occupancy(b->gauss, P.Z, P.diluted != 0, K, threads, Lg.total, &cg) != cudaSuccess ||
+            cg < clusters)
+            break;
+        L = Lg;
+    }
     b->cluster_k = K;
     b->cl = L;
     b->threads = threads;
@@ -1350,6 +1365,28 @@ icm_status icm_batch_cluster(const icm_batch *b, int32_t *K)
 {
     if (!b || !K) return ICM_ERR_ARG;
     *K = b->cluster_k;
+    return ICM_OK;
+}
+
+icm_status icm_batch_set_cluster_growth(icm_batch *b, int32_t mode)
+{
+    if (!b) return ICM_ERR_ARG;
+    if (mode < -1 || mode > 1) return fail(b->ctx, ICM_ERR_ARG, "cluster growth must be -1, 0 or 1");
+    const int was = b->cl_growth;
+    b->cl_growth = mode;
+    if (!b->cluster_k) return ICM_OK;
+    const icm_status st = apply_cluster(b, b->cluster_k, b->threads);
+    if (st) {
+        b->cl_growth = was;
+        apply_cluster(b, b->cluster_k, b->threads);
+    }
+    return st;
+}
+
+icm_status icm_batch_cluster_growth(const icm_batch *b, int32_t *pairs_per_group)
+{
+    if (!b || !pairs_per_group) return ICM_ERR_ARG;
+    *pairs_per_group = b->cluster_k ? b->cl.ufg : 0;
     return ICM_OK;
 }
 
@@ -1761,7 +1798,8 @@ icm_status icm_set_temperatures(icm_batch *b, const double *T, int32_t n_T, doub
     b->T_icm = T_icm;
     b->n_icm = n_icm;
     P.n_icm = n_icm;
-    return apply_threads(b, b->threads);          // the shared-memory layout depends on n_icm
+    // the shared-memory layout depends on n_icm; a clustered batch stays clustered
+    return b->cluster_k ? apply_cluster(b, b->cluster_k, b->threads) : apply_threads(b, b->threads);
 }
 
 // ---------------------------------------------------------------- checkpoint / resume

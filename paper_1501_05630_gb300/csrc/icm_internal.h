@@ -159,7 +159,12 @@ struct ClusterLayout {
     int Esw;        // float or int32 [R]       this CTA's share of the sweep energies (read remotely)
     int Epair;      // float or int32 [32]      this CTA's share of the copy-a energies (read remotely)
     int rtab;       // thresholds (+-J) or -2 beta log2(e) (Gaussian), as in SmemLayout
-    int mask;       // uint32 [32][NWl]         overlap masks of the ICM pairs
+    int mask;       // uint32 [32][NWl]         overlap masks of the ICM pairs (in the lab region)
+    int lab;        // uint32 [max(ufg, 1)][nls] union-find parents: the cluster-window address of the
+                    //                          parent's label word (a root holds its own address)
+    int ufg;        // pairs per union-find group; 0 = growth by in-place scans (no labels)
+    int sadr;       // uint32 [32]              cluster-window address of each pair's seed site (written remotely)
+    int sroot;      // uint32 [8]               root of each group pair's seed
     int cntloc;     // int32 [2][32]            q = -1 sites per colour block and pair (read remotely)
     int flags;      // uint32 [2]               growth-round stamps, by round parity (written remotely)
     int seed;       // int32 [32]               1 = the pair moves
@@ -172,7 +177,9 @@ struct ClusterLayout {
     int icmst;      // uint64 [2]               cluster moves and growth scans of this instance (rank 0)
     int total;
 };
-ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss);
+// ufg: pairs per union-find group (1..kMaxUfGroup), or 0 for growth by scans.
+constexpr int kMaxUfGroup = 8;
+ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss, int ufg);
 cudaError_t launch_cluster(const KParams &P, const ClusterLayout &CL, bool gauss, int threads, int n_clusters,
                            uint32_t n_sweeps, cudaStream_t st);
 cudaError_t cluster_occupancy(bool gauss, int Z, bool dil, int K, int threads, int smem, int *clusters);

@@ -52,6 +52,7 @@ EXPORTS = [
     "icm_read_bond_counts", "icm_server_create", "icm_server_destroy", "icm_server_last_error",
     "icm_server_submit", "icm_server_step", "icm_server_poll", "icm_server_status", "icm_server_class_info",
     "icm_server_clock", "icm_server_cancel", "icm_batch_set_cluster", "icm_batch_cluster",
+    "icm_batch_set_cluster_growth", "icm_batch_cluster_growth",
     "icm_read_trace", "icm_batch_info", "icm_energies_static", "icm_batch_set_slot", "icm_batch_set_active",
     "icm_batch_start_window", "icm_therm_update", "icm_batch_delta", "icm_batch_set_threads",
     "icm_batch_autotune", "icm_group_create", "icm_group_create_shared", "icm_group_info", "icm_group_run",
@@ -557,6 +558,17 @@ class Batch:
         k = ctypes.c_int32()
         self.ctx.check(self._lib.icm_batch_cluster(self._h, ctypes.byref(k)))
         return k.value
+
+    def set_cluster_growth(self, mode: int):
+        """Cluster growth of the thread-block-cluster layout: 1 union-find,
+        0 label propagation by scans, -1 the library's choice (propagation)."""
+        self.ctx.check(self._lib.icm_batch_set_cluster_growth(self._h, int(mode)))
+
+    def cluster_growth(self) -> int:
+        """Pairs per union-find group (0: label propagation or not clustered)."""
+        g = ctypes.c_int32()
+        self.ctx.check(self._lib.icm_batch_cluster_growth(self._h, ctypes.byref(g)))
+        return g.value
 
     def autotune(self, sweeps: int = 16):
         """Pick the fastest CTA width; the batch's state is left unchanged."""

@@ -20,13 +20,16 @@ from test_gpu_parity import _check_icm_only_step, _compare_sweeps, _e64, _setup,
 pytestmark = pytest.mark.gpu
 
 
-def _cluster(K, threads):
+def _cluster(K, threads, growth=-1):
     def setup(b):
+        b.set_cluster_growth(growth)
         b.set_cluster(K, threads)
         assert b.cluster() == K and b.info()["threads"] == threads
+        assert (b.cluster_growth() > 0) == (growth == 1)    # union-find only when asked for
     return setup
 
 
+@pytest.mark.parametrize("growth", [1, 0], ids=["union_find", "propagation"])
 @pytest.mark.parametrize("kind,L,nT,T_hi,T_icm,n_inst,K,threads", [
     (O.CUBIC3D, 8, 24, 2.0, 1.0, 3, 2, 128),      # two spin words, slabs of 4 planes
     (O.CUBIC3D, 8, 12, 2.0, 1.0, 2, 8, 32),       # one plane per CTA: every z-neighbour remote
@@ -34,13 +37,45 @@ def _cluster(K, threads):
     (O.CHIMERA, 4, 30, 3.0, 1.5, 2, 2, 32),       # per-site degrees, padded neighbour lists
     (O.SQUARE2D, 32, 32, 1.5, 1.0, 1, 8, 256),    # 64 replicas
 ])
-def test_cluster_pmj_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, n_inst, K, threads):
-    _compare_sweeps(icm, kind, L, nT, 0.2, T_hi, T_icm, n_inst, 30, 0xC1 + L + K, setup=_cluster(K, threads))
+def test_cluster_pmj_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, n_inst, K, threads, growth):
+    _compare_sweeps(icm, kind, L, nT, 0.2, T_hi, T_icm, n_inst, 30, 0xC1 + L + K, setup=_cluster(K, threads, growth))
 
 
-def test_cluster_2d_L128_64_replicas(icm):
+@pytest.mark.parametrize("growth,K,threads", [(1, 8, 1024), (1, 8, 512), (0, 8, 1024)],
+                         ids=["union_find_1024", "union_find_512", "propagation_1024"])
+def test_cluster_2d_L128_64_replicas(icm, growth, K, threads):
     _compare_sweeps(icm, O.SQUARE2D, 128, 32, 0.2, 1.5, 1.0, 1, 6, 0x1502, check_every=3,
-                    setup=_cluster(8, 1024))
+                    setup=_cluster(K, threads, growth))
+
+
+def test_cluster_growth_modes_and_ladder_change(icm):
+    """The growth mode switches on a clustered batch without changing the
+    chain; a new ladder keeps the batch on clusters; modes outside -1..1
+    are refused."""
+    icmpt, ctx = icm
+    T = I.ladder(0.2, 1.5, 16)
+    g, J, s0, ids = _setup(O.SQUARE2D, 32, I.PM_J, 2, T, 0x77)
+    runs = []
+    for modes in ((1, 1), (0, 1), (1, 0)):
+        b = icmpt.Batch(ctx, O.SQUARE2D, 32, I.PM_J, J, T, 1.0, 0x77, spins=s0)
+        b.set_cluster(4, 128)
+        b.set_cluster_growth(modes[0])
+        b.run(5)
+        b.set_cluster_growth(modes[1])
+        assert b.cluster() == 4 and (b.cluster_growth() > 0) == (modes[1] == 1)
+        b.run(5)
+        runs.append((b.read_spins(), b.read_energies()))
+        with pytest.raises(icmpt.IcmError):
+            b.set_cluster_growth(2)
+        b.set_temperatures(I.ladder(0.25, 1.5, 16), 1.1)
+        assert b.cluster() == 4
+        b.close()
+    for r in runs[1:]:
+        assert np.array_equal(r[0], runs[0][0]) and np.array_equal(r[1], runs[0][1])
+    ref = [O.Instance(g, J[a].astype(np.float64), T, s0[a], pm=True, T_icm=1.0, seed=0x77, inst=a) for a in range(2)]
+    for a, r in enumerate(ref):
+        r.run(10)
+        assert np.array_equal(runs[0][0][a], r.s) and np.array_equal(runs[0][1][a], r.E)
 
 
 def test_cluster_schedule_and_multi_sweep_launches(icm):
