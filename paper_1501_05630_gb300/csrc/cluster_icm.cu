@@ -116,7 +116,7 @@ __device__ __forceinline__ T cl_ldT(uint32_t addr)
 
 // This CTA's view: pointers into its shared memory and cluster addresses.
 struct CS {
-    uint32_t *s, *C0, *C1, *nb;
+    uint32_t *s, *C, *nb;
     float *Jd;
     uint8_t *Jb, *zdeg;
     void *E, *Epart, *Esw, *Epair, *esum;
@@ -140,8 +140,7 @@ __device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &
 {
     CS S;
     S.s = (uint32_t *)(smem + L.s);
-    S.C0 = (uint32_t *)(smem + L.C0);
-    S.C1 = (uint32_t *)(smem + L.C1);
+    S.C = (uint32_t *)(smem + L.C);
     S.nb = (uint32_t *)(smem + L.nb);
     S.Jd = (float *)(smem + L.coup);
     S.Jb = (uint8_t *)(smem + L.coup);
@@ -514,8 +513,7 @@ __device__ __forceinline__ void uf_mark(const Uf &U, const CS &S, uint32_t gm0, 
         if (!busy && more) {
             while (!(x0 | x1)) {
                 if (li >= 0 && (c0 | c1)) {          // the last site's bits are complete
-                    if (c0) S.C0[li] |= c0;
-                    if (c1) S.C1[li] |= c1;
+                    S.C[li] |= c0 | (c1 << 1);
                     c0 = c1 = 0u;
                 }
                 li += nth;
@@ -555,14 +553,11 @@ __device__ __forceinline__ void uf_mark(const Uf &U, const CS &S, uint32_t gm0, 
             }
         }
     }
-    if (li < nls && (c0 | c1)) {
-        if (c0) S.C0[li] |= c0;
-        if (c1) S.C1[li] |= c1;
-    }
+    if (li < nls && (c0 | c1)) S.C[li] |= c0 | (c1 << 1);
 }
 
 // Step 2b(c) by union-find: the seed's component of q = -1 sites of every
-// moving pair, set in the cluster words C0 / C1 of the own sites (the seed's
+// moving pair, set in the cluster words of the own sites (the seed's
 // bit is already set).  Pairs go in groups of L.ufg (act0 / act1: pair j of
 // word w at bit 2j of act_w).  Per group: labels reset (every site its own
 // root); union over the bonds inside this CTA, where every walk stays in this
@@ -650,10 +645,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         const int k = (lane >> 1) + 16 * (lane & 1);
         if (k < nicm) S.mask[k * NWl + m] = col;
     }
-    for (int i = tid; i < nls; i += nth) {
-        S.C0[i] = 0u;
-        S.C1[i] = 0u;
-    }
+    for (int i = tid; i < nls; i += nth) S.C[i] = 0u;
     if (tid < 2) S.flipw[tid] = 0u;
     if (tid < 32) S.csz[tid] = 0;
     __syncthreads();
@@ -694,7 +686,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                                 const uint32_t pc = (uint32_t)__popc(w);
                                 if (rank < pc) {
                                     const int li = 32 * m + nth_set_bit(w, rank);
-                                    atomicOr((k < 16 ? S.C0 : S.C1) + ICM_IDX(li, nls, 21), 1u << (2 * (k & 15)));
+                                    atomicOr(S.C + ICM_IDX(li, nls, 21), 1u << (2 * (k & 15) + (k >> 4)));
                                     if (L.ufg) {       // the seed's site address, for the union-find roots
                                         const uint32_t sa = cl_map(S.base, S.rank) + 4u * (uint32_t)li;
                                         for (uint32_t r2 = 0; r2 < S.K; ++r2) cl_st(cl_map(S.base + L.sadr + 4 * k, r2), sa);
@@ -741,6 +733,9 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         __syncthreads();
         return;                                      // the same decision in every CTA
     }
+    // One cluster word per site holds every pair: bit 2j = pair j, bit 2j + 1
+    // = pair 16 + j, so that the domain word is q of the first spin word | q
+    // of the second << 1 and a neighbour is one load.
     // Growth in cluster rounds of kScansPerRound scans of the own sites each,
     // updated in place; within a round the CTAs scan without barriers, reading
     // each other's words as they are.  A warp that grew a site writes the
@@ -752,27 +747,23 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     // q = -1.  Stamps are (t << 16) + round + 1 (at most N < 2^16 rounds), so
     // words need no reset; a stale equal value could only add one empty round.
     constexpr int kScansPerRound = 4;
-    const uint32_t dC0 = (uint32_t)(L.C0 - L.s), dC1 = (uint32_t)(L.C1 - L.s);
+    const uint32_t dC = (uint32_t)(L.C - L.s);
+    const uint32_t actc = act0 | (act1 << 1);
     if (L.ufg) cl_grow_uf<Z>(P, L, S, act0, act1);
     else for (int round = 0;; ++round) {
         int grew = 0;
         for (int scan = 0; scan < kScansPerRound; ++scan)
             for (int li = tid; li < nls; li += nth) {
                 const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
-                const uint32_t d0 = (w0 ^ (w0 >> 1)) & act0, d1 = (w1 ^ (w1 >> 1)) & act1;
-                const uint32_t c0 = S.C0[li], c1 = S.C1[li];
-                if (d0 == c0 && d1 == c1) continue;
-                uint32_t nb0 = 0u, nb1 = 0u;
+                const uint32_t dm = (((w0 ^ (w0 >> 1)) & 0x55555555u) | (((w1 ^ (w1 >> 1)) & 0x55555555u) << 1)) & actc;
+                const uint32_t c = S.C[li];
+                if (dm == c) continue;
+                uint32_t nb = 0u;
 #pragma unroll
-                for (int d = 0; d < Z; ++d) {
-                    const uint32_t e = S.nb[li * Z + d];
-                    nb0 |= cl_ld(e + dC0);
-                    if (G > 1) nb1 |= cl_ld(e + dC1);
-                }
-                const uint32_t n0 = c0 | (d0 & nb0), n1 = c1 | (d1 & nb1);
-                if (n0 != c0 || n1 != c1) {
-                    S.C0[li] = n0;
-                    S.C1[li] = n1;
+                for (int d = 0; d < Z; ++d) nb |= cl_ld(S.nb[li * Z + d] + dC);
+                const uint32_t n = c | (dm & nb);
+                if (n != c) {
+                    S.C[li] = n;
                     grew = 1;
                 }
             }
@@ -791,7 +782,8 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
 
     // (d) flip the own sites; copy-a energies of the moved pairs
     for (int li = tid; li < nls; li += nth) {
-        const uint32_t c0 = S.C0[li], c1 = S.C1[li];
+        const uint32_t cw = S.C[li];
+        const uint32_t c0 = cw & 0x55555555u, c1 = (cw >> 1) & 0x55555555u;
         if (c0) S.s[li] ^= c0 | (c0 << 1);
         if (c1) S.s[nls + li] ^= c1 | (c1 << 1);
         if (trace) {
@@ -1177,8 +1169,7 @@ ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwar
     };
     const int nls = L.nls;
     L.s = take(G * nls * 4);
-    L.C0 = take(nls * 4);
-    L.C1 = take(nls * 4);
+    L.C = take(nls * 4);
     L.nb = take(nls * Z * 4);
     L.coup = take(gauss ? nls * Z * 4 : nls);
     L.zdeg = take(nls);

@@ -150,7 +150,7 @@ SmemLayout smem_layout(int N, int Z, int R, int G, int nT, int n_icm, int nwarps
 struct ClusterLayout {
     int K, hs, nls, NWl;   // CTAs, own sites per colour, own sites (2 hs), mask words (nls / 32)
     int s;          // uint32 [G][nls]   spin words
-    int C0, C1;     // uint32 [nls]      cluster bits of word 0 / word 1 pairs
+    int C;          // uint32 [nls]      cluster word: bit 2j = pair j, bit 2j + 1 = pair 16 + j
     int nb;         // uint32 [nls][Z]   cluster-window address of the neighbour's s[0] word
     int coup;       // float [nls][Z] (Gaussian) or uint8 [nls] sign bits (+-J)
     int zdeg;       // uint8 [nls]
