@@ -49,6 +49,11 @@ WORKLOADS = {
                         seed=0x1501056300000008,
                         desc="2D EA L=128 periodic (16384 spins), +-J, 20 instances, 32 T geometric [0.2,1.5], "
                              "ICM T<=1.0"),
+    # the largest 3D size of the serving menu, a few instances at a time (with --cluster: 8 SMs each)
+    "3d_gauss_L16": dict(lattice=I.CUBIC3D, L=16, disorder=I.GAUSS, n_inst=20, T=(0.2, 2.0, 32), T_icm=1.0,
+                         seed=0x1501056300000009,
+                         desc="3D EA L=16 periodic (4096 spins), Gaussian N(0,1) fp32, 20 instances, "
+                              "32 T geometric [0.2,2.0], ICM T<=1.0"),
 }
 
 # Algorithmic integer/fp operations per spin update (the per-unit figure of the
