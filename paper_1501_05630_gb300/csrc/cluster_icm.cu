@@ -123,6 +123,7 @@ struct CS {
     uint32_t *thr;
     float *b2l;
     uint32_t *mask, *lab, *sadr, *sroot;
+    uint16_t *gord;
     int *cntloc, *flags, *seed, *csz, *cnt_n, *cnt_d;
     uint32_t *flipw;
     uint32_t *swap_x;
@@ -156,6 +157,7 @@ __device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &
     S.lab = (uint32_t *)(smem + L.lab);
     S.sadr = (uint32_t *)(smem + L.sadr);
     S.sroot = (uint32_t *)(smem + L.sroot);
+    S.gord = L.gord >= 0 ? (uint16_t *)(smem + L.gord) : nullptr;
     S.cntloc = (int *)(smem + L.cntloc);
     S.flags = (int *)(smem + L.flags);
     S.seed = (int *)(smem + L.seed);
@@ -754,16 +756,22 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     // with at most four own sites per thread, each thread keeps their domain
     // and cluster words in registers across the scans and skips the sites
     // already absorbed (2D L=128 on 8 x 512: +8%, with 50-100 bytes of
-    // register spills under the 64 registers of the launch bounds)
+    // register spills under the 64 registers of the launch bounds).  On 2D
+    // lattices with four sites per thread the host gives each thread a 2 x 2
+    // block of sites, taken around the block (S.gord): a scan then carries
+    // the growth across the block and into the next lane's block (a model of
+    // the in-place scans on this workload's domains: 118 scans per sweep
+    // instead of 155).
     const bool in_regs = nls <= 4 * nth;
+    auto own = [&](int j) { return S.gord ? (int)S.gord[j * nth + tid] : tid + j * nth; };
     uint32_t dm[4], cw[4];
     uint32_t todo = 0u;                              // bit j: own site j not yet absorbed
     if (!L.ufg && in_regs) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            const int li = tid + j * nth;
+            const int li = own(j);
             dm[j] = cw[j] = 0u;
-            if (li < nls) {
+            if (tid + j * nth < nls) {
                 const uint32_t w0 = S.s[li], w1 = G > 1 ? S.s[nls + li] : 0u;
                 dm[j] = (((w0 ^ (w0 >> 1)) & 0x55555555u) | (((w1 ^ (w1 >> 1)) & 0x55555555u) << 1)) & actc;
                 cw[j] = S.C[li];
@@ -779,7 +787,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (!((todo >> j) & 1u)) continue;
-                    const int li = tid + j * nth;
+                    const int li = own(j);
                     uint32_t nb = 0u;
 #pragma unroll
                     for (int d = 0; d < Z; ++d) nb |= cl_ld(S.nb[li * Z + d] + dC);
@@ -1049,6 +1057,8 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
             for (int li = tid; li < nls; li += nth) S.zdeg[li] = zdeg[pos_of(P, S, li)];
     };
     if constexpr (!DIL) neighbour_table(P.nbr, P.zdeg);
+    if (L.gord >= 0)
+        for (int i = tid; i < nls; i += nth) S.gord[i] = P.cl_order[i];
     if constexpr (GAUSS) {
         for (int r = tid; r < 32 * G; r += nth) S.b2l[r] = r < R ? P.b2l[r] : 0.f;
     } else {
@@ -1194,7 +1204,8 @@ int align_up16(int v) { return (v + 15) / 16 * 16; }
 
 }  // namespace
 
-ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss, int ufg)
+ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss, int ufg,
+                             bool order)
 {
     ClusterLayout L{};
     L.K = K;
@@ -1226,6 +1237,7 @@ ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwar
     L.mask = L.lab;
     L.sadr = take(32 * 4);
     L.sroot = take(kMaxUfGroup * 4);
+    L.gord = order ? take(nls * 2) : -1;
     L.cntloc = take(2 * 32 * 4);
     L.flags = take(2 * 4);
     L.seed = take(32 * 4);

@@ -289,6 +289,7 @@ struct icm_batch {
     // cluster layout: one instance per thread-block cluster of cluster_k CTAs
     int cluster_k = 0;
     int cl_growth = -1;               // cluster growth: -1 = by the library (scans), 0 = scans, 1 = union-find
+    uint16_t *d_cl_order = nullptr;   // [N] growth order of the cluster layout's own sites (KParams::cl_order)
     icm::ClusterLayout cl{};
     int n_clusters = 0;
     // wide (global-resident) layout: per-CTA scratch, grown on demand (in allocs)
@@ -1330,14 +1331,45 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     // group takes the most pairs (up to kMaxUfGroup) that keep as many
     // clusters resident
     const int ufg1 = b->cl_growth == 1 ? 1 : 0;
-    icm::ClusterLayout L = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss, ufg1);
+    // 2D lattices whose CTAs hold whole pairs of rows, four sites per thread:
+    // each thread grows a 2 x 2 block of sites, around the block
+    // (a (x0, y0), b (x0 + 1, y0), d (x0 + 1, y0 + 1), c (x0, y0 + 1)),
+    // threads along the rows; local index of (x, y) in a CTA's rows: colour
+    // c = (x + y) & 1, c hs + y L / 2 + x / 2 (rows per CTA even, so the
+    // colour of a local row is that of the lattice row)
+    const int Lx = b->L, nls = 2 * hs;
+    const bool order = b->lattice == ICM_SQUARE2D && hs % (Lx / 2) == 0 && (hs / (Lx / 2)) % 2 == 0 &&
+                       nls == 4 * threads;
+    std::vector<uint16_t> ord;
+    if (order) {
+        ord.assign(nls, 0);
+        std::vector<uint8_t> seen(nls, 0);
+        const int dy[4] = {0, 0, 1, 1}, dx[4] = {0, 1, 1, 0};
+        for (int t = 0; t < threads; ++t)
+            for (int j = 0; j < 4; ++j) {
+                const int y = 2 * (t / (Lx / 2)) + dy[j], x = 2 * (t % (Lx / 2)) + dx[j];
+                const int li = ((x + y) & 1) * hs + y * (Lx / 2) + x / 2;
+                if (li >= nls || seen[li]) return fail(b->ctx, ICM_ERR_STATE, "growth order is not a permutation");
+                seen[li] = 1;
+                ord[(size_t)j * threads + t] = (uint16_t)li;
+            }
+        if (!b->d_cl_order) {
+            icm_status st = dalloc(b, &b->d_cl_order, (size_t)P.N);
+            if (st) return st;
+        }
+        ICM_CUDA(b->ctx, cudaMemcpyAsync(b->d_cl_order, ord.data(), ord.size() * 2, cudaMemcpyHostToDevice,
+                                         b->ctx->stream));
+        ICM_CUDA(b->ctx, cudaStreamSynchronize(b->ctx->stream));   // the host table is read by the copy
+    }
+    icm::ClusterLayout L = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss, ufg1, order);
     if (L.total > b->ctx->max_smem_optin) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster slice exceeds shared memory");
     int clusters = 0;
     cudaError_t e = icm::cluster_occupancy(b->gauss, P.Z, P.diluted != 0, K, threads, L.total, &clusters);
     if (e != cudaSuccess) return cuda_fail(b->ctx, e, "cluster occupancy");
     if (clusters < 1) return fail(b->ctx, ICM_ERR_UNSUPPORTED, "cluster does not fit");
     for (int g = 2; ufg1 && g <= icm::kMaxUfGroup && g <= (P.n_icm > 1 ? P.n_icm : 1); ++g) {
-        const icm::ClusterLayout Lg = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss, g);
+        const icm::ClusterLayout Lg = icm::cluster_layout(P.N, P.Z, P.R, P.G, P.nT, K, threads / 32, b->gauss, g,
+                                                          order);
         int cg = 0;
         if (Lg.total > b->ctx->max_smem_optin ||
             icm::cluster_occupancy(b->gauss, P.Z, P.diluted != 0, K, threads, Lg.total, &cg) != cudaSuccess ||
@@ -1347,6 +1379,7 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     }
     b->cluster_k = K;
     b->cl = L;
+    P.cl_order = order ? b->d_cl_order : nullptr;
     b->threads = threads;
     b->n_clusters = b->n_inst < clusters ? b->n_inst : clusters;
     b->grid = b->n_clusters * K;

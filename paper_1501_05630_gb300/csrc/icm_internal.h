@@ -107,6 +107,9 @@ struct KParams {
     float *tr_eb, *tr_ea;                                // [n_inst][nT]
     uint8_t *tr_swap;                                    // [n_inst][2][nT-1]
     uint32_t *tr_cmask;   // [n_inst][N][2] cluster words of the traced sweep, by position (NULL = off)
+    // thread-block-cluster layout of 2D lattices: the own site that thread t
+    // of a CTA grows as its j-th, at [j nth + t] (2 x 2 blocks of sites), or null
+    const uint16_t *cl_order;     // [nls]
     SmemLayout sm;
 };
 
@@ -165,6 +168,7 @@ struct ClusterLayout {
     int ufg;        // pairs per union-find group; 0 = growth by in-place scans (no labels)
     int sadr;       // uint32 [32]              cluster-window address of each pair's seed site (written remotely)
     int sroot;      // uint32 [8]               root of each group pair's seed
+    int gord;       // uint16 [nls]             KParams::cl_order in shared memory, or -1 (site tid + j nth)
     int cntloc;     // int32 [2][32]            q = -1 sites per colour block and pair (read remotely)
     int flags;      // uint32 [2]               growth-round stamps, by round parity (written remotely)
     int seed;       // int32 [32]               1 = the pair moves
@@ -179,7 +183,8 @@ struct ClusterLayout {
 };
 // ufg: pairs per union-find group (1..kMaxUfGroup), or 0 for growth by scans.
 constexpr int kMaxUfGroup = 8;
-ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss, int ufg);
+ClusterLayout cluster_layout(int N, int Z, int R, int G, int nT, int K, int nwarps, bool gauss, int ufg,
+                             bool order);
 cudaError_t launch_cluster(const KParams &P, const ClusterLayout &CL, bool gauss, int threads, int n_clusters,
                            uint32_t n_sweeps, cudaStream_t st);
 cudaError_t cluster_occupancy(bool gauss, int Z, bool dil, int K, int threads, int smem, int *clusters);

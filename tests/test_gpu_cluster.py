@@ -36,13 +36,14 @@ def _cluster(K, threads, growth=-1):
     (O.SQUARE2D, 16, 16, 1.5, 1.0, 3, 4, 64),
     (O.CHIMERA, 4, 30, 3.0, 1.5, 2, 2, 32),       # per-site degrees, padded neighbour lists
     (O.SQUARE2D, 32, 32, 1.5, 1.0, 1, 8, 256),    # 64 replicas
+    (O.SQUARE2D, 32, 32, 1.5, 1.0, 2, 4, 64),     # four sites per thread: growth by 2 x 2 blocks
 ])
 def test_cluster_pmj_sweep_by_sweep(icm, kind, L, nT, T_hi, T_icm, n_inst, K, threads, growth):
     _compare_sweeps(icm, kind, L, nT, 0.2, T_hi, T_icm, n_inst, 30, 0xC1 + L + K, setup=_cluster(K, threads, growth))
 
 
-@pytest.mark.parametrize("growth,K,threads", [(1, 8, 1024), (1, 8, 512), (0, 8, 1024)],
-                         ids=["union_find_1024", "union_find_512", "propagation_1024"])
+@pytest.mark.parametrize("growth,K,threads", [(1, 8, 1024), (1, 8, 512), (0, 8, 1024), (0, 8, 512)],
+                         ids=["union_find_1024", "union_find_512", "propagation_1024", "propagation_512_blocks"])
 def test_cluster_2d_L128_64_replicas(icm, growth, K, threads):
     _compare_sweeps(icm, O.SQUARE2D, 128, 32, 0.2, 1.5, 1.0, 1, 6, 0x1502, check_every=3,
                     setup=_cluster(K, threads, growth))
