@@ -822,6 +822,7 @@ def main():
     ap.add_argument("--sweeps-per-step", type=int, default=256)
     ap.add_argument("--cluster", type=int, default=0, help="run each instance on a thread-block cluster of K CTAs")
     ap.add_argument("--cluster-threads", type=int, default=512)
+    ap.add_argument("--n-inst", type=int, default=0, help="instances per GPU instead of the workload's own count")
     ap.add_argument("--cluster-growth", type=int, default=-1,
                     help="cluster layout's growth: 1 union-find, 0 label propagation, -1 the library's choice")
     ap.add_argument("--ref-sweeps", type=int, default=32)
@@ -881,7 +882,7 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = icmpt.Context(local, stream.cuda_stream)
 
-    n = wl["n_inst"]
+    n = args.n_inst or wl["n_inst"]
     T = I.ladder(*wl["T"])
     N, Nb = icmpt.lattice_size(wl["lattice"], wl["L"])
     R = 2 * len(T)
@@ -1013,7 +1014,9 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32" if wl["disorder"] == I.GAUSS else "u32",
             "data": "synthetic",
-            "config": {"workload": args.workload, "desc": wl["desc"], "instances_per_gpu": n,
+            "config": {"workload": args.workload,
+                       "desc": wl["desc"] + (f"; run with {n} instances per GPU" if args.n_inst else ""),
+                       "instances_per_gpu": n,
                        "sweeps_per_step": S, "n_icm": n_icm, "l2": "flushed between steps (256 MB write)",
                        "threads": info["threads"], "ctas_per_sm": info["ctas_per_sm"], "grid": info["grid"],
                        "smem_bytes": info["smem_bytes"],
