@@ -571,7 +571,10 @@ icm_status icm_batch_set_cluster_growth(icm_batch *b, int32_t mode);
 icm_status icm_batch_cluster_growth(const icm_batch *b, int32_t *pairs_per_group);
 
 /* Kernel-level facts for measurement: threads per CTA, CTAs per SM, grid,
- * dynamic shared memory bytes per CTA and kernel launches issued so far. */
+ * dynamic shared memory bytes per CTA and kernel launches issued so far.
+ * For the thread-block-cluster layout, CTAs per SM is the count when the
+ * most clusters are resident (their CTAs over the SMs, rounded up) and the
+ * shared memory is that of one CTA of a cluster.                          */
 
 icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_per_sm,
                           int32_t *grid, int32_t *smem_bytes, int64_t *launches);

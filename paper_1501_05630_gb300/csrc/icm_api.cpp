@@ -1383,7 +1383,8 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
     b->threads = threads;
     b->n_clusters = b->n_inst < clusters ? b->n_inst : clusters;
     b->grid = b->n_clusters * K;
-    b->ctas_per_sm = 1;
+    // CTAs per SM when the most clusters are resident
+    b->ctas_per_sm = (clusters * K + b->ctx->num_sms - 1) / b->ctx->num_sms;
     P.small_counts = 0;
     return ICM_OK;
 }
@@ -1957,7 +1958,7 @@ icm_status icm_batch_info(const icm_batch *b, int32_t *threads, int32_t *ctas_pe
     if (threads) *threads = b->threads;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
     if (grid) *grid = b->grid;
-    if (smem_bytes) *smem_bytes = b->kp.sm.total;
+    if (smem_bytes) *smem_bytes = b->cluster_k ? b->cl.total : b->kp.sm.total;
     if (launches) *launches = b->launches;
     return ICM_OK;
 }
