@@ -161,17 +161,20 @@ def test_group_with_cluster_batch_equals_separate_launches(icm):
     grp.close()
 
 
-def test_diluted_couplings_keep_the_cluster_layout(icm):
+@pytest.mark.parametrize("lattice,L,K,threads", [(O.CUBIC3D, 8, 4, 64), (O.SQUARE2D, 32, 4, 64)],
+                         ids=["3d", "2d_blocks"])
+def test_diluted_couplings_keep_the_cluster_layout(icm, lattice, L, K, threads):
     """Loading diluted couplings into a clustered batch keeps it on clusters
-    (kernels with per-instance tables); the chain equals the oracle's."""
+    (kernels with per-instance tables); the chain equals the oracle's (2D:
+    with the 2 x 2 growth blocks, four sites per thread)."""
     icmpt, ctx = icm
     T = I.ladder(0.3, 2.0, 8)
-    g, J, s0, ids = _setup(O.CUBIC3D, 8, I.PM_J, 2, T, 5)
-    b = icmpt.Batch(ctx, O.CUBIC3D, 8, I.PM_J, J, T, 1.0, 5, spins=s0)
-    b.set_cluster(4, 64)
+    g, J, s0, ids = _setup(lattice, L, I.PM_J, 2, T, 5)
+    b = icmpt.Batch(ctx, lattice, L, I.PM_J, J, T, 1.0, 5, spins=s0)
+    b.set_cluster(K, threads)
     Jd = I.dilute(J, 0.2, 5, ids)
     b.load(couplings=Jd)
-    assert b.cluster() == 4
+    assert b.cluster() == K
     b.run(9)
     spins, E = b.read_spins(), b.read_energies()
     for a in range(2):
@@ -179,5 +182,5 @@ def test_diluted_couplings_keep_the_cluster_layout(icm):
         r.run(9)
         assert np.array_equal(spins[a], r.s) and np.array_equal(E[a], r.E)
     b.load(couplings=J)                                   # back to undiluted couplings
-    assert b.cluster() == 4
+    assert b.cluster() == K
     b.close()
