@@ -12,6 +12,9 @@ Prints one JSON line.  `value` is spin updates per ns over the K timed steps
 (device time from CUDA events on the launching stream, state resident in HBM,
 L2 flushed between steps); `e2e` is the same metric through the C ABI with
 host buffers (H2D of couplings and spins, run, D2H of the observables).
+The default line also carries the served form (`serving`: instances
+thermalized/s and latency against plain PT one instance at a time) and the
+mixed-size workload in one persistent kernel launch (`mixed_sizes`).
 `--impl reference` times the CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -447,11 +450,12 @@ MIXED = dict(sizes=(4, 6, 8, 10, 12), counts=(4096, 2048, 1024, 512, 256), T=(0.
                   "[0.2,2.0], ICM T<=1.0, one seed (instance ids distinct across sizes)")
 
 
-def run_mixed(args):
+def mixed_measurement(args, steps: int, warmup: int, mode: str) -> dict:
     """Workload 4: uneven sizes in one captured launch.  shared (default): the
     instances of all sizes share one persistent kernel (icm_group_create_shared),
     threads per instance tuned by timing (icmpt.tune_shared_widths); graph: one
-    kernel per size on forked streams, CTA width autotuned per size."""
+    kernel per size on forked streams, CTA width autotuned per size.  Returns
+    the bench line of the workload."""
     import torch
     from paper_1501_05630_gb300 import build, icmpt
     torch.cuda.set_device(0)
@@ -468,13 +472,13 @@ def run_mixed(args):
         J = torch.from_numpy(I.couplings(Nb, I.GAUSS, MIXED["seed"], ids)).cuda()
         s0 = torch.from_numpy(I.initial_spins(N, 2 * len(T), MIXED["seed"], ids)).cuda()
         b = icmpt.Batch(ctx, I.CUBIC3D, L, I.GAUSS, J, T, MIXED["T_icm"], MIXED["seed"], spins=s0, instance_ids=ids)
-        if args.mixed_mode == "graph":
+        if mode == "graph":
             th, ms = b.autotune(sweeps=8)
             tuned[f"L{L}"] = {"threads": th, "ctas_per_sm": b.info()["ctas_per_sm"]}
         batches.append(b)
         updates += n * 2 * len(T) * N
     S = args.sweeps_per_step
-    if args.mixed_mode == "shared":
+    if mode == "shared":
         if args.team_threads:
             widths = [int(x) for x in args.team_threads.split(",")]
             table = {c: {} for c in range(len(batches))}
@@ -490,12 +494,12 @@ def run_mixed(args):
     else:
         g = icmpt.Group(ctx, batches, S)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.run(1)
     torch.cuda.synchronize()
     times = []
     with ClockSampler(0) as clk:
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -505,20 +509,28 @@ def run_mixed(args):
             e1.synchronize()
             times.append(e0.elapsed_time(e1))
     ms = float(np.sum(times))
-    value = updates * S * args.steps / (ms * 1e6)
+    value = updates * S * steps / (ms * 1e6)
     desc = MIXED["desc"] + (", all sizes in one persistent kernel launch (CUDA graph), threads per instance tuned"
-                            if args.mixed_mode == "shared" else
+                            if mode == "shared" else
                             ", one CUDA graph per step (one kernel per size on forked streams), CTA width "
                             "autotuned per size")
-    print(json.dumps({
-        "metric": "spin_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+    out = {
+        "metric": "spin_updates_per_ns", "value": value, "unit": "updates/ns", "n_gpus": 1, "steps": steps,
+        "warmup": warmup, "ms_per_step": ms / steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "3d_gauss_mixed", "mode": args.mixed_mode, "desc": desc, "sweeps_per_step": S,
+        "config": {"workload": "3d_gauss_mixed", "mode": mode, "desc": desc, "sweeps_per_step": S,
                    "tuned": tuned, "l2": "flushed between steps (256 MB write)"},
-        "gpu_launches": args.steps if args.mixed_mode == "shared" else args.steps * len(batches),
-        "clocks": clk.summary()}))
+        "gpu_launches": steps if mode == "shared" else steps * len(batches),
+        "clocks": clk.summary()}
     g.close()
+    for b in batches:
+        b.close()
+    ctx.close()
+    return out
+
+
+def run_mixed(args):
+    print(json.dumps(mixed_measurement(args, args.steps, args.warmup, args.mixed_mode)))
 
 
 THERMO = [
@@ -808,8 +820,10 @@ def main():
     ap.add_argument("--alone-sample", type=int, default=3, help="serving: one-at-a-time requests per menu kind")
     ap.add_argument("--alone-seconds", type=float, default=40.0,
                     help="serving: start one-at-a-time requests while this many seconds last")
-    ap.add_argument("--no-serving", action="store_true", help="default workload: leave out the serving leg")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="default workload: leave out the serving leg (and the mixed-size leg)")
     ap.add_argument("--no-phases", action="store_true", help="leave out the sweep-only / ICM-only launches")
+    ap.add_argument("--no-mixed", action="store_true", help="default workload: leave out the mixed-size leg")
     ap.add_argument("--team-threads", default="",
                     help="3d_gauss_mixed shared: threads per instance of each size (comma list) instead of tuning")
     ap.add_argument("--mixed-mode", default="shared", choices=["shared", "graph"],
@@ -1033,6 +1047,12 @@ def main():
             out.update({k: sv[k] for k in ("instances_thermalized_per_s", "latency_p50_s", "latency_p99_s")})
             sv.pop("clocks", None)
             out["serving"] = sv
+        if world == 1 and args.workload == "3d_gauss_L8" and not (args.no_mixed or args.no_serving):
+            # the benchmark spec item 2: uneven sizes sharing one persistent kernel launch
+            mx = mixed_measurement(args, 5, 3, "shared")
+            out["mixed_sizes"] = {k: mx[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "gpu_launches",
+                                                     "clocks")}
+            out["mixed_sizes"]["config"] = mx["config"]
         print(json.dumps(out))
     b.close()
     ctx.close()
