@@ -13,8 +13,9 @@ Prints one JSON line.  `value` is spin updates per ns over the K timed steps
 L2 flushed between steps); `e2e` is the same metric through the C ABI with
 host buffers (H2D of couplings and spins, run, D2H of the observables).
 The default line also carries the served form (`serving`: instances
-thermalized/s and latency against plain PT one instance at a time) and the
-mixed-size workload in one persistent kernel launch (`mixed_sizes`).
+thermalized/s and latency against plain PT one instance at a time), the
+mixed-size workload in one persistent kernel launch (`mixed_sizes`) and 2D
+L=128 on thread-block clusters (`large_instances`: 20 and 36 instances).
 `--impl reference` times the CPU oracle on the host cores instead.
 """
 from __future__ import annotations
@@ -525,6 +526,43 @@ def mixed_measurement(args, steps: int, warmup: int, mode: str) -> dict:
     g.close()
     for b in batches:
         b.close()
+    ctx.close()
+    return out
+
+
+def cluster_measurement(n_inst: int, steps: int = 3, warmup: int = 2, sweeps: int = 64) -> dict:
+    """The largest 2D size of the serving menu on 8-CTA thread-block clusters
+    (the 2d_pmj_L128 workload with n_inst instances): spin updates/ns over
+    `steps` launches of `sweeps` sweeps, CUDA events, L2 flushed between."""
+    import torch
+    from paper_1501_05630_gb300 import icmpt
+    wl = WORKLOADS["2d_pmj_L128"]
+    stream = torch.cuda.current_stream()
+    ctx = icmpt.Context(torch.cuda.current_device(), stream.cuda_stream)
+    T = I.ladder(*wl["T"])
+    N, Nb = icmpt.lattice_size(wl["lattice"], wl["L"])
+    ids = np.arange(n_inst, dtype=np.uint32)
+    b = icmpt.Batch(ctx, wl["lattice"], wl["L"], wl["disorder"], I.couplings(Nb, wl["disorder"], wl["seed"], ids), T,
+                    wl["T_icm"], wl["seed"], spins=I.initial_spins(N, 2 * len(T), wl["seed"], ids), instance_ids=ids)
+    b.set_cluster(8, 512)
+    info = b.info()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        b.run(sweeps)
+    torch.cuda.synchronize()
+    ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.run(sweeps)
+        e1.record(stream)
+        e1.synchronize()
+        ms += e0.elapsed_time(e1)
+    out = {"value": n_inst * 2 * len(T) * N * sweeps * steps / (ms * 1e6), "unit": "updates/ns",
+           "ms_per_step": ms / steps, "sweeps_per_step": sweeps, "steps": steps, "instances": n_inst,
+           "clusters": info["grid"] // 8, "gpu_launches": steps}
+    b.close()
     ctx.close()
     return out
 
@@ -1053,6 +1091,11 @@ def main():
             out["mixed_sizes"] = {k: mx[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "gpu_launches",
                                                      "clocks")}
             out["mixed_sizes"]["config"] = mx["config"]
+            # the largest serving size on 8-CTA thread-block clusters: 20 instances,
+            # and one per resident cluster of 8 x 512 (36 on a full GB300)
+            out["large_instances"] = {"workload": "2D EA L=128 periodic (16384 spins), +-J, 32 T geometric [0.2,1.5], "
+                                                  "ICM T<=1.0, one instance per 8-CTA cluster of 512 threads",
+                                      "x20": cluster_measurement(20), "x36": cluster_measurement(36)}
         print(json.dumps(out))
     b.close()
     ctx.close()
