@@ -1086,7 +1086,7 @@ def main():
             sv.pop("clocks", None)
             out["serving"] = sv
         if world == 1 and args.workload == "3d_gauss_L8" and not (args.no_mixed or args.no_serving):
-            # the benchmark spec item 2: uneven sizes sharing one persistent kernel launch
+            # uneven sizes (3D L = 4..12) sharing one persistent kernel launch
             mx = mixed_measurement(args, 5, 3, "shared")
             out["mixed_sizes"] = {k: mx[k] for k in ("value", "unit", "ms_per_step", "steps", "warmup", "gpu_launches",
                                                      "clocks")}
