@@ -181,6 +181,35 @@ __device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &
     return S;
 }
 
+// The Z neighbour addresses of own site li, in 16-byte loads when Z is a
+// multiple of 4 (a row starts 16-byte aligned), else 8-byte loads: one
+// shared-memory instruction instead of four for a 2D site.
+template <int Z>
+__device__ __forceinline__ void nb_row(const uint32_t *nb, int li, uint32_t (&e)[Z])
+{
+    const uint32_t *row = nb + li * Z;
+    if constexpr (Z % 4 == 0) {
+#pragma unroll
+        for (int d = 0; d < Z; d += 4) {
+            const uint4 v = *reinterpret_cast<const uint4 *>(row + d);
+            e[d] = v.x;
+            e[d + 1] = v.y;
+            e[d + 2] = v.z;
+            e[d + 3] = v.w;
+        }
+    } else if constexpr (Z % 2 == 0) {
+#pragma unroll
+        for (int d = 0; d < Z; d += 2) {
+            const uint2 v = *reinterpret_cast<const uint2 *>(row + d);
+            e[d] = v.x;
+            e[d + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int d = 0; d < Z; ++d) e[d] = row[d];
+    }
+}
+
 // Sum over the cluster, in rank order, of the ET value at byte offset `off`
 // of every CTA's shared memory (the same result in every CTA).
 template <typename ET>
@@ -222,8 +251,9 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
         const uint32_t sw = sw0 >> sh0;
         const uint32_t site = __ldg(P.pos2site + pos_of(P, S, li));
         uint32_t nw[Z];
+        nb_row<Z>(S.nb, li, nw);
 #pragma unroll
-        for (int d = 0; d < Z; ++d) nw[d] = cl_ld(S.nb[li * Z + d] + goff);
+        for (int d = 0; d < Z; ++d) nw[d] = cl_ld(nw[d] + goff);
         uint32_t flip = 0;
         if constexpr (GAUSS) {
             float J2[Z];
@@ -789,8 +819,12 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                     if (!((todo >> j) & 1u)) continue;
                     const int li = own(j);
                     uint32_t nb = 0u;
+                    // the site's neighbour row in one 16-byte (Z = 4) or 8-byte loads
+                    // (2D L=128 on 8 x 512: +22% against four 4-byte loads)
+                    uint32_t e[Z];
+                    nb_row<Z>(S.nb, li, e);
 #pragma unroll
-                    for (int d = 0; d < Z; ++d) nb |= cl_ld(S.nb[li * Z + d] + dC);
+                    for (int d = 0; d < Z; ++d) nb |= cl_ld(e[d] + dC);
                     const uint32_t n = cw[j] | (dm[j] & nb);
                     if (n != cw[j]) {
                         S.C[li] = n;
@@ -807,9 +841,10 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                     const uint32_t dmw = (((w0 ^ (w0 >> 1)) & 0x55555555u) | (((w1 ^ (w1 >> 1)) & 0x55555555u) << 1)) & actc;
                     const uint32_t c = S.C[li];
                     if (dmw == c) continue;
-                    uint32_t nb = 0u;
+                    uint32_t e[Z], nb = 0u;
+                    nb_row<Z>(S.nb, li, e);
 #pragma unroll
-                    for (int d = 0; d < Z; ++d) nb |= cl_ld(S.nb[li * Z + d] + dC);
+                    for (int d = 0; d < Z; ++d) nb |= cl_ld(e[d] + dC);
                     const uint32_t n = c | (dmw & nb);
                     if (n != c) {
                         S.C[li] = n;
@@ -865,8 +900,9 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                 const int li = hs + j;               // colour-1 sites: every bond once
                 const uint32_t sw = sg[li] >> cb;
                 uint32_t nw[Z];
+                nb_row<Z>(S.nb, li, nw);
 #pragma unroll
-                for (int d = 0; d < Z; ++d) nw[d] = cl_ld(S.nb[li * Z + d] + goff) >> cb;
+                for (int d = 0; d < Z; ++d) nw[d] = cl_ld(nw[d] + goff) >> cb;
                 if constexpr (GAUSS) {
                     float J2[Z];
                     float Jsum = 0.f;
@@ -996,9 +1032,10 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
             const uint32_t w = sg[li];
             const uint32_t qp = (w ^ (w >> 1)) & 0x55555555u;
             uint32_t x[Z];                 // a padding entry points at the site itself: x = 0
+            nb_row<Z>(S.nb, li, x);
 #pragma unroll
             for (int d = 0; d < Z; ++d) {
-                const uint32_t wq = cl_ld(S.nb[li * Z + d] + goff);
+                const uint32_t wq = cl_ld(x[d] + goff);
                 x[d] = (qp ^ ((wq ^ (wq >> 1)) & 0x55555555u)) << 1;
             }
             uint32_t c0, c1, c2, c3;
