@@ -793,7 +793,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     // the in-place scans on this workload's domains: 118 scans per sweep
     // instead of 155).
     const bool in_regs = nls <= 4 * nth;
-    auto own = [&](int j) { return S.gord ? (int)S.gord[j * nth + tid] : tid + j * nth; };
+    auto own = [&](int j) { return S.gord ? (int)S.gord[4 * tid + j] : tid + j * nth; };
     uint32_t dm[4], cw[4];
     uint32_t todo = 0u;                              // bit j: own site j not yet absorbed
     if (!L.ufg && in_regs) {
@@ -814,10 +814,13 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         int grew = 0;
         if (in_regs) {
             for (int scan = 0; scan < kScansPerRound; ++scan) {
+                // the thread's four block sites in one 8-byte load
+                uint2 o = make_uint2(0u, 0u);
+                if (S.gord) o = *reinterpret_cast<const uint2 *>(S.gord + 4 * tid);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (!((todo >> j) & 1u)) continue;
-                    const int li = own(j);
+                    const int li = S.gord ? (int)(((j < 2 ? o.x : o.y) >> (16 * (j & 1))) & 0xFFFFu) : tid + j * nth;
                     uint32_t nb = 0u;
                     // the site's neighbour row in one 16-byte (Z = 4) or 8-byte loads
                     // (2D L=128 on 8 x 512: +22% against four 4-byte loads)

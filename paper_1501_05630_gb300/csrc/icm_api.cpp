@@ -1351,7 +1351,7 @@ static icm_status apply_cluster(icm_batch *b, int K, int threads)
                 const int li = ((x + y) & 1) * hs + y * (Lx / 2) + x / 2;
                 if (li >= nls || seen[li]) return fail(b->ctx, ICM_ERR_STATE, "growth order is not a permutation");
                 seen[li] = 1;
-                ord[(size_t)j * threads + t] = (uint16_t)li;
+                ord[(size_t)4 * t + j] = (uint16_t)li;
             }
         if (!b->d_cl_order) {
             icm_status st = dalloc(b, &b->d_cl_order, (size_t)P.N);

@@ -108,7 +108,7 @@ struct KParams {
     uint8_t *tr_swap;                                    // [n_inst][2][nT-1]
     uint32_t *tr_cmask;   // [n_inst][N][2] cluster words of the traced sweep, by position (NULL = off)
     // thread-block-cluster layout of 2D lattices: the own site that thread t
-    // of a CTA grows as its j-th, at [j nth + t] (2 x 2 blocks of sites), or null
+    // of a CTA grows as its j-th, at [4 t + j] (2 x 2 blocks of sites), or null
     const uint16_t *cl_order;     // [nls]
     SmemLayout sm;
 };
