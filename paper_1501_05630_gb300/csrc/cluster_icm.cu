@@ -133,6 +133,7 @@ struct CS {
     long long *acc64, *nmeas;
     unsigned long long *icmst;
     uint32_t base;        // shared-window address of this CTA's dynamic shared memory
+    uint32_t dCs;         // a neighbour-table entry (the neighbour's cluster word) minus this: its spin word 0
     uint32_t rank, K;
     int hs, nls;
 };
@@ -174,6 +175,7 @@ __device__ __forceinline__ CS make_cs(unsigned char *smem, const ClusterLayout &
     S.nmeas = (long long *)(smem + L.nmeas);
     S.icmst = (unsigned long long *)(smem + L.icmst);
     S.base = (uint32_t)__cvta_generic_to_shared(smem);
+    S.dCs = (uint32_t)(L.C - L.s);
     S.rank = cl_rank();
     S.K = (uint32_t)L.K;
     S.hs = L.hs;
@@ -240,7 +242,7 @@ __device__ __forceinline__ void cl_sweep_pass(const KParams &P, const CS &S, uin
     const int rbase = 32 * g + 16 * H;
     const int sh0 = 16 * H;
     const int npairs8 = (P.R - rbase + 7) >> 3;
-    const uint32_t goff = (uint32_t)(g * S.nls * 4);
+    const uint32_t goff = (uint32_t)(g * S.nls * 4) - S.dCs;   // neighbour entry -> its spin word g
     uint32_t *sg = S.s + g * S.nls;
     ET acc[16];
 #pragma unroll
@@ -477,7 +479,7 @@ __device__ __forceinline__ void uf_unions(const Uf &U, const CS &S, uint32_t gm0
                     ea = U.lab + 4u * (uint32_t)li;
                     continue;
                 }
-                const uint32_t e = S.nb[li * Z + d];
+                const uint32_t e = S.nb[li * Z + d] - S.dCs;   // the neighbour's spin word 0
                 ++d;
                 const uint32_t o = e - mys;
                 if ((o >= qstride) != REMOTE) continue;
@@ -781,7 +783,6 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
     // q = -1.  Stamps are (t << 16) + round + 1 (at most N < 2^16 rounds), so
     // words need no reset; a stale equal value could only add one empty round.
     constexpr int kScansPerRound = 6;
-    const uint32_t dC = (uint32_t)(L.C - L.s);
     const uint32_t actc = act0 | (act1 << 1);
     // with at most four own sites per thread, each thread keeps their domain
     // and cluster words in registers across the scans and skips the sites
@@ -827,7 +828,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                     uint32_t e[Z];
                     nb_row<Z>(S.nb, li, e);
 #pragma unroll
-                    for (int d = 0; d < Z; ++d) nb |= cl_ld(e[d] + dC);
+                    for (int d = 0; d < Z; ++d) nb |= cl_ld(e[d]);
                     const uint32_t n = cw[j] | (dm[j] & nb);
                     if (n != cw[j]) {
                         S.C[li] = n;
@@ -847,7 +848,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                     uint32_t e[Z], nb = 0u;
                     nb_row<Z>(S.nb, li, e);
 #pragma unroll
-                    for (int d = 0; d < Z; ++d) nb |= cl_ld(e[d] + dC);
+                    for (int d = 0; d < Z; ++d) nb |= cl_ld(e[d]);
                     const uint32_t n = c | (dmw & nb);
                     if (n != c) {
                         S.C[li] = n;
@@ -894,7 +895,7 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
         for (int g = 0; g < G; ++g) {
             const uint32_t act = g ? act1 : act0;
             if (!act) continue;
-            const uint32_t goff = (uint32_t)(g * nls * 4);
+            const uint32_t goff = (uint32_t)(g * nls * 4) - S.dCs;   // neighbour entry -> its spin word g
             const uint32_t *sg = S.s + g * nls;
             ET acc[16];
 #pragma unroll
@@ -1022,7 +1023,7 @@ __device__ void cl_measure(const KParams &P, const ClusterLayout &L, const CS &S
     __syncthreads();
     for (int g = 0; g < P.G; ++g) {
         const int npair = min(16, nT - 16 * g);
-        const uint32_t goff = (uint32_t)(g * nls * 4);
+        const uint32_t goff = (uint32_t)(g * nls * 4) - S.dCs;   // neighbour entry -> its spin word g
         const uint32_t *sg = S.s + g * nls;
         uint32_t pl[kPlanes];   // even bit 2k: q = -1 sites of pair k; odd bit 2k+1: its q_i q_j = -1 bonds
 #pragma unroll
@@ -1081,7 +1082,7 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
     const int N = P.N, R = P.R, nT = P.nT, G = P.G, nls = S.nls, hs = S.hs, half = P.half;
 
     if (tid < 2) S.flags[tid] = 0;   // growth round stamps (the same in every CTA at all times)
-    // neighbour table: cluster-window address of each neighbour's spin word
+    // neighbour table: cluster-window address of each neighbour's cluster word
     // (of the batch's lattice here; per instance for diluted batches, below)
     auto neighbour_table = [&](const uint16_t *nbr, const uint8_t *zdeg) {
         for (int i = tid; i < nls * Z; i += nth) {
@@ -1091,7 +1092,7 @@ __global__ void __launch_bounds__(kMaxThreadsWide, 1) cluster_kernel(const KPara
             const int hq = q - cq * half;
             const uint32_t rq = (uint32_t)(hq / hs);
             const int lq = cq * hs + hq % hs;
-            S.nb[i] = cl_map(S.base + L.s, rq) + 4u * (uint32_t)lq;
+            S.nb[i] = cl_map(S.base + L.C, rq) + 4u * (uint32_t)lq;
         }
         if (!GAUSS && (DIL || !P.const_z))
             for (int li = tid; li < nls; li += nth) S.zdeg[li] = zdeg[pos_of(P, S, li)];

@@ -154,7 +154,7 @@ struct ClusterLayout {
     int K, hs, nls, NWl;   // CTAs, own sites per colour, own sites (2 hs), mask words (nls / 32)
     int s;          // uint32 [G][nls]   spin words
     int C;          // uint32 [nls]      cluster word: bit 2j = pair j, bit 2j + 1 = pair 16 + j
-    int nb;         // uint32 [nls][Z]   cluster-window address of the neighbour's s[0] word
+    int nb;         // uint32 [nls][Z]   cluster-window address of the neighbour's cluster word C
     int coup;       // float [nls][Z] (Gaussian) or uint8 [nls] sign bits (+-J)
     int zdeg;       // uint8 [nls]
     int E;          // float or int32 [R]       energies (the same in every CTA)
