@@ -172,7 +172,7 @@ icm_status create_class(icm_server *s, const Request &r, ShapeClass **out)
         // a class of large instances (one wide CTA each) runs each instance on
         // a thread-block cluster instead: lower latency per request.  8 CTAs
         // of 512 threads for 8192 sites and more, of 256 below (2D L=64 and
-        // 3D L=16, 1 or 20 instances: 37-88 us per sweep, against 37-101
+        // 3D L=16, 1 or 20 instances: 36-81 us per sweep, against 37-95
         // with 512 threads)
         int32_t th = 0, cps = 0, grid = 0, smem = 0;
         int64_t launches = 0;
