@@ -820,7 +820,14 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                 if (S.gord) o = *reinterpret_cast<const uint2 *>(S.gord + 4 * tid);
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    if (!((todo >> j) & 1u)) continue;
+                    // absorbed sites are skipped, except on 2D lattices, where the
+                    // test costs more than it saves (2D L=128: +3.9% without it;
+                    // 3D L=16: -1.7%)
+                    if constexpr (Z != 4) {
+                        if (!((todo >> j) & 1u)) continue;
+                    } else {
+                        if (tid + j * nth >= nls) continue;
+                    }
                     const int li = S.gord ? (int)(((j < 2 ? o.x : o.y) >> (16 * (j & 1))) & 0xFFFFu) : tid + j * nth;
                     uint32_t nb = 0u;
                     // the site's neighbour row in one 16-byte (Z = 4) or 8-byte loads
@@ -834,7 +841,8 @@ __device__ void cl_cluster_moves(const KParams &P, const ClusterLayout &L, const
                         S.C[li] = n;
                         cw[j] = n;
                         grew = 1;
-                        if (n == dm[j]) todo &= ~(1u << j);
+                        if constexpr (Z != 4)
+                            if (n == dm[j]) todo &= ~(1u << j);
                     }
                 }
             }
